@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Throughput of the sum-factorized SIPG DG-Laplace apply on GB300.
+
+Headline workload: y = A x in FP64, k = 3 (n = 4) on 128^3 cells of the unit
+cube, 134,217,728 DoFs, x ~ U[-1, 1] (seed 0); one step = one tp_apply
+launch. Vectors are 1.07 GB each, far larger than the 129 MB L2, so no L2
+flush is needed between steps. Metric: GDoF/s (DoFs of all ranks / time).
+
+--impl reference times the CPU oracle (oracle/sipg.py block apply) on a
+bounded slab sample of the same workload on the host cores.
+Multi-GPU (torchrun): every rank applies its own independent replica
+(no data exchange); value = all ranks' DoFs / max-over-ranks time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_DEG, NC = 3, 128
+METRIC = "GDoF/s of sum-factorized DG-Laplace apply (FP64, k=3, 128^3 cells)"
+WORKLOAD = "SIPG DG-Laplace apply y=Ax, FP64, k=3, 128^3 cells (134,217,728 DoFs), unit cube, penalty (k+1)^2/h"
+SLAB = (128, 128, 8)  # oracle sample: same k and per-DoF work, 8,388,608 DoFs
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
+    p.add_argument("--kernel-only", action="store_true",
+                   help="only the warm-up and timed applies (for profiler captures of a smaller case)")
+    p.add_argument("--cells", type=int, default=None, help="cells per direction (default 128)")
+    p.add_argument("--k", type=int, default=None, help="degree (default 3)")
+    p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def profile_traffic(kernel_src, summary):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel is unchanged since."""
+    path = os.path.join(ROOT, "profiles", summary)
+    src = os.path.join(ROOT, "paper_2407_09621_gb300", "csrc", kernel_src)
+    if not (os.path.exists(path) and os.path.exists(src)):
+        return None
+    text = open(path).read()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    m_h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not (m_h and m_t) or m_h.group(1) != h:
+        return None
+    return float(m_t.group(1))
+
+
+def oracle_sample(seconds=10.0):
+    """The CPU oracle's block apply on a slab of the workload, repeated for ~`seconds`."""
+    from oracle.sipg import Mesh, BlockOperator
+    from tp_synth import uniform_vector
+    m = Mesh(*SLAB)
+    bo = BlockOperator(m, K_DEG)
+    x = uniform_vector(m.ncells * (K_DEG + 1) ** 3, seed=0)
+    reps, t_total = 0, 0.0
+    while t_total < seconds or reps < 1:
+        t0 = time.perf_counter()
+        bo.apply(x)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    cores = len(os.sched_getaffinity(0))
+    return {"value": reps * len(x) / t_total / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle block apply (numpy/BLAS, FP64) on a {SLAB[0]}x{SLAB[1]}x{SLAB[2]}-cell slab, "
+                      f"k={K_DEG}, {len(x)} DoFs, {reps} reps, {t_total:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.sipg import Mesh, BlockOperator
+    from tp_synth import uniform_vector
+    m = Mesh(*SLAB)
+    bo = BlockOperator(m, K_DEG)
+    x = uniform_vector(m.ncells * (K_DEG + 1) ** 3, seed=0)
+    for _ in range(args.warmup):
+        bo.apply(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        bo.apply(x)
+    dt = time.perf_counter() - t0
+    value = args.steps * len(x) / dt / 1e9
+    cores = len(os.sched_getaffinity(0))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{SLAB[0]}x{SLAB[1]}x{SLAB[2]}-cell slab per step"},
+        "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
+                         "sample": f"oracle block apply on a {SLAB[0]}x{SLAB[1]}x{SLAB[2]}-cell slab per step"},
+        "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def time_applies(op, y, x, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        op.apply(y, x, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        op.apply(y, x, stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    return per, ev[0][0].elapsed_time(ev[-1][1])
+
+
+def secondary(stream):
+    """A few steps of the other apply configurations (same kernel family), reported beside the headline."""
+    import torch
+    from paper_2407_09621_gb300 import DGLaplace
+    from tp_synth import uniform_vector
+    out = []
+    for k, nc, prec in [(7, 64, "fp64"), (3, 80, "fp32"), (3, 80, "fp16"), (3, 80, "bf16"),
+                        (7, 40, "fp32"), (7, 40, "fp16")]:
+        op = DGLaplace(nc, nc, nc, k, prec)
+        x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
+        y = torch.empty_like(x)
+        per, _ = time_applies(op, y, x, 10, 3, stream)
+        ms = statistics.mean(per)
+        out.append({"k": k, "cells": f"{nc}^3", "precision": prec, "dofs": op.ndofs, "ms": ms,
+                    "gdofs": op.ndofs / ms / 1e6,
+                    "hbm_gbs": 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6,
+                    "tflops": op.info["flops_per_dof"] * op.ndofs / ms / 1e9})
+        op.close()
+        del x, y
+    return out
+
+
+def run_ours(args):
+    import torch
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    from tp_synth import uniform_vector
+
+    nc = args.cells or NC
+    kdeg = args.k or K_DEG
+    op = DGLaplace(nc, nc, nc, kdeg, args.prec)
+    ndofs = op.ndofs
+    if args.kernel_only:
+        x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)
+        y = torch.empty_like(x)
+        per, total_ms = time_applies(op, y, x, args.steps, args.warmup, torch.cuda.current_stream())
+        print(json.dumps({"kernel_only": True, "k": kdeg, "cells": nc, "prec": args.prec, "dofs": ndofs,
+                          "ms_per_apply": statistics.mean(per), "gdofs": ndofs / statistics.mean(per) / 1e6}))
+        op.close()
+        return
+    x_host = torch.from_numpy(uniform_vector(ndofs, seed=rank)).pin_memory()
+    y_host = torch.empty_like(x_host).pin_memory()
+    x = x_host.to("cuda")
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        op.apply(y, x, stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    per, total_ms = time_applies(op, y, x, args.steps, 0, stream)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = world * ndofs * args.steps / (total_ms * 1e-3) / 1e9
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region)
+    e2e_steps = max(3, min(args.steps, 10))
+    op.apply_host(y_host, x_host)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        op.apply_host(y_host, x_host)
+    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+    e2e_bytes = ndofs * op.info["elem_bytes"]
+    e2e_t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
+    if world > 1:
+        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = world * ndofs / float(e2e_t.item()) / 1e9
+
+    avg_launch_ms = statistics.mean(per)
+    flops_launch = op.info["flops_per_dof"] * ndofs
+    achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
+    peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
+    traffic = profile_traffic("apply_cc.cu", "apply_cc_fp64_k3_128cubed.md")
+
+    if rank != 0:
+        return
+    extra = None if args.no_extra else secondary(stream)
+    cpu = oracle_sample() if world == 1 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "k": K_DEG, "cells": [NC, NC, NC], "dofs": ndofs,
+                   "l2": "inputs (1.07 GB per vector) larger than L2, no flush", "parallelism": f"replicas x{world}",
+                   "kernel": "apply_cc (FP64 DFMA sum factorization)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": "FP64 DFMA pipe, measured live by tp_bench_fma_peak (register-only FMA chains)",
+                     "flops_per_dof": op.info["flops_per_dof"],
+                     "hbm_gbs_algorithmic": 16.0 * ndofs / (avg_launch_ms * 1e-3) / 1e9},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": e2e_bytes,
+                "d2h_bytes_per_step": e2e_bytes},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "extra": extra,
+    }
+    print(json.dumps(line), flush=True)
+    op.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,32 @@
+/*
+ * libtp measurement support (not part of the method).
+ *
+ * The paper reports arithmetic rates against the hardware peak of the pipe a
+ * kernel runs on (Sec. 4.2, Sec. 6). The FP64 and FP32 FMA-pipe peaks of the
+ * GPU are not published per part and clocks, so the library measures them
+ * with a register-only kernel: every thread runs a fixed number of
+ * independent fused multiply-add chains, no memory traffic except one store
+ * per thread at the end.
+ */
+#ifndef TP_BENCH_H
+#define TP_BENCH_H
+
+#include "tp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Measures the FMA-pipe throughput for precision p (TP_FP64: DFMA,
+ * TP_FP32: FFMA) on the current device, on `stream` (NULL = default),
+ * best of 5 timed launches after 2 warm-ups, CUDA-event timed.
+ * *tflops receives flops/s / 1e12 (FMA = 2 flops). Allocates and frees a
+ * small device buffer. Blocks until done. Errors: TP_ERR_INVALID_ARG (NULL
+ * out, other precisions), TP_ERR_CUDA, TP_ERR_OOM. */
+tp_status tp_bench_fma_peak(int precision, double* tflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TP_BENCH_H */

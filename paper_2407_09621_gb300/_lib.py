@@ -1,0 +1,127 @@
+"""ctypes binding of libtp (include/tp.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls. Device
+vectors are passed as integer addresses (e.g. ``torch.Tensor.data_ptr()``)
+and streams as integer ``cudaStream_t`` handles (e.g.
+``torch.cuda.current_stream().cuda_stream``). A non-zero tp_status raises
+``TPError`` carrying the library's message. There is no fallback: if
+libtp.so has not been built, importing this module raises.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtp.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+HEADERS = [os.path.join(INCLUDE, f) for f in ("tp.h", "tp_bench.h")]
+
+TP_OK, TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_OOM = 0, 1, 2, 3
+TP_ERR_NONFINITE, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = 4, 5, 6, 7
+STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ERR_OOM",
+                4: "TP_ERR_NONFINITE", 5: "TP_ERR_NOT_CONVERGED", 6: "TP_ERR_TIMEOUT",
+                7: "TP_ERR_UNSUPPORTED"}
+TP_FP64, TP_FP32, TP_FP16, TP_BF16 = 0, 1, 2, 3
+TP_PENALTY_CONFIG, TP_PENALTY_PAPER = 0, 1
+TP_KERNEL_AUTO, TP_KERNEL_CUDA_CORE, TP_KERNEL_TENSOR = 0, 1, 2
+
+
+class TPError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libtp.so is not built ({LIB_PATH}); run `python paper_2407_09621_gb300/build.py` "
+                      "(the CUDA library is required: there is no CPU fallback)")
+lib = ctypes.CDLL(LIB_PATH)
+
+
+class tp_op_opts(ctypes.Structure):
+    _fields_ = [("penalty", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int)]
+
+
+class tp_op_info_t(ctypes.Structure):
+    _fields_ = [("ncells", ctypes.c_longlong), ("ndofs", ctypes.c_longlong), ("k", ctypes.c_int),
+                ("n", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_sig = {
+    "tp_last_error": (ctypes.c_char_p, []),
+    "tp_mesh_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "tp_mesh_destroy": (ctypes.c_int, [_vp]),
+    "tp_dg_laplace_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.c_int, ctypes.c_int,
+                                            ctypes.POINTER(tp_op_opts)]),
+    "tp_op_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(tp_op_info_t)]),
+    "tp_op_destroy": (ctypes.c_int, [_vp]),
+    "tp_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "tp_apply_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "tp_bench_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def header_functions():
+    """Names of every function the public headers declare."""
+    text = ""
+    for h in HEADERS:
+        with open(h) as f:
+            text += f.read()
+    return sorted(set(re.findall(r"^\s*(?:tp_status|const char\s*\*|void)\s+(tp_\w+)\s*\(", text, re.M)))
+
+
+def _check(status):
+    if status != TP_OK:
+        raise TPError(status, lib.tp_last_error().decode())
+
+
+def tp_last_error():
+    return lib.tp_last_error().decode()
+
+
+def tp_mesh_create(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0):
+    h = _vp()
+    _check(lib.tp_mesh_create(ctypes.byref(h), nx, ny, nz, lx, ly, lz))
+    return h
+
+
+def tp_mesh_destroy(mesh):
+    _check(lib.tp_mesh_destroy(mesh))
+
+
+def tp_dg_laplace_create(mesh, k, precision, penalty=TP_PENALTY_CONFIG, kernel=TP_KERNEL_AUTO, ec=0):
+    h = _vp()
+    opts = tp_op_opts(penalty, kernel, ec)
+    _check(lib.tp_dg_laplace_create(ctypes.byref(h), mesh, k, precision, ctypes.byref(opts)))
+    return h
+
+
+def tp_op_get_info(op):
+    info = tp_op_info_t()
+    _check(lib.tp_op_get_info(op, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in tp_op_info_t._fields_}
+
+
+def tp_op_destroy(op):
+    _check(lib.tp_op_destroy(op))
+
+
+def tp_apply(op, y_ptr, x_ptr, stream=0):
+    _check(lib.tp_apply(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))
+
+
+def tp_apply_host(op, y_ptr, x_ptr, stream=0):
+    _check(lib.tp_apply_host(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))
+
+
+def tp_bench_fma_peak(precision, stream=0):
+    out = ctypes.c_double()
+    _check(lib.tp_bench_fma_peak(precision, ctypes.byref(out), _vp(stream)))
+    return out.value

@@ -1,0 +1,217 @@
+// C-ABI entry points of libtp: handles, validation, error text, dispatch.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+tp_status cuda_status(int err, const char* what) {
+  if (err == cudaSuccess) return TP_OK;
+  set_error("%s: %s", what, cudaGetErrorString((cudaError_t)err));
+  return err == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA;
+}
+
+cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+
+size_t elem_bytes(tp_precision p) {
+  switch (p) {
+    case TP_FP64: return 8;
+    case TP_FP32: return 4;
+    case TP_FP16: return 2;
+    case TP_BF16: return 2;
+  }
+  return 0;
+}
+
+template <typename T>
+static void fill_const(OpConst<T>& c, const tp_op_s* op) {
+  memset(&c, 0, sizeof(c));
+  const int n = op->n;
+  for (int d = 0; d < 3; ++d) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        c.M[d][i * kMaxN + j] = (T)op->dir[d].M[i * n + j];
+        c.L[d][i * kMaxN + j] = (T)op->dir[d].L[i * n + j];
+      }
+    c.gamma[d] = (T)op->dir[d].gamma;
+    c.half_inv_h[d] = (T)(0.5 / op->dir[d].h);
+  }
+  for (int i = 0; i < n; ++i) {
+    c.d0[i] = (T)op->ref.d0[i];
+    c.d1[i] = (T)op->ref.d1[i];
+  }
+}
+
+// algorithmic flops per DoF of the sum-factorized apply (FMA = 2 flops):
+// 7 n x n contractions (7n^4 FMAs per cell) + 6 derivative traces (n^3 each)
+// + tangential masses on face arrays (y: 4 n^3, z: 8 n^3) + 6 normal expansions (n^3)
+double apply_flops_per_dof(int n) { return 2.0 * (7.0 * n + 24.0); }
+
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+const char* tp_last_error(void) { return g_err; }
+
+tp_status tp_mesh_create(tp_mesh* out, int nx, int ny, int nz, double lx, double ly, double lz) {
+  if (!out) { set_error("tp_mesh_create: out is NULL"); return TP_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) { set_error("tp_mesh_create: cell counts must be >= 1"); return TP_ERR_INVALID_ARG; }
+  if (!(lx > 0) || !(ly > 0) || !(lz > 0)) { set_error("tp_mesh_create: lengths must be > 0"); return TP_ERR_INVALID_ARG; }
+  const long long nc = (long long)nx * ny * nz;
+  if (nc > (1LL << 53)) { set_error("tp_mesh_create: too many cells"); return TP_ERR_INVALID_ARG; }
+  tp_mesh_s* m = new (std::nothrow) tp_mesh_s{nx, ny, nz, lx, ly, lz};
+  if (!m) { set_error("tp_mesh_create: out of host memory"); return TP_ERR_OOM; }
+  *out = m;
+  return TP_OK;
+}
+
+tp_status tp_mesh_destroy(tp_mesh m) {
+  delete m;
+  return TP_OK;
+}
+
+tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, const tp_op_opts* opts) {
+  if (!out) { set_error("tp_dg_laplace_create: out is NULL"); return TP_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!m) { set_error("tp_dg_laplace_create: mesh is NULL"); return TP_ERR_INVALID_ARG; }
+  if (k < 1 || k > 7) { set_error("tp_dg_laplace_create: degree k=%d outside [1,7]", k); return TP_ERR_INVALID_ARG; }
+  if (p != TP_FP64 && p != TP_FP32 && p != TP_FP16 && p != TP_BF16) {
+    set_error("tp_dg_laplace_create: unknown precision %d", (int)p);
+    return TP_ERR_INVALID_ARG;
+  }
+  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0};
+  if (opts) o = *opts;
+  if (o.penalty != TP_PENALTY_CONFIG && o.penalty != TP_PENALTY_PAPER) {
+    set_error("tp_dg_laplace_create: unknown penalty mode %d", o.penalty);
+    return TP_ERR_INVALID_ARG;
+  }
+  if (o.kernel < TP_KERNEL_AUTO || o.kernel > TP_KERNEL_TENSOR) {
+    set_error("tp_dg_laplace_create: unknown kernel family %d", o.kernel);
+    return TP_ERR_INVALID_ARG;
+  }
+  if (o.kernel == TP_KERNEL_TENSOR) {
+    set_error("tp_dg_laplace_create: tensor-core kernel not available for this precision/degree");
+    return TP_ERR_UNSUPPORTED;
+  }
+  if (o.ec) { set_error("tp_dg_laplace_create: error correction needs the tensor-core kernel"); return TP_ERR_UNSUPPORTED; }
+  const long long ncells = (long long)m->nx * m->ny * m->nz;
+  const long long n3 = (long long)(k + 1) * (k + 1) * (k + 1);
+  if (ncells > (1LL << 62) / n3) { set_error("tp_dg_laplace_create: DoF count overflows"); return TP_ERR_INVALID_ARG; }
+  tp_op_s* op = new (std::nothrow) tp_op_s();
+  if (!op) { set_error("tp_dg_laplace_create: out of host memory"); return TP_ERR_OOM; }
+  op->mesh = *m;
+  op->k = k;
+  op->n = k + 1;
+  op->prec = p;
+  op->opts = o;
+  op->opts.kernel = TP_KERNEL_CUDA_CORE;
+  op->ncells = ncells;
+  op->ndofs = ncells * n3;
+  op->ref = make_ref1d(k);
+  const double hs[3] = {m->lx / m->nx, m->ly / m->ny, m->lz / m->nz};
+  for (int d = 0; d < 3; ++d) op->dir[d] = make_dir1d(op->ref, hs[d], o.penalty);
+  tp_status st = cuda_status(cudaGetDevice(&op->device), "cudaGetDevice");
+  if (st != TP_OK) { delete op; return st; }
+  OpConst<double> c64;
+  fill_const(c64, op);
+  st = cuda_status(cudaMalloc(&op->dconst64, sizeof(c64)), "cudaMalloc(op constants)");
+  if (st == TP_OK) st = cuda_status(cudaMemcpy(op->dconst64, &c64, sizeof(c64), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == TP_OK) {
+    if (p == TP_FP64) {
+      op->dconst = op->dconst64;
+    } else {
+      OpConst<float> c32;
+      fill_const(c32, op);
+      st = cuda_status(cudaMalloc(&op->dconst, sizeof(c32)), "cudaMalloc(op constants)");
+      if (st == TP_OK) st = cuda_status(cudaMemcpy(op->dconst, &c32, sizeof(c32), cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+  }
+  if (st != TP_OK) {
+    tp_op_destroy(op);
+    return st;
+  }
+  *out = op;
+  return TP_OK;
+}
+
+tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
+  if (!op || !info) { set_error("tp_op_get_info: NULL argument"); return TP_ERR_INVALID_ARG; }
+  info->ncells = op->ncells;
+  info->ndofs = op->ndofs;
+  info->k = op->k;
+  info->n = op->n;
+  info->precision = op->prec;
+  info->kernel = op->opts.kernel;
+  info->elem_bytes = elem_bytes(op->prec);
+  info->flops_per_dof = apply_flops_per_dof(op->n);
+  return TP_OK;
+}
+
+tp_status tp_op_destroy(tp_op op) {
+  if (!op) return TP_OK;
+  if (op->dconst && op->dconst != op->dconst64) cudaFree(op->dconst);
+  if (op->dconst64) cudaFree(op->dconst64);
+  if (op->hx) cudaFree(op->hx);
+  if (op->hy) cudaFree(op->hy);
+  delete op;
+  return TP_OK;
+}
+
+static tp_status check_vectors(tp_op op, const void* y, const void* x, const char* who) {
+  if (!op) { set_error("%s: op is NULL", who); return TP_ERR_INVALID_ARG; }
+  if (!x || !y) { set_error("%s: NULL vector", who); return TP_ERR_INVALID_ARG; }
+  if (((uintptr_t)x & 15) || ((uintptr_t)y & 15)) { set_error("%s: vectors must be 16-byte aligned", who); return TP_ERR_INVALID_ARG; }
+  const size_t bytes = (size_t)op->ndofs * elem_bytes(op->prec);
+  const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
+  if (xa < ya + bytes && ya < xa + bytes) { set_error("%s: x and y overlap", who); return TP_ERR_INVALID_ARG; }
+  return TP_OK;
+}
+
+tp_status tp_apply(tp_op op, void* y, const void* x, void* stream) {
+  tp_status st = check_vectors(op, y, x, "tp_apply");
+  if (st != TP_OK) return st;
+  return cuda_status(launch_apply_cc(op, y, x, (cudaStream_t)stream), "tp_apply launch");
+}
+
+tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream) {
+  if (!op || !x_host || !y_host) { set_error("tp_apply_host: NULL argument"); return TP_ERR_INVALID_ARG; }
+  const size_t bytes = (size_t)op->ndofs * elem_bytes(op->prec);
+  const uintptr_t xa = (uintptr_t)x_host, ya = (uintptr_t)y_host;
+  if (xa < ya + bytes && ya < xa + bytes) { set_error("tp_apply_host: x and y overlap"); return TP_ERR_INVALID_ARG; }
+  if (op->hbytes < bytes) {
+    if (op->hx) cudaFree(op->hx);
+    if (op->hy) cudaFree(op->hy);
+    op->hx = op->hy = nullptr;
+    op->hbytes = 0;
+    tp_status st = cuda_status(cudaMalloc(&op->hx, bytes), "tp_apply_host staging");
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&op->hy, bytes), "tp_apply_host staging");
+    if (st != TP_OK) return st;
+    op->hbytes = bytes;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  tp_status st = cuda_status(cudaMemcpyAsync(op->hx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host H2D");
+  if (st == TP_OK) st = cuda_status(launch_apply_cc(op, op->hy, op->hx, s), "tp_apply_host launch");
+  if (st == TP_OK) st = cuda_status(cudaMemcpyAsync(y_host, op->hy, bytes, cudaMemcpyDeviceToHost, s), "tp_apply_host D2H");
+  if (st == TP_OK) st = cuda_status(cudaStreamSynchronize(s), "tp_apply_host sync");
+  return st;
+}
+
+}  // extern "C"

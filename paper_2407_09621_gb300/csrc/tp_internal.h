@@ -1,0 +1,73 @@
+// Internal declarations of libtp (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tp.h"
+
+namespace tp {
+
+constexpr int kMaxN = 8;  // n = k + 1 <= 8 (k <= 7)
+
+// 1D reference data of the Gauss-Lobatto Lagrange basis on [0, 1] (Sec. 2).
+struct Ref1D {
+  int k = 0, n = 0;
+  std::vector<double> nodes;  // n Gauss-Lobatto points, ascending
+  std::vector<double> Mhat;   // n*n, int phi_i phi_j (row-major, [i*n + j])
+  std::vector<double> Khat;   // n*n, int phi_i' phi_j'
+  std::vector<double> d0, d1; // phi_i'(0), phi_i'(1)
+};
+
+Ref1D make_ref1d(int k);
+void gauss_legendre(int q, std::vector<double>& x, std::vector<double>& w);  // on [0, 1]
+// Lagrange basis values (rows = points) of the Gauss-Lobatto nodes at points x.
+std::vector<double> lagrange_eval(const std::vector<double>& nodes, const std::vector<double>& x);
+
+// Per-direction 1D operator data for a uniform mesh (Sec. 2.1, Eq. (9)).
+// M = h Mhat; L = interior diagonal block of the 1D SIPG stiffness
+//   Khat/h + g(v1 v1^T + v0 v0^T) - (v1 d1^T + d1 v1^T)/(2h) + (v0 d0^T + d0 v0^T)/(2h).
+struct Dir1D {
+  double h = 0, gamma = 0;
+  std::vector<double> M, L;  // n*n row-major
+};
+
+Dir1D make_dir1d(const Ref1D& r, double h, int penalty_mode);
+
+// Device-side constant block shared by all apply kernels, templated on the
+// compute type. Lives in device global memory, owned by the operator.
+template <typename T>
+struct OpConst {
+  T M[3][kMaxN * kMaxN];
+  T L[3][kMaxN * kMaxN];
+  T d0[kMaxN], d1[kMaxN];
+  T gamma[3], half_inv_h[3];
+};
+
+void set_error(const char* fmt, ...);
+tp_status cuda_status(int err, const char* what);
+
+}  // namespace tp
+
+struct tp_mesh_s {
+  int nx, ny, nz;
+  double lx, ly, lz;
+};
+
+struct tp_op_s {
+  tp_mesh_s mesh;
+  int k, n;
+  tp_precision prec;
+  tp_op_opts opts;
+  long long ncells, ndofs;
+  void* dconst = nullptr;     // OpConst<double> or OpConst<float> on the device
+  void* dconst64 = nullptr;   // OpConst<double> (always present)
+  int device = 0;
+  // host-buffer path (tp_apply_host): library-owned staging
+  void* hx = nullptr; void* hy = nullptr;
+  size_t hbytes = 0;
+  tp::Ref1D ref;
+  tp::Dir1D dir[3];
+};

@@ -1,0 +1,57 @@
+"""Host-side checks of the C ABI: the library loads, exports every function the
+header declares, and validates arguments (no GPU needed)."""
+import ctypes
+
+import pytest
+import torch
+
+from paper_2407_09621_gb300 import _lib
+
+
+def test_header_functions_are_exported():
+    names = _lib.header_functions()
+    assert "tp_apply" in names and "tp_mesh_create" in names
+    for name in names:
+        assert hasattr(_lib.lib, name), f"{name} declared in include/tp.h but not exported"
+        assert hasattr(_lib, name), f"{name} has no Python binding"
+
+
+def test_mesh_validation():
+    with pytest.raises(_lib.TPError) as e:
+        _lib.tp_mesh_create(0, 4, 4)
+    assert e.value.status == _lib.TP_ERR_INVALID_ARG
+    with pytest.raises(_lib.TPError):
+        _lib.tp_mesh_create(4, 4, 4, -1.0, 1.0, 1.0)
+    m = _lib.tp_mesh_create(3, 1, 7, 0.5, 2.0, 1.0)
+    _lib.tp_mesh_destroy(m)
+    assert _lib.lib.tp_mesh_create(None, 1, 1, 1, 1.0, 1.0, 1.0) == _lib.TP_ERR_INVALID_ARG
+
+
+def test_operator_argument_validation():
+    m = _lib.tp_mesh_create(2, 2, 2)
+    try:
+        for k in (0, 8):
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_dg_laplace_create(m, k, _lib.TP_FP64)
+            assert e.value.status == _lib.TP_ERR_INVALID_ARG
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_dg_laplace_create(m, 3, 9)
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_dg_laplace_create(m, 3, _lib.TP_FP64, penalty=5)
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
+    finally:
+        _lib.tp_mesh_destroy(m)
+    assert _lib.lib.tp_apply(None, None, None, None) == _lib.TP_ERR_INVALID_ARG
+    assert "NULL" in _lib.tp_last_error()
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU failure path")
+def test_create_without_gpu_fails_loudly():
+    m = _lib.tp_mesh_create(2, 2, 2)
+    try:
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_dg_laplace_create(m, 3, _lib.TP_FP64)
+        assert e.value.status in (_lib.TP_ERR_CUDA, _lib.TP_ERR_OOM)
+    finally:
+        _lib.tp_mesh_destroy(m)

@@ -1,0 +1,163 @@
+"""GPU parity of tp_apply against the CPU oracle (element by element).
+
+Small meshes: every entry against the assembled SIPG matrix (or its block
+form, pinned to it). Full-size meshes: sampled cells computed one by one
+from the element and face matrices, plus the rank-1 closed form of
+Eq. (9), which holds at any size. Tolerances are relative l2 errors
+(Sec. 5.2): 1e-12 FP64, 1e-5 FP32, 5e-3 FP16/BF16.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.sipg import Mesh, assemble, BlockOperator, global_1d
+from tp_synth import uniform_vector, sample_cells
+from tests.gpu_util import TOL, DTYPES, rel_l2, to_device, to_host64
+
+pytestmark = pytest.mark.gpu
+
+torch_ok = torch.cuda.is_available()
+
+
+def _gpu_apply(dims, k, prec, x64, kernel=0, penalty=0, lengths=(1.0, 1.0, 1.0)):
+    from paper_2407_09621_gb300 import DGLaplace
+    op = DGLaplace(*dims, k, prec, penalty=penalty, kernel=kernel, lengths=lengths)
+    try:
+        x = to_device(x64, prec)
+        y = torch.empty_like(x)
+        op.apply(y, x)
+        torch.cuda.synchronize()
+        return to_host64(y)
+    finally:
+        op.close()
+
+
+def test_config0_fp64_8cubed_k3_full_matrix():
+    # 8^3 cells, k = 3, x ~ U[-1,1] seed 0: every entry against the assembled matrix
+    m = Mesh(8, 8, 8)
+    A = assemble(m, 3)
+    x = uniform_vector(A.shape[0], seed=0)
+    y = _gpu_apply((8, 8, 8), 3, "fp64", x)
+    ref = A @ x
+    assert rel_l2(y, ref) < TOL["fp64"]
+    assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("k", range(1, 8))
+@pytest.mark.parametrize("dims", [(1, 1, 1), (3, 2, 5), (5, 1, 2), (2, 7, 1)])
+def test_fp64_all_degrees_ragged_meshes(k, dims):
+    m = Mesh(*dims)
+    bo = BlockOperator(m, k)
+    x = uniform_vector(m.ncells * (k + 1) ** 3, seed=k)
+    y = _gpu_apply(dims, k, "fp64", x)
+    ref = bo.apply(x)
+    assert rel_l2(y, ref) < TOL["fp64"]
+    assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pen", [0, 1])
+def test_fp64_paper_penalty_and_anisotropic_box(pen):
+    dims, k, lengths = (4, 3, 2), 2, (0.7, 1.9, 0.45)
+    m = Mesh(*dims, *lengths)
+    A = assemble(m, k, "paper" if pen else "config")
+    x = uniform_vector(A.shape[0], seed=3)
+    y = _gpu_apply(dims, k, "fp64", x, penalty=pen, lengths=lengths)
+    assert rel_l2(y, A @ x) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_low_precision_against_fp64_oracle(prec, k):
+    dims = (5, 3, 4)
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * (k + 1) ** 3, seed=10 + k)
+    y = _gpu_apply(dims, k, prec, x)
+    assert rel_l2(y, BlockOperator(m, k).apply(x)) < TOL[prec]
+
+
+def test_apply_is_deterministic_fp64():
+    x = uniform_vector(6 * 5 * 4 * 64, seed=4)
+    a = _gpu_apply((6, 5, 4), 3, "fp64", x)
+    b = _gpu_apply((6, 5, 4), 3, "fp64", x)
+    assert np.array_equal(a, b)
+
+
+def test_host_buffer_entry_point_matches_device():
+    from paper_2407_09621_gb300 import DGLaplace
+    dims, k = (4, 4, 4), 3
+    x = uniform_vector(64 * 64, seed=7)
+    op = DGLaplace(*dims, k, "fp64")
+    try:
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        op.apply_host(yh, xh)
+        yd = torch.empty(op.ndofs, dtype=torch.float64, device="cuda")
+        op.apply(yd, xh.cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(yh.numpy(), yd.cpu().numpy())
+    finally:
+        op.close()
+
+
+def test_invalid_device_arguments_rejected():
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    op = DGLaplace(2, 2, 2, 2, "fp64")
+    try:
+        x = torch.zeros(op.ndofs + 8, dtype=torch.float64, device="cuda")
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_apply(op.op, x.data_ptr() + 8, x.data_ptr(), 0)  # overlapping
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_apply(op.op, x.data_ptr() + 8, x.data_ptr() + 4, 0)  # unaligned
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
+    finally:
+        op.close()
+
+
+def _rank1_vectors(k, nc, seed):
+    """x = c (x) b (x) a and, by Eq. (9) with the global 1D factors,
+    A x = L c (x) M b (x) M a + M c (x) L b (x) M a + M c (x) M b (x) L a, cell-major order.
+    Exact for any 1D vectors, so it checks every entry at any mesh size."""
+    M, L = global_1d(k, nc)
+    rng = np.random.default_rng(seed)
+    n = k + 1
+    nodes = np.concatenate([(c + np.linspace(0, 1, n)) / nc for c in range(nc)])
+    a, b = rng.uniform(-1, 1, (2, nc * n))
+    c = np.sin(np.pi * nodes)  # one smooth factor
+    r = lambda v: v.reshape(nc, n)
+    t = lambda vz, vy, vx: np.einsum("zl,yj,xi->zyxlji", r(vz), r(vy), r(vx), optimize=True).reshape(-1)
+    x = t(c, b, a)
+    y = t(L @ c, M @ b, M @ a) + t(M @ c, L @ b, M @ a) + t(M @ c, M @ b, L @ a)
+    return x, y
+
+
+@pytest.mark.parametrize("k,nc", [(3, 128), (7, 64)])
+def test_config1_full_size_fp64_sampled_and_rank1(k, nc):
+    # 134,217,728 DoFs: sampled cells against the oracle's element/face matrices
+    dims = (nc, nc, nc)
+    m = Mesh(*dims)
+    ndofs = m.ncells * (k + 1) ** 3
+    x = uniform_vector(ndofs, seed=0)
+    y = _gpu_apply(dims, k, "fp64", x)
+    cells = sample_cells(m.ncells, 1024 if k == 7 else 4096, seed=1, nx=nc, ny=nc, nz=nc)
+    ref = BlockOperator(m, k).rows(x, cells)
+    got = y.reshape(m.ncells, -1)[cells]
+    assert rel_l2(got, ref) < TOL["fp64"]
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    del x, y
+    # rank-1 closed form of Eq. (9) on every entry
+    xs, ys = _rank1_vectors(k, nc, seed=17)
+    y2 = _gpu_apply(dims, k, "fp64", xs)
+    assert rel_l2(y2, ys) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("k,nc", [(2, 107), (3, 80), (4, 64), (5, 54), (7, 40)])
+def test_config2_precision_sweep_sampled(prec, k, nc):
+    dims = (nc, nc, nc)
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * (k + 1) ** 3, seed=0)
+    y = _gpu_apply(dims, k, prec, x)
+    cells = sample_cells(m.ncells, 512, seed=2, nx=nc, ny=nc, nz=nc)
+    ref = BlockOperator(m, k).rows(x, cells)
+    assert rel_l2(y.reshape(m.ncells, -1)[cells], ref) < TOL[prec]
