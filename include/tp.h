@@ -105,6 +105,106 @@ tp_status tp_apply(tp_op op, void* y, const void* x, void* stream);
  * until tp_op_destroy. Errors as tp_apply, plus TP_ERR_OOM. */
 tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream);
 
+
+/* ------------------------------------------------------------------ multigrid
+ * Geometric multigrid V-cycle of Algorithm 2 (Sec. 7.1) on the operator's box:
+ * levels from uniform coarsening by 2 in every direction (while all cell
+ * counts are even and one exceeds coarse_cells), the same degree and penalty
+ * on every level, the operator rediscretized with that level's h.
+ *  - smoother S_l: `degree` steps of Chebyshev iteration on D^{-1} A_l,
+ *    D = diag(A_l), eigenvalue interval [lmax/ratio, lmax] (the paper's
+ *    vertex-patch Schwarz smoother is replaced by Chebyshev-Jacobi);
+ *  - restriction I_down = P^T, prolongation I_up = P, the exact embedding of
+ *    the coarse DG space into the fine one;
+ *  - coarse solve A_0^{-1}: exact, in FP64, by fast diagonalization.
+ * Vectors of the V-cycle have the multigrid precision (TP_FP64 or TP_FP32;
+ * the latter is the low-precision preconditioner of Sec. 7.1). Level 0 is the
+ * coarsest, level `levels-1` the finest (the operator given at creation). */
+#define TP_MAX_LEVELS 16
+
+typedef struct tp_mg_s* tp_mg;
+
+typedef struct {
+  int degree;        /* Chebyshev degree per smoothing step (default 3) */
+  double ratio;      /* lmax / lmin of the Chebyshev interval (default 15) */
+  double safety;     /* factor applied to the estimated lmax (default 1.1) */
+  double lmax;       /* > 0: use this bound on every level instead of estimating it */
+  int coarse_cells;  /* stop coarsening once no direction has more cells (default 4) */
+  int precision;     /* TP_FP64 or TP_FP32 (default) */
+  int power_iters;   /* power iterations for the lmax estimate (default 20) */
+} tp_mg_opts;
+
+typedef struct {
+  int levels;
+  int precision;
+  int cells[TP_MAX_LEVELS][3];
+  long long ndofs[TP_MAX_LEVELS];
+  double lmax[TP_MAX_LEVELS];  /* smoother bound used on each level (0 on level 0) */
+} tp_mg_info_t;
+
+/* Builds the hierarchy below `finest` (which must outlive the hierarchy; its
+ * mesh, degree and penalty are used, not its precision). opts may be NULL.
+ * Allocates the level operators, vectors and scratch (owned until
+ * tp_mg_destroy) and, unless opts->lmax > 0, estimates lmax(D^{-1}A_l) per
+ * level by power iteration on the GPU (synchronizes the device).
+ * Errors: TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_NONFINITE. */
+tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts);
+tp_status tp_mg_get_info(tp_mg mg, tp_mg_info_t* info);
+/* Level operator (owned by the hierarchy; valid until tp_mg_destroy). */
+tp_status tp_mg_level_op(tp_mg mg, int level, tp_op* op);
+tp_status tp_mg_destroy(tp_mg mg);
+
+/* One V-cycle (Algorithm 2) on the finest level: x <- Vcycle(A, x, b).
+ * x (in/out, initial guess) and b are DEVICE vectors of the multigrid
+ * precision and the finest level's size, 16-byte aligned. Asynchronous on
+ * `stream`; uses the hierarchy's vectors, so calls on one hierarchy must not
+ * overlap. */
+tp_status tp_vcycle(tp_mg mg, void* x, const void* b, void* stream);
+/* The steps of Algorithm 2 one at a time (same vector rules, level sizes):
+ * smoothing x <- S_l(x, b) on level l >= 1; coarse = P^T fine (level l >= 1 is
+ * the fine side); fine += P coarse; x = A_0^{-1} b on level 0. */
+tp_status tp_mg_smooth(tp_mg mg, int level, void* x, const void* b, void* stream);
+tp_status tp_mg_restrict(tp_mg mg, int level, void* coarse, const void* fine, void* stream);
+tp_status tp_mg_prolongate_add(tp_mg mg, int level, void* fine, const void* coarse, void* stream);
+tp_status tp_mg_coarse_solve(tp_mg mg, void* x, const void* b, void* stream);
+
+/* ------------------------------------------------------------------ FGMRES
+ * Flexible GMRES (Saad 1993) with right preconditioning, restarted every
+ * `restart` iterations, in FP64 on the GPU (Sec. 7.1): Arnoldi vectors,
+ * Gram-Schmidt orthogonalization (classical, with one re-orthogonalization
+ * pass), the operator applications w = A z_j and the true residual at each
+ * restart are FP64; the preconditioner is one V-cycle of `mg` in its own
+ * precision with zero initial guess (the input is converted, scaled by
+ * sqrt(ndofs), and the output converted back). Stops when the Arnoldi
+ * residual norm drops below rtol * ||b - A x0||. */
+typedef struct tp_solver_s* tp_solver;
+
+typedef struct {
+  int iterations;          /* preconditioned Arnoldi steps taken */
+  int restarts;
+  int converged;           /* 1 if the tolerance was met */
+  double rel_residual;     /* final Arnoldi estimate ||r|| / ||r0|| */
+  double true_rel_residual;/* ||b - A x|| / ||b - A x0|| recomputed in FP64 at the end */
+  const double* history;   /* host array of relative residual estimates, one per iteration + 1;
+                              owned by the solver, valid until the next solve or destroy */
+  int history_len;
+} tp_solve_info;
+
+/* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's
+ * mesh (NULL: no preconditioner). Allocates (restart+1)+restart+1 FP64
+ * vectors of A's size plus two vectors of mg's precision. Errors:
+ * TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA. */
+tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart);
+/* Solves A x = b. x (in: initial guess, out: solution) and b are DEVICE FP64
+ * vectors, 16-byte aligned. Runs on `stream` and synchronizes it (the
+ * Arnoldi scalars are read on the host every iteration). Returns TP_OK when
+ * converged, TP_ERR_NOT_CONVERGED after maxit iterations (x holds the last
+ * iterate), TP_ERR_NONFINITE if a NaN/Inf appears in the Arnoldi process.
+ * `info` (may be NULL) is filled in every case. */
+tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, double rtol, int maxit, tp_solve_info* info,
+                          void* stream);
+tp_status tp_solver_destroy(tp_solver s);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* tp_last_error(void);
 

@@ -125,3 +125,115 @@ def tp_bench_fma_peak(precision, stream=0):
     out = ctypes.c_double()
     _check(lib.tp_bench_fma_peak(precision, ctypes.byref(out), _vp(stream)))
     return out.value
+
+
+# ---------------------------------------------------------------- multigrid / FGMRES
+TP_MAX_LEVELS = 16
+
+
+class tp_mg_opts(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int), ("ratio", ctypes.c_double), ("safety", ctypes.c_double),
+                ("lmax", ctypes.c_double), ("coarse_cells", ctypes.c_int), ("precision", ctypes.c_int),
+                ("power_iters", ctypes.c_int)]
+
+
+class tp_mg_info_t(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("precision", ctypes.c_int),
+                ("cells", (ctypes.c_int * 3) * TP_MAX_LEVELS), ("ndofs", ctypes.c_longlong * TP_MAX_LEVELS),
+                ("lmax", ctypes.c_double * TP_MAX_LEVELS)]
+
+
+class tp_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int)]
+
+
+_sig2 = {
+    "tp_mg_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, ctypes.POINTER(tp_mg_opts)]),
+    "tp_mg_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(tp_mg_info_t)]),
+    "tp_mg_level_op": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "tp_mg_destroy": (ctypes.c_int, [_vp]),
+    "tp_vcycle": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "tp_mg_smooth": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "tp_mg_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "tp_mg_prolongate_add": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "tp_mg_coarse_solve": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "tp_fgmres_create": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _vp, ctypes.c_int]),
+    "tp_fgmres_solve": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(tp_solve_info), _vp]),
+    "tp_solver_destroy": (ctypes.c_int, [_vp]),
+}
+for _name, (_res, _args) in _sig2.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def tp_mg_create(op, degree=3, ratio=15.0, safety=1.1, lmax=0.0, coarse_cells=4, precision=TP_FP32,
+                 power_iters=20):
+    h = _vp()
+    o = tp_mg_opts(degree, ratio, safety, lmax, coarse_cells, precision, power_iters)
+    _check(lib.tp_mg_create(ctypes.byref(h), op, ctypes.byref(o)))
+    return h
+
+
+def tp_mg_get_info(mg):
+    info = tp_mg_info_t()
+    _check(lib.tp_mg_get_info(mg, ctypes.byref(info)))
+    L = info.levels
+    return {"levels": L, "precision": info.precision,
+            "cells": [tuple(info.cells[l]) for l in range(L)], "ndofs": [info.ndofs[l] for l in range(L)],
+            "lmax": [info.lmax[l] for l in range(L)]}
+
+
+def tp_mg_level_op(mg, level):
+    h = _vp()
+    _check(lib.tp_mg_level_op(mg, level, ctypes.byref(h)))
+    return h
+
+
+def tp_mg_destroy(mg):
+    _check(lib.tp_mg_destroy(mg))
+
+
+def tp_vcycle(mg, x_ptr, b_ptr, stream=0):
+    _check(lib.tp_vcycle(mg, _vp(x_ptr), _vp(b_ptr), _vp(stream)))
+
+
+def tp_mg_smooth(mg, level, x_ptr, b_ptr, stream=0):
+    _check(lib.tp_mg_smooth(mg, level, _vp(x_ptr), _vp(b_ptr), _vp(stream)))
+
+
+def tp_mg_restrict(mg, level, coarse_ptr, fine_ptr, stream=0):
+    _check(lib.tp_mg_restrict(mg, level, _vp(coarse_ptr), _vp(fine_ptr), _vp(stream)))
+
+
+def tp_mg_prolongate_add(mg, level, fine_ptr, coarse_ptr, stream=0):
+    _check(lib.tp_mg_prolongate_add(mg, level, _vp(fine_ptr), _vp(coarse_ptr), _vp(stream)))
+
+
+def tp_mg_coarse_solve(mg, x_ptr, b_ptr, stream=0):
+    _check(lib.tp_mg_coarse_solve(mg, _vp(x_ptr), _vp(b_ptr), _vp(stream)))
+
+
+def tp_fgmres_create(op, mg=None, restart=30):
+    h = _vp()
+    _check(lib.tp_fgmres_create(ctypes.byref(h), op, mg, restart))
+    return h
+
+
+def tp_fgmres_solve(solver, x_ptr, b_ptr, rtol=1e-10, maxit=200, stream=0, raise_on_error=True):
+    """Returns (status, info dict); raises TPError on failure unless raise_on_error is False."""
+    info = tp_solve_info()
+    st = lib.tp_fgmres_solve(solver, _vp(x_ptr), _vp(b_ptr), rtol, maxit, ctypes.byref(info), _vp(stream))
+    d = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
+         "rel_residual": info.rel_residual, "true_rel_residual": info.true_rel_residual,
+         "history": [info.history[i] for i in range(info.history_len)] if info.history else []}
+    if st != TP_OK and raise_on_error:
+        raise TPError(st, lib.tp_last_error().decode())
+    return st, d
+
+
+def tp_solver_destroy(solver):
+    _check(lib.tp_solver_destroy(solver))

@@ -15,9 +15,13 @@
 // (alpha, beta) that are expanded along the normal after the tangential
 // masses of the directions already contracted have been applied to them.
 //
-// Thread layout (App. A's two-dimensional block): one thread per (i, j)
-// column of a cell, CPB cells per block; the z-contraction runs in registers.
-// TS = storage type of the vectors, TC = arithmetic type.
+// Work layout: n^2 threads per cell, CPB cells per block. In each
+// contraction phase a thread owns one line of the cell along the contracted
+// direction (x, then y, then z), so every 1D-matrix coefficient is the same
+// for the whole warp: the matrices are a __grid_constant__ kernel parameter
+// and enter the FMAs as constant-bank operands. Lines move between phases
+// through shared memory. TS = storage type of the vectors, TC = arithmetic
+// type.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -27,197 +31,208 @@
 namespace tp {
 
 template <typename TS, typename TC>
-__device__ __forceinline__ TC load_as(const TS* p) { return static_cast<TC>(*p); }
+__device__ __forceinline__ TC load_as(const TS* p) { return static_cast<TC>(__ldg(p)); }
 template <>
-__device__ __forceinline__ float load_as<__half, float>(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float load_as<__half, float>(const __half* p) { return __half2float(__ldg(p)); }
 template <>
-__device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
 
 template <typename TS, typename TC>
 __device__ __forceinline__ void store_as(TS* p, TC v) { *p = static_cast<TS>(v); }
 template <>
 __device__ __forceinline__ void store_as<__half, float>(__half* p, float v) { *p = __float2half_rn(v); }
 template <>
-__device__ __forceinline__ void store_as<__nv_bfloat16, float>(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_as<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
 
 template <int N>
 __host__ __device__ constexpr int cc_cells_per_block() { return (128 / (N * N)) > 0 ? 128 / (N * N) : 1; }
 
-// face index f: 0 = x-, 1 = x+, 2 = y-, 3 = y+, 4 = z-, 5 = z+ ; array 2f = alpha, 2f+1 = beta
+template <typename TC, int N>
+__host__ __device__ constexpr size_t cc_smem_bytes() {
+  return sizeof(TC) * cc_cells_per_block<N>() * (4 * N * N * N + 20 * N * N);
+}
+
+// Face f: 0 = x-, 1 = x+, 2 = y-, 3 = y+, 4 = z-, 5 = z+; face arrays 2f = alpha, 2f+1 = beta.
+// Face-point order inside an array (slow, fast): x faces (l, j), y faces (l, i), z faces (j, i).
 template <typename TS, typename TC, int N>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N>())
-apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const OpConst<TC>* __restrict__ cst,
+apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ OpConst<TC> P,
                 int nx, int ny, int nz, long long ncells) {
   constexpr int CPB = cc_cells_per_block<N>();
   constexpr int N2 = N * N, N3 = N * N * N;
-  __shared__ TC sM[3][N2], sL[3][N2], sd0[N], sd1[N], sg[3], shh[3];
-  __shared__ TC sU[CPB][N3], sB[CPB][N3];
-  __shared__ TC sF[CPB][12][N2], sT[CPB][12][N2];
-
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
-  for (int e = tid; e < 3 * N2; e += blockDim.x) {
-    const int d = e / N2, r = e % N2, ii = r / N, jj = r % N;
-    sM[d][r] = cst->M[d][ii * kMaxN + jj];
-    sL[d][r] = cst->L[d][ii * kMaxN + jj];
-  }
-  if (tid < N) { sd0[tid] = cst->d0[tid]; sd1[tid] = cst->d1[tid]; }
-  if (tid < 3) { sg[tid] = cst->gamma[tid]; shh[tid] = cst->half_inv_h[tid]; }
+  const int cs = tid / N2, t = tid % N2;
+  TC* sU = base + cs * N3;                   // u, later c1
+  TC* sA = base + (CPB + cs) * N3;           // a = M_x u
+  TC* sB = base + (2 * CPB + cs) * N3;       // b = L_x u + x faces
+  TC* sC = base + (3 * CPB + cs) * N3;       // c2 = M_y a
+  TC* sF = base + 4 * CPB * N3 + cs * 12 * N2;                // raw face arrays (12), later z arrays final
+  TC* sT = base + 4 * CPB * N3 + CPB * 12 * N2 + cs * 8 * N2;  // y/z face arrays after M_x
 
-  const int cs = tid / N2, t = tid % N2, i = t % N, j = t / N;
   const long long cell = (long long)blockIdx.x * CPB + cs;
   const bool valid = cell < ncells;
   const int cx = valid ? (int)(cell % nx) : 0;
   const int cy = valid ? (int)((cell / nx) % ny) : 0;
   const int cz = valid ? (int)(cell / ((long long)nx * ny)) : 0;
-  const TS* xc = x + cell * N3;
-  __syncthreads();
+  const TS* xc = x + (valid ? cell : 0) * N3;
 
-  // ---- gather: own column into shared memory
-  TC u[N];
+  // ---- gather u (coalesced) and the raw traces of the six faces at face point t = (p, q)
 #pragma unroll
-  for (int l = 0; l < N; ++l) {
-    u[l] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
-    sU[cs][l * N2 + t] = u[l];
-  }
-
-  // ---- face traces: alpha/beta of the six faces (raw, before tangential masses)
-  if (valid) {
-    const long long sx = 1, sy = nx, sz = (long long)nx * ny;
-    const int co[3] = {cx, cy, cz};
-    const int nc[3] = {nx, ny, nz};
-    const long long st[3] = {sx, sy, sz};
+  for (int l = 0; l < N; ++l) sU[l * N2 + t] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
+  {
+    const int p = t / N, q = t % N;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      // line along direction d handled by this thread, and its slot in the face array
-      long long base;  // offset of node 0 of the line inside a cell
-      int step;        // stride of the line inside a cell
-      int slot;
-      if (d == 0) { base = (long long)i * N2 + j * N; step = 1; slot = i * N + j; }       // line (l=i, j), array [l][j]
-      else if (d == 1) { base = (long long)j * N2 + i; step = N; slot = j * N + i; }      // line (l=j, i), array [l][i]
-      else { base = (long long)j * N + i; step = N2; slot = j * N + i; }                  // line (j, i), array [j][i]
-      const TC g = sg[d], hh = shh[d];
+      const int co = d == 0 ? cx : (d == 1 ? cy : cz);
+      const int ncd = d == 0 ? nx : (d == 1 ? ny : nz);
+      const long long std_ = d == 0 ? 1LL : (d == 1 ? (long long)nx : (long long)nx * ny);
+      const int off = d == 0 ? p * N2 + q * N : (d == 1 ? p * N2 + q : p * N + q);
+      const int step = d == 0 ? 1 : (d == 1 ? N : N2);
+      const TC g = P.gamma[d], hh = P.half_inv_h[d];
 #pragma unroll
       for (int side = 0; side < 2; ++side) {
-        const bool nb = side ? (co[d] < nc[d] - 1) : (co[d] > 0);
-        const TS* src = nb ? (xc + (side ? st[d] : -st[d]) * N3) : xc;
+        const bool nb = valid && (side ? (co < ncd - 1) : (co > 0));
+        const TS* src = (nb ? xc + (side ? std_ : -std_) * N3 : xc) + off;
         TC w[N];
 #pragma unroll
-        for (int m = 0; m < N; ++m) w[m] = load_as<TS, TC>(src + base + m * step);
-        TC alpha, beta;
-        if (side == 1) {
-          if (nb) {
-            TC sd = 0;
+        for (int m = 0; m < N; ++m) w[m] = valid ? load_as<TS, TC>(src + m * step) : TC(0);
+        // value trace s and derivative trace sd of the line at the face
+        const TC s = (side == nb) ? w[0] : w[N - 1];
+        TC sd = TC(0);
+        if (side == nb) {
 #pragma unroll
-            for (int m = 0; m < N; ++m) sd += sd0[m] * w[m];
-            alpha = -g * w[0] - hh * sd;
-            beta = hh * w[0];
-          } else {
-            TC sd = 0;
-#pragma unroll
-            for (int m = 0; m < N; ++m) sd += sd1[m] * w[m];
-            alpha = -hh * sd;
-            beta = -hh * w[N - 1];
-          }
+          for (int m = 0; m < N; ++m) sd = fma(P.d0[m], w[m], sd);
         } else {
-          if (nb) {
-            TC sd = 0;
 #pragma unroll
-            for (int m = 0; m < N; ++m) sd += sd1[m] * w[m];
-            alpha = -g * w[N - 1] + hh * sd;
-            beta = -hh * w[N - 1];
-          } else {
-            TC sd = 0;
-#pragma unroll
-            for (int m = 0; m < N; ++m) sd += sd0[m] * w[m];
-            alpha = hh * sd;
-            beta = hh * w[0];
-          }
+          for (int m = 0; m < N; ++m) sd = fma(P.d1[m], w[m], sd);
         }
-        const int f = 2 * d + side;
-        sF[cs][2 * f][slot] = alpha;
-        sF[cs][2 * f + 1][slot] = beta;
+        TC alpha, beta;
+        if (nb) {
+          alpha = side ? fma(-g, s, -hh * sd) : fma(-g, s, hh * sd);
+          beta = side ? hh * s : -hh * s;
+        } else {
+          alpha = side ? -hh * sd : hh * sd;
+          beta = side ? -hh * s : hh * s;
+        }
+        sF[(4 * d + 2 * side) * N2 + t] = alpha;
+        sF[(4 * d + 2 * side + 1) * N2 + t] = beta;
       }
     }
-  } else {
-#pragma unroll
-    for (int a = 0; a < 12; ++a) sF[cs][a][t] = TC(0);
   }
   __syncthreads();
 
-  // ---- x contraction: a = M_x u, b = L_x u + x-face terms
-  TC a[N], b[N];
+  // ---- M_x along the fast index of the y- and z-face arrays (8 arrays x N rows)
+  for (int w = t; w < 8 * N; w += N2) {
+    const int q = w / N, r = w % N;
+    TC row[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) {
-    TC sa = 0, sb = 0;
+    for (int m = 0; m < N; ++m) row[m] = sF[(4 + q) * N2 + r * N + m];
 #pragma unroll
-    for (int m = 0; m < N; ++m) {
-      const TC um = sU[cs][l * N2 + j * N + m];
-      sa += sM[0][i * N + m] * um;
-      sb += sL[0][i * N + m] * um;
+    for (int i = 0; i < N; ++i) {
+      TC s = TC(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) s = fma(P.M[0][i * kMaxN + m], row[m], s);
+      sT[q * N2 + r * N + i] = s;
     }
-    const int fs = l * N + j;
-    sb += sd1[i] * sF[cs][3][fs] + sd0[i] * sF[cs][1][fs];
-    if (i == N - 1) sb += sF[cs][2][fs];
-    if (i == 0) sb += sF[cs][0][fs];
-    a[l] = sa;
-    b[l] = sb;
-  }
-  // tangential mass M_x on the y-face arrays (index [l][i], l = j here) and on the z-face arrays ([j][i])
-#pragma unroll
-  for (int q = 4; q < 12; ++q) {
-    TC s = 0;
-#pragma unroll
-    for (int m = 0; m < N; ++m) s += sM[0][i * N + m] * sF[cs][q][j * N + m];
-    sT[cs][q][j * N + i] = s;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int l = 0; l < N; ++l) {
-    sU[cs][l * N2 + t] = a[l];
-    sB[cs][l * N2 + t] = b[l];
-  }
-  // z-face arrays: second tangential mass M_y (along j)
-#pragma unroll
-  for (int q = 8; q < 12; ++q) {
-    TC s = 0;
-#pragma unroll
-    for (int p = 0; p < N; ++p) s += sM[1][j * N + p] * sT[cs][q][p * N + i];
-    sF[cs][q][t] = s;
   }
   __syncthreads();
 
-  // ---- y contraction: c1 = M_y b + L_y a + y-face terms, c2 = M_y a
-  TC c1[N], c2[N];
+  // ---- x contraction on x-line (l, j): a = M_x u, b = L_x u + x-face terms
+  {
+    const int l = t / N, j = t % N;
+    TC u[N];
 #pragma unroll
-  for (int l = 0; l < N; ++l) {
-    TC s1 = 0, s2 = 0;
+    for (int m = 0; m < N; ++m) u[m] = sU[l * N2 + j * N + m];
+    const TC am = sF[0 * N2 + t], bm = sF[1 * N2 + t], ap = sF[2 * N2 + t], bp = sF[3 * N2 + t];
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-      const TC ap = sU[cs][l * N2 + p * N + i];
-      const TC bp = sB[cs][l * N2 + p * N + i];
-      s1 += sM[1][j * N + p] * bp + sL[1][j * N + p] * ap;
-      s2 += sM[1][j * N + p] * ap;
+    for (int i = 0; i < N; ++i) {
+      TC sa = TC(0), sb = TC(0);
+#pragma unroll
+      for (int m = 0; m < N; ++m) {
+        sa = fma(P.M[0][i * kMaxN + m], u[m], sa);
+        sb = fma(P.L[0][i * kMaxN + m], u[m], sb);
+      }
+      sb = fma(P.d1[i], bp, sb);
+      sb = fma(P.d0[i], bm, sb);
+      if (i == N - 1) sb += ap;
+      if (i == 0) sb += am;
+      sA[l * N2 + j * N + i] = sa;
+      sB[l * N2 + j * N + i] = sb;
     }
-    const int fs = l * N + i;
-    s1 += sd1[j] * sT[cs][7][fs] + sd0[j] * sT[cs][5][fs];
-    if (j == N - 1) s1 += sT[cs][6][fs];
-    if (j == 0) s1 += sT[cs][4][fs];
-    c1[l] = s1;
-    c2[l] = s2;
   }
+  // ---- M_y along the slow index of the z-face arrays (4 arrays x N columns)
+  for (int w = t; w < 4 * N; w += N2) {
+    const int q = w / N, i = w % N;
+    TC col[N];
+#pragma unroll
+    for (int pp = 0; pp < N; ++pp) col[pp] = sT[(4 + q) * N2 + pp * N + i];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      TC s = TC(0);
+#pragma unroll
+      for (int pp = 0; pp < N; ++pp) s = fma(P.M[1][j * kMaxN + pp], col[pp], s);
+      sF[(8 + q) * N2 + j * N + i] = s;
+    }
+  }
+  __syncthreads();
 
-  // ---- z contraction in registers: v = M_z c1 + L_z c2 + z-face terms; scatter
+  // ---- y contraction on y-line (l, i): c1 = M_y b + L_y a + y-face terms, c2 = M_y a
+  {
+    const int l = t / N, i = t % N;
+    TC a[N], b[N];
+#pragma unroll
+    for (int pp = 0; pp < N; ++pp) {
+      a[pp] = sA[l * N2 + pp * N + i];
+      b[pp] = sB[l * N2 + pp * N + i];
+    }
+    const TC am = sT[0 * N2 + t], bm = sT[1 * N2 + t], ap = sT[2 * N2 + t], bp = sT[3 * N2 + t];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+      TC s1 = TC(0), s2 = TC(0);
+#pragma unroll
+      for (int pp = 0; pp < N; ++pp) {
+        s1 = fma(P.M[1][j * kMaxN + pp], b[pp], s1);
+        s1 = fma(P.L[1][j * kMaxN + pp], a[pp], s1);
+        s2 = fma(P.M[1][j * kMaxN + pp], a[pp], s2);
+      }
+      s1 = fma(P.d1[j], bp, s1);
+      s1 = fma(P.d0[j], bm, s1);
+      if (j == N - 1) s1 += ap;
+      if (j == 0) s1 += am;
+      sU[l * N2 + j * N + i] = s1;
+      sC[l * N2 + j * N + i] = s2;
+    }
+  }
+  __syncthreads();
+
+  // ---- z contraction on z-line (j, i) = t: v = M_z c1 + L_z c2 + z-face terms; scatter
   if (valid) {
+    TC c1[N], c2[N];
+#pragma unroll
+    for (int pp = 0; pp < N; ++pp) {
+      c1[pp] = sU[pp * N2 + t];
+      c2[pp] = sC[pp * N2 + t];
+    }
+    const TC am = sF[8 * N2 + t], bm = sF[9 * N2 + t], ap = sF[10 * N2 + t], bp = sF[11 * N2 + t];
     TS* yc = y + cell * N3;
-    const TC azp = sF[cs][10][t], bzp = sF[cs][11][t], azm = sF[cs][8][t], bzm = sF[cs][9][t];
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      TC s = 0;
+      TC s = TC(0);
 #pragma unroll
-      for (int p = 0; p < N; ++p) s += sM[2][l * N + p] * c1[p] + sL[2][l * N + p] * c2[p];
-      s += sd1[l] * bzp + sd0[l] * bzm;
-      if (l == N - 1) s += azp;
-      if (l == 0) s += azm;
+      for (int pp = 0; pp < N; ++pp) {
+        s = fma(P.M[2][l * kMaxN + pp], c1[pp], s);
+        s = fma(P.L[2][l * kMaxN + pp], c2[pp], s);
+      }
+      s = fma(P.d1[l], bp, s);
+      s = fma(P.d0[l], bm, s);
+      if (l == N - 1) s += ap;
+      if (l == 0) s += am;
       store_as<TS, TC>(yc + l * N2 + t, s);
     }
   }
@@ -226,12 +241,44 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const OpConst<TC>*
 template <typename TS, typename TC, int N>
 static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
   constexpr int CPB = cc_cells_per_block<N>();
+  constexpr size_t smem = cc_smem_bytes<TC, N>();
   const long long blocks = (op->ncells + CPB - 1) / CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  apply_cc_kernel<TS, TC, N><<<(unsigned)blocks, N * N * CPB, 0, s>>>(
-      static_cast<const TS*>(x), static_cast<TS*>(y), static_cast<const OpConst<TC>*>(op->dconst),
-      op->mesh.nx, op->mesh.ny, op->mesh.nz, op->ncells);
+  const OpConst<TC>& P = *static_cast<const OpConst<TC>*>(op->hconst(sizeof(TC)));
+  apply_cc_kernel<TS, TC, N><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
+      static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, op->ncells);
   return cudaGetLastError();
+}
+
+template <typename TS, typename TC, int N>
+static cudaError_t prepare_cc_n() {
+  return cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cc_smem_bytes<TC, N>());
+}
+
+template <typename TS, typename TC>
+static cudaError_t prepare_cc_t(int n) {
+  switch (n) {
+    case 2: return prepare_cc_n<TS, TC, 2>();
+    case 3: return prepare_cc_n<TS, TC, 3>();
+    case 4: return prepare_cc_n<TS, TC, 4>();
+    case 5: return prepare_cc_n<TS, TC, 5>();
+    case 6: return prepare_cc_n<TS, TC, 6>();
+    case 7: return prepare_cc_n<TS, TC, 7>();
+    case 8: return prepare_cc_n<TS, TC, 8>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Sets the dynamic shared-memory limit of the kernel instantiation on the current device.
+cudaError_t prepare_apply_cc(const tp_op_s* op) {
+  switch (op->prec) {
+    case TP_FP64: return prepare_cc_t<double, double>(op->n);
+    case TP_FP32: return prepare_cc_t<float, float>(op->n);
+    case TP_FP16: return prepare_cc_t<__half, float>(op->n);
+    case TP_BF16: return prepare_cc_t<__nv_bfloat16, float>(op->n);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <typename TS, typename TC>

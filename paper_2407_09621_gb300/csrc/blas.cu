@@ -1,0 +1,165 @@
+// Vector kernels of the Krylov and multigrid drivers: (multi-)dot products,
+// (multi-)axpy, scaling and precision conversion. Dot products accumulate in
+// FP64 and reduce deterministically: one partial per block written to a
+// scratch array (fixed grid), then one block sums the partials in a fixed
+// order, so repeated runs give bit-identical results.
+#include <cuda_runtime.h>
+
+#include "tp_internal.h"
+#include "tp_vec.h"
+
+namespace tp {
+
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+// partial[q * gridDim.x + blockIdx.x] = sum over this block's grid-stride slice of w * v_q
+template <typename T, int Q>
+__global__ void __launch_bounds__(kRedThreads) multi_dot_partial(long long n, const T* __restrict__ w,
+                                                                  MultiPtr<T> v, int nq, double* __restrict__ partial) {
+  __shared__ double red[Q][kRedThreads / 32];
+  double acc[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wi = to_d(w[i]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q < nq) acc[q] = fma(wi, to_d(v.p[q][i]), acc[q]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    double s = acc[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[q][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < Q && (int)threadIdx.x < nq) {
+    double s = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) s += red[threadIdx.x][k];
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void reduce_partials(const double* __restrict__ partial, int nblocks, int nq, double* __restrict__ out) {
+  __shared__ double red[kRedThreads / 32];
+  for (int q = 0; q < nq; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(size_t)q * nblocks + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += red[k];
+      out[q] = t;
+    }
+    __syncthreads();
+  }
+}
+
+int dot_blocks(long long n) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  long long want = (n + kRedThreads - 1) / kRedThreads;
+  long long cap = (long long)sms * 8;
+  return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <typename T>
+cudaError_t multi_dot(long long n, const T* w, const T* const* v, int nq, double* partial, double* out,
+                      cudaStream_t s) {
+  const int blocks = dot_blocks(n);
+  for (int q0 = 0; q0 < nq; q0 += kMaxMulti) {
+    const int m = nq - q0 < kMaxMulti ? nq - q0 : kMaxMulti;
+    MultiPtr<T> mp;
+    for (int q = 0; q < m; ++q) mp.p[q] = v[q0 + q];
+    if (m <= 1)
+      multi_dot_partial<T, 1><<<blocks, kRedThreads, 0, s>>>(n, w, mp, m, partial);
+    else if (m <= 4)
+      multi_dot_partial<T, 4><<<blocks, kRedThreads, 0, s>>>(n, w, mp, m, partial);
+    else if (m <= 8)
+      multi_dot_partial<T, 8><<<blocks, kRedThreads, 0, s>>>(n, w, mp, m, partial);
+    else
+      multi_dot_partial<T, kMaxMulti><<<blocks, kRedThreads, 0, s>>>(n, w, mp, m, partial);
+    reduce_partials<<<1, kRedThreads, 0, s>>>(partial, blocks, m, out + q0);
+  }
+  return cudaGetLastError();
+}
+
+// w = beta * w + sum_q c[q] * v_q   (c on the host, passed by value). w may be one of the v_q:
+// every entry is read and written by the same thread.
+template <typename T, int Q>
+__global__ void multi_axpy_kernel(long long n, T* w, double beta, MultiPtr<T> v, MultiCoef c, int nq) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double acc = beta == 0.0 ? 0.0 : beta * to_d(w[i]);
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q < nq) acc = fma(c.c[q], to_d(v.p[q][i]), acc);
+    w[i] = (T)acc;
+  }
+}
+
+int stream_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  const long long cap = 152LL * 16;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T>
+cudaError_t multi_axpy(long long n, T* w, double beta, const T* const* v, const double* c, int nq, cudaStream_t s) {
+  const int blocks = stream_blocks(n);
+  if (nq == 0) {
+    MultiPtr<T> mp{};
+    MultiCoef mc{};
+    multi_axpy_kernel<T, 1><<<blocks, 256, 0, s>>>(n, w, beta, mp, mc, 0);
+    return cudaGetLastError();
+  }
+  for (int q0 = 0; q0 < nq; q0 += kMaxMulti) {
+    const int m = nq - q0 < kMaxMulti ? nq - q0 : kMaxMulti;
+    MultiPtr<T> mp;
+    MultiCoef mc;
+    for (int q = 0; q < m; ++q) { mp.p[q] = v[q0 + q]; mc.c[q] = c[q0 + q]; }
+    const double b = q0 == 0 ? beta : 1.0;
+    if (m <= 1)
+      multi_axpy_kernel<T, 1><<<blocks, 256, 0, s>>>(n, w, b, mp, mc, m);
+    else if (m <= 4)
+      multi_axpy_kernel<T, 4><<<blocks, 256, 0, s>>>(n, w, b, mp, mc, m);
+    else if (m <= 8)
+      multi_axpy_kernel<T, 8><<<blocks, 256, 0, s>>>(n, w, b, mp, mc, m);
+    else
+      multi_axpy_kernel<T, kMaxMulti><<<blocks, 256, 0, s>>>(n, w, b, mp, mc, m);
+  }
+  return cudaGetLastError();
+}
+
+template <typename TO, typename TI>
+__global__ void convert_kernel(long long n, TO* __restrict__ out, const TI* __restrict__ in, double scale) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (TO)(scale * (double)in[i]);
+}
+
+template <typename TO, typename TI>
+cudaError_t convert(long long n, TO* out, const TI* in, double scale, cudaStream_t s) {
+  convert_kernel<TO, TI><<<stream_blocks(n), 256, 0, s>>>(n, out, in, scale);
+  return cudaGetLastError();
+}
+
+template cudaError_t multi_dot<double>(long long, const double*, const double* const*, int, double*, double*, cudaStream_t);
+template cudaError_t multi_dot<float>(long long, const float*, const float* const*, int, double*, double*, cudaStream_t);
+template cudaError_t multi_axpy<double>(long long, double*, double, const double* const*, const double*, int, cudaStream_t);
+template cudaError_t multi_axpy<float>(long long, float*, double, const float* const*, const double*, int, cudaStream_t);
+template cudaError_t convert<float, double>(long long, float*, const double*, double, cudaStream_t);
+template cudaError_t convert<double, float>(long long, double*, const float*, double, cudaStream_t);
+template cudaError_t convert<double, double>(long long, double*, const double*, double, cudaStream_t);
+template cudaError_t convert<float, float>(long long, float*, const float*, double, cudaStream_t);
+
+}  // namespace tp

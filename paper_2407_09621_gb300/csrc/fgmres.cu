@@ -1,0 +1,280 @@
+// Flexible GMRES (Saad 1993) with right preconditioning in FP64 on the GPU
+// (Sec. 7.1: the outer iteration in double precision, the multigrid
+// preconditioner in lower precision with conversion at its entry and exit).
+//
+// Arnoldi step j: z_j = M^{-1} v_j (one V-cycle, zero initial guess),
+// w = A z_j (FP64 apply), classical Gram-Schmidt with one re-orthogonalization
+// pass (two fused multi-dot/multi-axpy passes over V), v_{j+1} = w/||w||.
+// The small Hessenberg least-squares problem is solved on the host with
+// Givens rotations; its residual |g_{j+1}| is the convergence test.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tp_internal.h"
+#include "tp_vec.h"
+
+namespace tp {
+tp_status cuda_status(int err, const char* what);
+cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s);
+int mg_finest_level(const tp_mg_s* mg);
+tp_precision mg_precision(const tp_mg_s* mg);
+long long mg_finest_ndofs(const tp_mg_s* mg);
+size_t elem_bytes(tp_precision p);
+}  // namespace tp
+
+struct tp_solver_s {
+  tp_op_s* A = nullptr;
+  tp_mg_s* mg = nullptr;
+  int m = 30;
+  long long n = 0;
+  std::vector<double*> V, Z;
+  double* w = nullptr;
+  void* pb = nullptr;  // preconditioner input (mg precision)
+  void* px = nullptr;  // preconditioner output
+  double* partial = nullptr;
+  double* dots = nullptr;
+  std::vector<double> history;
+};
+
+using namespace tp;
+
+static void solver_free(tp_solver_s* s) {
+  for (double* p : s->V) if (p) cudaFree(p);
+  for (double* p : s->Z) if (p) cudaFree(p);
+  if (s->w) cudaFree(s->w);
+  if (s->pb) cudaFree(s->pb);
+  if (s->px) cudaFree(s->px);
+  if (s->partial) cudaFree(s->partial);
+  if (s->dots) cudaFree(s->dots);
+}
+
+extern "C" {
+
+tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart) {
+  if (!out) { set_error("tp_fgmres_create: out is NULL"); return TP_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!A || A->prec != TP_FP64) { set_error("tp_fgmres_create: A must be an FP64 operator"); return TP_ERR_INVALID_ARG; }
+  if (restart < 1 || restart > 256) { set_error("tp_fgmres_create: restart must be in [1, 256]"); return TP_ERR_INVALID_ARG; }
+  if (mg && mg_finest_ndofs(mg) != A->ndofs) { set_error("tp_fgmres_create: preconditioner size differs from A"); return TP_ERR_INVALID_ARG; }
+  tp_solver_s* s = new (std::nothrow) tp_solver_s();
+  if (!s) { set_error("tp_fgmres_create: out of host memory"); return TP_ERR_OOM; }
+  s->A = A;
+  s->mg = mg;
+  s->m = restart;
+  s->n = A->ndofs;
+  const size_t bytes = sizeof(double) * (size_t)s->n;
+  tp_status st = TP_OK;
+  s->V.assign(restart + 1, nullptr);
+  s->Z.assign(restart, nullptr);
+  for (int i = 0; i <= restart && st == TP_OK; ++i) st = cuda_status(cudaMalloc(&s->V[i], bytes), "tp_fgmres_create: Krylov basis");
+  for (int i = 0; i < restart && st == TP_OK; ++i) st = cuda_status(cudaMalloc(&s->Z[i], bytes), "tp_fgmres_create: flexible basis");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->w, bytes), "tp_fgmres_create: work vector");
+  if (st == TP_OK && mg) {
+    const size_t pbytes = elem_bytes(mg_precision(mg)) * (size_t)s->n;
+    st = cuda_status(cudaMalloc(&s->pb, pbytes), "tp_fgmres_create: preconditioner vectors");
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&s->px, pbytes), "tp_fgmres_create: preconditioner vectors");
+  }
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->partial, sizeof(double) * kMaxMulti * dot_blocks(s->n)), "tp_fgmres_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->dots, sizeof(double) * (restart + 2)), "tp_fgmres_create: scratch");
+  if (st != TP_OK) {
+    solver_free(s);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return TP_OK;
+}
+
+tp_status tp_solver_destroy(tp_solver s) {
+  if (!s) return TP_OK;
+  solver_free(s);
+  delete s;
+  return TP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct Ctx {
+  tp_solver_s* s;
+  cudaStream_t st;
+};
+
+cudaError_t dots_to_host(Ctx& c, const double* w, int nq, double* host) {
+  std::vector<const double*> v(c.s->V.begin(), c.s->V.begin() + nq);
+  cudaError_t e = multi_dot<double>(c.s->n, w, v.data(), nq, c.s->partial, c.s->dots, c.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, c.s->dots, sizeof(double) * nq, cudaMemcpyDeviceToHost, c.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+  return e;
+}
+
+cudaError_t norm_to_host(Ctx& c, const double* w, double* out) {
+  const double* v[1] = {w};
+  cudaError_t e = multi_dot<double>(c.s->n, w, v, 1, c.s->partial, c.s->dots, c.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, c.s->dots, sizeof(double), cudaMemcpyDeviceToHost, c.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+  if (e == cudaSuccess) *out = std::sqrt(*out);
+  return e;
+}
+
+// out = b - A x
+cudaError_t residual64(Ctx& c, double* out, const double* b, const double* x) {
+  cudaError_t e = launch_apply_cc(c.s->A, c.s->w, x, c.st);
+  const double coef[2] = {1.0, -1.0};
+  const double* v[2] = {b, c.s->w};
+  if (e == cudaSuccess) e = multi_axpy<double>(c.s->n, out, 0.0, v, coef, 2, c.st);
+  return e;
+}
+
+}  // namespace
+
+extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, double rtol, int maxit,
+                                     tp_solve_info* info, void* stream) {
+  if (info) memset(info, 0, sizeof(*info));
+  if (!s || !x || !b) { set_error("tp_fgmres_solve: NULL argument"); return TP_ERR_INVALID_ARG; }
+  if (((uintptr_t)x & 15) || ((uintptr_t)b & 15)) { set_error("tp_fgmres_solve: vectors must be 16-byte aligned"); return TP_ERR_INVALID_ARG; }
+  if (!(rtol > 0) || maxit < 1) { set_error("tp_fgmres_solve: rtol must be > 0 and maxit >= 1"); return TP_ERR_INVALID_ARG; }
+  Ctx c{s, (cudaStream_t)stream};
+  const int m = s->m;
+  const long long n = s->n;
+  const double pscale = std::sqrt((double)n);  // v_j has unit norm: scale to O(1) entries for low precision
+  s->history.clear();
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 2), h2(m + 2);
+  auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  int its = 0, restarts = 0, converged = 0;
+  double beta0 = 0.0, rel = 1.0;
+  cudaError_t e = residual64(c, s->V[0], b, x);
+  if (e == cudaSuccess) e = norm_to_host(c, s->V[0], &beta0);
+  if (e != cudaSuccess) return cuda_status(e, "tp_fgmres_solve");
+  if (!std::isfinite(beta0)) { set_error("tp_fgmres_solve: non-finite initial residual"); return TP_ERR_NONFINITE; }
+  s->history.push_back(1.0);
+  tp_status status = TP_OK;
+  if (beta0 == 0.0) converged = 1;
+  double beta = beta0;
+  while (!converged && its < maxit && status == TP_OK) {
+    if (restarts > 0) {
+      e = residual64(c, s->V[0], b, x);
+      if (e == cudaSuccess) e = norm_to_host(c, s->V[0], &beta);
+      if (e != cudaSuccess) { status = cuda_status(e, "tp_fgmres_solve"); break; }
+      if (beta <= rtol * beta0) { converged = 1; break; }
+    }
+    {
+      const double c1[1] = {1.0 / beta};
+      const double* v[1] = {s->V[0]};
+      e = multi_axpy<double>(n, s->V[0], 0.0, v, c1, 1, c.st);
+    }
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m && e == cudaSuccess; ++j) {
+      // z_j = M^{-1} v_j
+      if (s->mg) {
+        const int fl = mg_finest_level(s->mg);
+        if (mg_precision(s->mg) == TP_FP64) {
+          e = convert<double, double>(n, (double*)s->pb, s->V[j], pscale, c.st);
+          if (e == cudaSuccess) e = mg_vcycle(s->mg, fl, s->px, s->pb, 1, c.st);
+          if (e == cudaSuccess) e = convert<double, double>(n, s->Z[j], (const double*)s->px, 1.0 / pscale, c.st);
+        } else {
+          e = convert<float, double>(n, (float*)s->pb, s->V[j], pscale, c.st);
+          if (e == cudaSuccess) e = mg_vcycle(s->mg, fl, s->px, s->pb, 1, c.st);
+          if (e == cudaSuccess) e = convert<double, float>(n, s->Z[j], (const float*)s->px, 1.0 / pscale, c.st);
+        }
+      } else {
+        e = cudaMemcpyAsync(s->Z[j], s->V[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st);
+      }
+      if (e == cudaSuccess) e = launch_apply_cc(s->A, s->w, s->Z[j], c.st);
+      // classical Gram-Schmidt, two passes
+      if (e == cudaSuccess) e = dots_to_host(c, s->w, j + 1, h.data());
+      if (e == cudaSuccess) {
+        std::vector<double> neg(j + 1);
+        for (int i = 0; i <= j; ++i) neg[i] = -h[i];
+        std::vector<const double*> v(s->V.begin(), s->V.begin() + j + 1);
+        e = multi_axpy<double>(n, s->w, 1.0, v.data(), neg.data(), j + 1, c.st);
+      }
+      if (e == cudaSuccess) e = dots_to_host(c, s->w, j + 1, h2.data());
+      if (e == cudaSuccess) {
+        std::vector<double> neg(j + 1);
+        for (int i = 0; i <= j; ++i) { neg[i] = -h2[i]; h[i] += h2[i]; }
+        std::vector<const double*> v(s->V.begin(), s->V.begin() + j + 1);
+        e = multi_axpy<double>(n, s->w, 1.0, v.data(), neg.data(), j + 1, c.st);
+      }
+      double hn = 0.0;
+      if (e == cudaSuccess) e = norm_to_host(c, s->w, &hn);
+      if (e != cudaSuccess) break;
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h[i];
+      Hij(j + 1, j) = hn;
+      bool finite = std::isfinite(hn);
+      for (int i = 0; i <= j; ++i) finite = finite && std::isfinite(h[i]);
+      if (!finite) {
+        set_error("tp_fgmres_solve: non-finite value in the Arnoldi process (iteration %d)", its);
+        status = TP_ERR_NONFINITE;
+        break;
+      }
+      if (hn > 0) {
+        const double c1[1] = {1.0 / hn};
+        const double* v[1] = {s->w};
+        e = multi_axpy<double>(n, s->V[j + 1], 0.0, v, c1, 1, c.st);
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = den > 0 ? Hij(j, j) / den : 1.0;
+      sn[j] = den > 0 ? Hij(j + 1, j) / den : 0.0;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++its;
+      jend = j + 1;
+      rel = std::fabs(g[j + 1]) / beta0;
+      s->history.push_back(rel);
+      if (rel <= rtol) { converged = 1; break; }
+      if (its >= maxit || hn == 0.0) break;
+    }
+    if (e != cudaSuccess) { status = cuda_status(e, "tp_fgmres_solve"); break; }
+    if (status != TP_OK) break;
+    for (int i = jend - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int k2 = i + 1; k2 < jend; ++k2) sum -= Hij(i, k2) * y[k2];
+      y[i] = sum / Hij(i, i);
+    }
+    {
+      std::vector<const double*> v(s->Z.begin(), s->Z.begin() + jend);
+      e = multi_axpy<double>(n, x, 1.0, v.data(), y.data(), jend, c.st);
+      if (e != cudaSuccess) { status = cuda_status(e, "tp_fgmres_solve"); break; }
+    }
+    if (!converged) ++restarts;
+  }
+  double true_rel = NAN;
+  if (status == TP_OK || status == TP_ERR_NOT_CONVERGED) {
+    double rn = 0.0;
+    e = residual64(c, s->V[0], b, x);
+    if (e == cudaSuccess) e = norm_to_host(c, s->V[0], &rn);
+    if (e != cudaSuccess) status = cuda_status(e, "tp_fgmres_solve");
+    true_rel = beta0 > 0 ? rn / beta0 : 0.0;
+  }
+  if (info) {
+    info->iterations = its;
+    info->restarts = restarts;
+    info->converged = converged;
+    info->rel_residual = rel;
+    info->true_rel_residual = true_rel;
+    info->history = s->history.data();
+    info->history_len = (int)s->history.size();
+  }
+  if (status == TP_OK && !converged) {
+    set_error("tp_fgmres_solve: not converged after %d iterations (relative residual %.3e)", its, rel);
+    return TP_ERR_NOT_CONVERGED;
+  }
+  return status;
+}

@@ -1,0 +1,731 @@
+// Geometric multigrid V-cycle (Algorithm 2, Sec. 7.1) for the SIPG operator.
+//
+// Levels: uniform coarsening by 2 in every direction, same degree k, the
+// operator rediscretized on each level (Sec. 2 with that level's h).
+// Smoother: Chebyshev semi-iteration of the given degree on D^{-1} A with
+// D = diag(A) evaluated from the Kronecker form of Eq. (9) (the paper's
+// vertex-patch Schwarz smoother is not used). Transfer: prolongation is the
+// exact embedding of the coarse DG space (coarse basis evaluated at the fine
+// nodes, a Kronecker product of 1D n x n matrices per child), restriction
+// its transpose; both sum-factorized. Coarse solve: exact, in FP64, by fast
+// diagonalization with the 1D generalized eigenpairs L V = M V Lambda.
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tp_internal.h"
+#include "tp_vec.h"
+
+namespace tp {
+
+tp_status cuda_status(int err, const char* what);
+cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+size_t elem_bytes(tp_precision p);
+
+template <typename T>
+struct JacobiParams {
+  T Md[3][kMaxN], Ld[3][kMaxN];  // diagonals of the 1D mass and interior stiffness blocks
+  T lo[3], hi[3];                // boundary corrections of L's diagonal at node 0 / node n-1
+  int nx, ny, nz;
+};
+
+template <typename T>
+struct TransferParams {
+  T P[2][kMaxN * kMaxN];  // P[c][i*kMaxN + j] = phi_j((c + x_i)/2)
+};
+
+// D^{-1} at DoF (cell, l, j, i)
+template <typename T, int N>
+__device__ __forceinline__ T jacobi_inv(const JacobiParams<T>& J, long long idx) {
+  constexpr int N3 = N * N * N;
+  const long long cell = idx / N3;
+  const int loc = (int)(idx % N3);
+  const int i = loc % N, j = (loc / N) % N, l = loc / (N * N);
+  const int cx = (int)(cell % J.nx), cy = (int)((cell / J.nx) % J.ny), cz = (int)(cell / ((long long)J.nx * J.ny));
+  T lx = J.Ld[0][i], ly = J.Ld[1][j], lz = J.Ld[2][l];
+  if (cx == 0 && i == 0) lx += J.lo[0];
+  if (cx == J.nx - 1 && i == N - 1) lx += J.hi[0];
+  if (cy == 0 && j == 0) ly += J.lo[1];
+  if (cy == J.ny - 1 && j == N - 1) ly += J.hi[1];
+  if (cz == 0 && l == 0) lz += J.lo[2];
+  if (cz == J.nz - 1 && l == N - 1) lz += J.hi[2];
+  const T mx = J.Md[0][i], my = J.Md[1][j], mz = J.Md[2][l];
+  return T(1) / (lz * my * mx + mz * ly * mx + mz * my * lx);
+}
+
+// Chebyshev update: if t: r -= t;  d = c1*d + c2*D^{-1} r (c1 == 0: d is not read);  x = (x_zero ? 0 : x) + d
+template <typename T, int N>
+__global__ void cheb_update_kernel(long long n, const __grid_constant__ JacobiParams<T> J, T* __restrict__ x,
+                                   T* __restrict__ r, T* __restrict__ d, const T* __restrict__ t, T c1, T c2,
+                                   int x_zero) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T ri = r[i];
+    if (t) {
+      ri -= t[i];
+      r[i] = ri;
+    }
+    T di = c2 * jacobi_inv<T, N>(J, i) * ri;
+    if (c1 != T(0)) di = fma(c1, d[i], di);
+    d[i] = di;
+    x[i] = x_zero ? di : x[i] + di;
+  }
+}
+
+// y = s * D^{-1} t (inv = 1) or y = s * D t (inv = 0)
+template <typename T, int N>
+__global__ void dinv_kernel(long long n, const __grid_constant__ JacobiParams<T> J, T* __restrict__ y,
+                            const T* __restrict__ t, T s, int inv) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const T di = jacobi_inv<T, N>(J, i);
+    y[i] = inv ? s * di * t[i] : s * t[i] / di;
+  }
+}
+
+// xf += P xc : one block per coarse cell, thread (l, j, i); children in turn.
+template <typename T, int N>
+__global__ void __launch_bounds__(N * N * N) prolong_add_kernel(T* __restrict__ xf, const T* __restrict__ xc,
+                                                                const __grid_constant__ TransferParams<T> P, int ncx,
+                                                                int ncy, int ncz) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  __shared__ T u[N3], t1[N3], t2[N3];
+  const long long C = blockIdx.x;
+  const int tid = threadIdx.x, i = tid % N, j = (tid / N) % N, l = tid / N2;
+  const int cx = (int)(C % ncx), cy = (int)((C / ncx) % ncy), cz = (int)(C / ((long long)ncx * ncy));
+  u[tid] = xc[C * N3 + tid];
+  __syncthreads();
+  for (int b = 0; b < 8; ++b) {
+    const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+    T s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[bx][i * kMaxN + m], u[l * N2 + j * N + m], s);
+    t1[tid] = s;
+    __syncthreads();
+    s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[by][j * kMaxN + m], t1[l * N2 + m * N + i], s);
+    t2[tid] = s;
+    __syncthreads();
+    s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[bz][l * kMaxN + m], t2[m * N2 + j * N + i], s);
+    const long long F = ((long long)(2 * cz + bz) * (2 * ncy) + (2 * cy + by)) * (2LL * ncx) + (2 * cx + bx);
+    xf[F * N3 + tid] += s;
+    __syncthreads();
+  }
+}
+
+// xc = P^T rf : one block per coarse cell, sum over the eight children.
+template <typename T, int N>
+__global__ void __launch_bounds__(N * N * N) restrict_kernel(T* __restrict__ xc, const T* __restrict__ rf,
+                                                             const __grid_constant__ TransferParams<T> P, int ncx,
+                                                             int ncy, int ncz) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  __shared__ T u[N3], t1[N3], t2[N3];
+  const long long C = blockIdx.x;
+  const int tid = threadIdx.x, i = tid % N, j = (tid / N) % N, l = tid / N2;
+  const int cx = (int)(C % ncx), cy = (int)((C / ncx) % ncy), cz = (int)(C / ((long long)ncx * ncy));
+  T acc = 0;
+  for (int b = 0; b < 8; ++b) {
+    const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
+    const long long F = ((long long)(2 * cz + bz) * (2 * ncy) + (2 * cy + by)) * (2LL * ncx) + (2 * cx + bx);
+    u[tid] = rf[F * N3 + tid];
+    __syncthreads();
+    T s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[bx][m * kMaxN + i], u[l * N2 + j * N + m], s);
+    t1[tid] = s;
+    __syncthreads();
+    s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[by][m * kMaxN + j], t1[l * N2 + m * N + i], s);
+    t2[tid] = s;
+    __syncthreads();
+    s = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) s = fma(P.P[bz][m * kMaxN + l], t2[m * N2 + j * N + i], s);
+    acc += s;
+    __syncthreads();
+  }
+  xc[C * N3 + tid] = acc;
+}
+
+// ---- coarse solve by fast diagonalization (FP64), on a lexicographic N1z x N1y x N1x tensor
+struct FDDims {
+  int n, nx, ny, nz;     // nodes per direction, cells
+  int N1[3];             // nx*n, ny*n, nz*n
+};
+
+template <typename T>
+__global__ void fd_gather(const T* __restrict__ b, double* __restrict__ lex, FDDims D, double scale) {
+  const long long tot = (long long)D.N1[0] * D.N1[1] * D.N1[2];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(e % D.N1[0]), gy = (int)((e / D.N1[0]) % D.N1[1]), gz = (int)(e / ((long long)D.N1[0] * D.N1[1]));
+    const long long cell = ((long long)(gz / D.n) * D.ny + gy / D.n) * D.nx + gx / D.n;
+    const int loc = ((gz % D.n) * D.n + gy % D.n) * D.n + gx % D.n;
+    lex[e] = scale * (double)b[cell * D.n * D.n * D.n + loc];
+  }
+}
+
+template <typename T>
+__global__ void fd_scatter(const double* __restrict__ lex, T* __restrict__ x, FDDims D, double scale) {
+  const long long tot = (long long)D.N1[0] * D.N1[1] * D.N1[2];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(e % D.N1[0]), gy = (int)((e / D.N1[0]) % D.N1[1]), gz = (int)(e / ((long long)D.N1[0] * D.N1[1]));
+    const long long cell = ((long long)(gz / D.n) * D.ny + gy / D.n) * D.nx + gx / D.n;
+    const int loc = ((gz % D.n) * D.n + gy % D.n) * D.n + gx % D.n;
+    x[cell * D.n * D.n * D.n + loc] = (T)(scale * lex[e]);
+  }
+}
+
+// out = W applied along `axis` (0 = x fastest, 2 = z): out[..a..] = sum_m W(m, a) in[..m..],
+// W(m, a) = V[m*N + a] (transpose == 0, i.e. V^T applied) or V[a*N + m] (transpose == 1, V applied).
+__global__ void fd_contract(const double* __restrict__ in, double* __restrict__ out, const double* __restrict__ V,
+                            FDDims D, int axis, int transpose) {
+  const long long tot = (long long)D.N1[0] * D.N1[1] * D.N1[2];
+  const int N = D.N1[axis];
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? D.N1[0] : (long long)D.N1[0] * D.N1[1]);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)((e / stride) % N);
+    const long long base = e - (long long)a * stride;
+    double s = 0.0;
+    for (int m = 0; m < N; ++m) {
+      const double w = transpose ? V[(size_t)a * N + m] : V[(size_t)m * N + a];
+      s = fma(w, in[base + m * stride], s);
+    }
+    out[e] = s;
+  }
+}
+
+__global__ void fd_divide(double* __restrict__ t, const double* __restrict__ lx, const double* __restrict__ ly,
+                          const double* __restrict__ lz, FDDims D) {
+  const long long tot = (long long)D.N1[0] * D.N1[1] * D.N1[2];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(e % D.N1[0]), gy = (int)((e / D.N1[0]) % D.N1[1]), gz = (int)(e / ((long long)D.N1[0] * D.N1[1]));
+    t[e] /= lx[gx] + ly[gy] + lz[gz];
+  }
+}
+
+// deterministic pseudo-random start vector in [-1, 1] (power iteration)
+template <typename T>
+__global__ void hash_fill(long long n, T* __restrict__ x, unsigned seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i * 0x9E3779B97F4A7C15ULL + seed;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    x[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+}  // namespace tp
+
+// ------------------------------------------------------------------ host side
+struct tp_mg_level {
+  int nc[3];
+  tp_op_s* op = nullptr;  // owned
+  long long ndofs = 0;
+  void *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
+  double lmax = 0.0;
+  tp::JacobiParams<double> j64;
+  tp::JacobiParams<float> j32;
+};
+
+struct tp_mg_s {
+  int k = 0, n = 0;
+  tp_precision prec = TP_FP32;  // storage/arithmetic of the V-cycle vectors
+  tp_mg_opts opts;
+  std::vector<tp_mg_level> lv;  // 0 = coarsest
+  tp::TransferParams<double> p64;
+  tp::TransferParams<float> p32;
+  tp::FDDims fd;
+  double *fdV[3] = {nullptr, nullptr, nullptr}, *fdL[3] = {nullptr, nullptr, nullptr};
+  double *fdT0 = nullptr, *fdT1 = nullptr;
+  double* partial = nullptr;  // reduction scratch
+  double* dots = nullptr;     // device results of reductions
+};
+
+namespace tp {
+
+static int grid_for(long long n) { return stream_blocks(n); }
+
+template <typename T>
+static const JacobiParams<T>& jparams(const tp_mg_level& L);
+template <>
+const JacobiParams<double>& jparams<double>(const tp_mg_level& L) { return L.j64; }
+template <>
+const JacobiParams<float>& jparams<float>(const tp_mg_level& L) { return L.j32; }
+
+template <typename T>
+static const TransferParams<T>& tparams(const tp_mg_s* mg);
+template <>
+const TransferParams<double>& tparams<double>(const tp_mg_s* mg) { return mg->p64; }
+template <>
+const TransferParams<float>& tparams<float>(const tp_mg_s* mg) { return mg->p32; }
+
+template <typename T, int N>
+static cudaError_t cheb_update_n(const tp_mg_level& L, void* x, void* r, void* d, const void* t, double c1, double c2,
+                                 int x_zero, cudaStream_t s) {
+  cheb_update_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<T>(L), (T*)x, (T*)r, (T*)d,
+                                                             (const T*)t, (T)c1, (T)c2, x_zero);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t dinv_n(const tp_mg_level& L, void* y, const void* t, double sc, int inv, cudaStream_t s) {
+  dinv_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<T>(L), (T*)y, (const T*)t, (T)sc, inv);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t prolong_n(const tp_mg_s* mg, int l, void* xf, const void* xc, cudaStream_t s) {
+  const tp_mg_level& C = mg->lv[l - 1];
+  const long long nc = (long long)C.nc[0] * C.nc[1] * C.nc[2];
+  prolong_add_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xf, (const T*)xc, tparams<T>(mg), C.nc[0], C.nc[1],
+                                                              C.nc[2]);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t restrict_n(const tp_mg_s* mg, int l, void* xc, const void* rf, cudaStream_t s) {
+  const tp_mg_level& C = mg->lv[l - 1];
+  const long long nc = (long long)C.nc[0] * C.nc[1] * C.nc[2];
+  restrict_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xc, (const T*)rf, tparams<T>(mg), C.nc[0], C.nc[1],
+                                                           C.nc[2]);
+  return cudaGetLastError();
+}
+
+#define TP_DISPATCH_N(n, CALL) \
+  switch (n) {                 \
+    case 2: return CALL(2);    \
+    case 3: return CALL(3);    \
+    case 4: return CALL(4);    \
+    case 5: return CALL(5);    \
+    case 6: return CALL(6);    \
+    case 7: return CALL(7);    \
+    case 8: return CALL(8);    \
+  }                            \
+  return cudaErrorInvalidValue;
+
+static cudaError_t cheb_update(const tp_mg_s* mg, const tp_mg_level& L, void* x, void* r, void* d, const void* t,
+                               double c1, double c2, int x_zero, cudaStream_t s) {
+  if (mg->prec == TP_FP64) {
+#define C64(N) cheb_update_n<double, N>(L, x, r, d, t, c1, c2, x_zero, s)
+    TP_DISPATCH_N(mg->n, C64)
+#undef C64
+  } else {
+#define C32(N) cheb_update_n<float, N>(L, x, r, d, t, c1, c2, x_zero, s)
+    TP_DISPATCH_N(mg->n, C32)
+#undef C32
+  }
+}
+
+static cudaError_t dinv(const tp_mg_s* mg, const tp_mg_level& L, void* y, const void* t, double sc, int inv,
+                        cudaStream_t s) {
+  if (mg->prec == TP_FP64) {
+#define D64(N) dinv_n<double, N>(L, y, t, sc, inv, s)
+    TP_DISPATCH_N(mg->n, D64)
+#undef D64
+  } else {
+#define D32(N) dinv_n<float, N>(L, y, t, sc, inv, s)
+    TP_DISPATCH_N(mg->n, D32)
+#undef D32
+  }
+}
+
+cudaError_t mg_prolong_add(const tp_mg_s* mg, int l, void* xf, const void* xc, cudaStream_t s) {
+  if (mg->prec == TP_FP64) {
+#define P64(N) prolong_n<double, N>(mg, l, xf, xc, s)
+    TP_DISPATCH_N(mg->n, P64)
+#undef P64
+  } else {
+#define P32(N) prolong_n<float, N>(mg, l, xf, xc, s)
+    TP_DISPATCH_N(mg->n, P32)
+#undef P32
+  }
+}
+
+cudaError_t mg_restrict(const tp_mg_s* mg, int l, void* xc, const void* rf, cudaStream_t s) {
+  if (mg->prec == TP_FP64) {
+#define R64(N) restrict_n<double, N>(mg, l, xc, rf, s)
+    TP_DISPATCH_N(mg->n, R64)
+#undef R64
+  } else {
+#define R32(N) restrict_n<float, N>(mg, l, xc, rf, s)
+    TP_DISPATCH_N(mg->n, R32)
+#undef R32
+  }
+}
+
+static long long fd_total(const FDDims& D) { return (long long)D.N1[0] * D.N1[1] * D.N1[2]; }
+
+cudaError_t mg_coarse_solve(const tp_mg_s* mg, void* x, const void* b, cudaStream_t s) {
+  const FDDims& D = mg->fd;
+  const long long tot = fd_total(D);
+  const int g = grid_for(tot);
+  if (mg->prec == TP_FP64)
+    fd_gather<double><<<g, 256, 0, s>>>((const double*)b, mg->fdT0, D, 1.0);
+  else
+    fd_gather<float><<<g, 256, 0, s>>>((const float*)b, mg->fdT0, D, 1.0);
+  double *a = mg->fdT0, *c = mg->fdT1;
+  for (int ax = 0; ax < 3; ++ax) {
+    fd_contract<<<g, 256, 0, s>>>(a, c, mg->fdV[ax], D, ax, 0);
+    double* tmp = a; a = c; c = tmp;
+  }
+  fd_divide<<<g, 256, 0, s>>>(a, mg->fdL[0], mg->fdL[1], mg->fdL[2], D);
+  for (int ax = 0; ax < 3; ++ax) {
+    fd_contract<<<g, 256, 0, s>>>(a, c, mg->fdV[ax], D, ax, 1);
+    double* tmp = a; a = c; c = tmp;
+  }
+  if (mg->prec == TP_FP64)
+    fd_scatter<double><<<g, 256, 0, s>>>(a, (double*)x, D, 1.0);
+  else
+    fd_scatter<float><<<g, 256, 0, s>>>(a, (float*)x, D, 1.0);
+  return cudaGetLastError();
+}
+
+// r = b - A x  (t is scratch)
+static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, const void* b, const void* x, void* t,
+                            cudaStream_t s) {
+  cudaError_t e = launch_apply_cc(L.op, t, x, s);
+  if (e != cudaSuccess) return e;
+  const double c[2] = {1.0, -1.0};
+  if (mg->prec == TP_FP64) {
+    const double* v[2] = {(const double*)b, (const double*)t};
+    return multi_axpy<double>(L.ndofs, (double*)r, 0.0, v, c, 2, s);
+  }
+  const float* v[2] = {(const float*)b, (const float*)t};
+  return multi_axpy<float>(L.ndofs, (float*)r, 0.0, v, c, 2, s);
+}
+
+// `degree` Chebyshev-Jacobi steps on level l from x (x_zero: x is taken as 0 and not read)
+cudaError_t mg_smooth(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s) {
+  const tp_mg_level& L = mg->lv[l];
+  const double lmax = L.lmax, lmin = lmax / mg->opts.ratio;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  cudaError_t e;
+  if (x_zero) {
+    e = cudaMemcpyAsync(L.r, b, L.ndofs * elem_bytes(mg->prec), cudaMemcpyDeviceToDevice, s);
+  } else {
+    e = residual(mg, L, L.r, b, x, L.t, s);
+  }
+  if (e != cudaSuccess) return e;
+  e = cheb_update(mg, L, x, L.r, L.d, nullptr, 0.0, 1.0 / theta, x_zero, s);
+  for (int it = 1; it < mg->opts.degree && e == cudaSuccess; ++it) {
+    e = launch_apply_cc(L.op, L.t, L.d, s);
+    if (e != cudaSuccess) break;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    e = cheb_update(mg, L, x, L.r, L.d, L.t, rho_new * rho, 2.0 * rho_new / delta, 0, s);
+    rho = rho_new;
+  }
+  return e;
+}
+
+cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s) {
+  if (l == 0) return mg_coarse_solve(mg, x, b, s);
+  const tp_mg_level& L = mg->lv[l];
+  const tp_mg_level& C = mg->lv[l - 1];
+  cudaError_t e = mg_smooth(mg, l, x, b, x_zero, s);
+  if (e == cudaSuccess) e = residual(mg, L, L.r, b, x, L.t, s);
+  if (e == cudaSuccess) e = mg_restrict(mg, l, C.b, L.r, s);
+  if (e == cudaSuccess) e = mg_vcycle(mg, l - 1, C.x, C.b, 1, s);
+  if (e == cudaSuccess) e = mg_prolong_add(mg, l, x, C.x, s);
+  if (e == cudaSuccess) e = mg_smooth(mg, l, x, b, 0, s);
+  return e;
+}
+
+// lmax(D^{-1}A) on level l: power iteration x <- D^{-1}A x / |.| from a fixed
+// pseudo-random start; the estimate is the generalized Rayleigh quotient
+// (x, A x) / (x, D x) of the last iterate, which never exceeds lmax.
+static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, double* out) {
+  tp_mg_level& L = mg->lv[l];
+  const bool f64 = mg->prec == TP_FP64;
+  if (f64)
+    hash_fill<double><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, (double*)L.d, 12345u + l);
+  else
+    hash_fill<float><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, (float*)L.d, 12345u + l);
+  double rho = 0.0, h[2];
+  // L.d = x, L.t = A x, L.r = D x then D^{-1} A x
+  for (int it = 0; it < iters; ++it) {
+    cudaError_t e = launch_apply_cc(L.op, L.t, L.d, s);
+    if (e == cudaSuccess) e = dinv(mg, L, L.r, L.d, 1.0, 0, s);
+    if (e == cudaSuccess) {
+      if (f64) {
+        const double* v[2] = {(const double*)L.t, (const double*)L.r};
+        e = multi_dot<double>(L.ndofs, (const double*)L.d, v, 2, mg->partial, mg->dots, s);
+      } else {
+        const float* v[2] = {(const float*)L.t, (const float*)L.r};
+        e = multi_dot<float>(L.ndofs, (const float*)L.d, v, 2, mg->partial, mg->dots, s);
+      }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, mg->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "tp_mg_create: eigenvalue estimate");
+    rho = h[0] / h[1];
+    if (!std::isfinite(rho) || !(h[1] > 0)) {
+      set_error("tp_mg_create: eigenvalue estimate broke down on level %d", l);
+      return TP_ERR_NONFINITE;
+    }
+    // x <- D^{-1} A x, normalised
+    e = dinv(mg, L, L.r, L.t, 1.0, 1, s);
+    double nn = 0.0;
+    if (e == cudaSuccess) {
+      if (f64) {
+        const double* v[1] = {(const double*)L.r};
+        e = multi_dot<double>(L.ndofs, (const double*)L.r, v, 1, mg->partial, mg->dots, s);
+      } else {
+        const float* v[1] = {(const float*)L.r};
+        e = multi_dot<float>(L.ndofs, (const float*)L.r, v, 1, mg->partial, mg->dots, s);
+      }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, mg->dots, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e, "tp_mg_create: eigenvalue estimate");
+    if (!(nn > 0) || !std::isfinite(nn)) {
+      set_error("tp_mg_create: eigenvalue estimate broke down on level %d", l);
+      return TP_ERR_NONFINITE;
+    }
+    const double c[1] = {1.0 / std::sqrt(nn)};
+    if (f64) {
+      const double* v[1] = {(const double*)L.r};
+      e = multi_axpy<double>(L.ndofs, (double*)L.d, 0.0, v, c, 1, s);
+    } else {
+      const float* v[1] = {(const float*)L.r};
+      e = multi_axpy<float>(L.ndofs, (float*)L.d, 0.0, v, c, 1, s);
+    }
+    if (e != cudaSuccess) return cuda_status(e, "tp_mg_create: eigenvalue estimate");
+  }
+  *out = rho;
+  return TP_OK;
+}
+
+int mg_finest_level(const tp_mg_s* mg) { return (int)mg->lv.size() - 1; }
+tp_precision mg_precision(const tp_mg_s* mg) { return mg->prec; }
+long long mg_finest_ndofs(const tp_mg_s* mg) { return mg->lv.back().ndofs; }
+
+}  // namespace tp
+
+using namespace tp;
+
+static void free_level(tp_mg_level& L, bool own_xb) {
+  if (L.op) tp_op_destroy(L.op);
+  if (own_xb) {
+    if (L.x) cudaFree(L.x);
+    if (L.b) cudaFree(L.b);
+  }
+  if (L.r) cudaFree(L.r);
+  if (L.d) cudaFree(L.d);
+  if (L.t) cudaFree(L.t);
+  L = tp_mg_level();
+}
+
+extern "C" {
+
+tp_status tp_mg_destroy(tp_mg mg) {
+  if (!mg) return TP_OK;
+  for (size_t l = 0; l < mg->lv.size(); ++l) free_level(mg->lv[l], l + 1 < mg->lv.size());
+  for (int d = 0; d < 3; ++d) {
+    if (mg->fdV[d]) cudaFree(mg->fdV[d]);
+    if (mg->fdL[d]) cudaFree(mg->fdL[d]);
+  }
+  if (mg->fdT0) cudaFree(mg->fdT0);
+  if (mg->fdT1) cudaFree(mg->fdT1);
+  if (mg->partial) cudaFree(mg->partial);
+  if (mg->dots) cudaFree(mg->dots);
+  delete mg;
+  return TP_OK;
+}
+
+tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
+  if (!out) { set_error("tp_mg_create: out is NULL"); return TP_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (!finest) { set_error("tp_mg_create: operator is NULL"); return TP_ERR_INVALID_ARG; }
+  tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20};
+  if (opts) o = *opts;
+  if (o.degree < 1 || o.degree > 16 || !(o.ratio > 1.0) || !(o.safety > 0) || o.coarse_cells < 1 ||
+      (o.precision != TP_FP64 && o.precision != TP_FP32) || o.power_iters < 1 || o.lmax < 0) {
+    set_error("tp_mg_create: invalid options (degree 1..16, ratio > 1, safety > 0, coarse_cells >= 1, "
+              "precision FP64 or FP32, power_iters >= 1, lmax >= 0)");
+    return TP_ERR_INVALID_ARG;
+  }
+  tp_mg_s* mg = new (std::nothrow) tp_mg_s();
+  if (!mg) { set_error("tp_mg_create: out of host memory"); return TP_ERR_OOM; }
+  mg->k = finest->k;
+  mg->n = finest->n;
+  mg->prec = (tp_precision)o.precision;
+  mg->opts = o;
+  // level sizes: halve every direction while all are even and any exceeds coarse_cells
+  std::vector<std::array<int, 3>> sizes;
+  std::array<int, 3> cur = {finest->mesh.nx, finest->mesh.ny, finest->mesh.nz};
+  sizes.push_back(cur);
+  while ((cur[0] > o.coarse_cells || cur[1] > o.coarse_cells || cur[2] > o.coarse_cells) && cur[0] % 2 == 0 &&
+         cur[1] % 2 == 0 && cur[2] % 2 == 0) {
+    cur = {cur[0] / 2, cur[1] / 2, cur[2] / 2};
+    sizes.push_back(cur);
+  }
+  const int nl = (int)sizes.size();
+  if (nl > TP_MAX_LEVELS) {
+    delete mg;
+    set_error("tp_mg_create: more than %d levels", TP_MAX_LEVELS);
+    return TP_ERR_INVALID_ARG;
+  }
+  mg->lv.resize(nl);
+  const size_t eb = elem_bytes(mg->prec);
+  tp_status st = TP_OK;
+  tp_op_opts oo{finest->opts.penalty, TP_KERNEL_CUDA_CORE, 0};
+  for (int l = 0; l < nl && st == TP_OK; ++l) {
+    tp_mg_level& L = mg->lv[l];
+    const auto& sz = sizes[nl - 1 - l];
+    L.nc[0] = sz[0]; L.nc[1] = sz[1]; L.nc[2] = sz[2];
+    tp_mesh_s m{sz[0], sz[1], sz[2], finest->mesh.lx, finest->mesh.ly, finest->mesh.lz};
+    st = tp_dg_laplace_create(&L.op, &m, mg->k, mg->prec, &oo);
+    if (st != TP_OK) break;
+    L.ndofs = L.op->ndofs;
+    const size_t bytes = (size_t)L.ndofs * eb;
+    if (l + 1 < nl) {
+      st = cuda_status(cudaMalloc(&L.x, bytes), "tp_mg_create: level vectors");
+      if (st == TP_OK) st = cuda_status(cudaMalloc(&L.b, bytes), "tp_mg_create: level vectors");
+    }
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&L.r, bytes), "tp_mg_create: level vectors");
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&L.d, bytes), "tp_mg_create: level vectors");
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&L.t, bytes), "tp_mg_create: level vectors");
+    // Jacobi diagonal data
+    if (st == TP_OK) {
+      memset(&L.j64, 0, sizeof(L.j64));
+      for (int d = 0; d < 3; ++d) {
+        const Dir1D& dd = L.op->dir[d];
+        for (int i = 0; i < mg->n; ++i) {
+          L.j64.Md[d][i] = dd.M[i * mg->n + i];
+          L.j64.Ld[d][i] = dd.L[i * mg->n + i];
+        }
+        L.j64.lo[d] = L.op->ref.d0[0] / dd.h;
+        L.j64.hi[d] = -L.op->ref.d1[mg->n - 1] / dd.h;
+      }
+      L.j64.nx = sz[0]; L.j64.ny = sz[1]; L.j64.nz = sz[2];
+      L.j32.nx = sz[0]; L.j32.ny = sz[1]; L.j32.nz = sz[2];
+      for (int d = 0; d < 3; ++d) {
+        for (int i = 0; i < kMaxN; ++i) { L.j32.Md[d][i] = (float)L.j64.Md[d][i]; L.j32.Ld[d][i] = (float)L.j64.Ld[d][i]; }
+        L.j32.lo[d] = (float)L.j64.lo[d];
+        L.j32.hi[d] = (float)L.j64.hi[d];
+      }
+    }
+  }
+  // transfer matrices
+  if (st == TP_OK) {
+    memset(&mg->p64, 0, sizeof(mg->p64));
+    const Ref1D& r = mg->lv.back().op->ref;
+    for (int c = 0; c < 2; ++c) {
+      std::vector<double> xs(mg->n);
+      for (int i = 0; i < mg->n; ++i) xs[i] = 0.5 * (c + r.nodes[i]);
+      std::vector<double> V = lagrange_eval(r.nodes, xs);
+      for (int i = 0; i < mg->n; ++i)
+        for (int j = 0; j < mg->n; ++j) {
+          mg->p64.P[c][i * kMaxN + j] = V[i * mg->n + j];
+          mg->p32.P[c][i * kMaxN + j] = (float)V[i * mg->n + j];
+        }
+    }
+  }
+  // coarse fast diagonalization
+  if (st == TP_OK) {
+    tp_mg_level& C = mg->lv[0];
+    mg->fd.n = mg->n;
+    mg->fd.nx = C.nc[0]; mg->fd.ny = C.nc[1]; mg->fd.nz = C.nc[2];
+    for (int d = 0; d < 3 && st == TP_OK; ++d) {
+      const int N1 = C.nc[d] * mg->n;
+      mg->fd.N1[d] = N1;
+      std::vector<double> M, L, lam, V;
+      global_1d(C.op->ref, C.op->dir[d], C.nc[d], M, L);
+      if (!gen_eig(N1, M, L, lam, V)) { set_error("tp_mg_create: coarse mass matrix not positive definite"); st = TP_ERR_INVALID_ARG; break; }
+      st = cuda_status(cudaMalloc(&mg->fdV[d], sizeof(double) * N1 * N1), "tp_mg_create: coarse solve");
+      if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->fdL[d], sizeof(double) * N1), "tp_mg_create: coarse solve");
+      if (st == TP_OK) st = cuda_status(cudaMemcpy(mg->fdV[d], V.data(), sizeof(double) * N1 * N1, cudaMemcpyHostToDevice), "cudaMemcpy");
+      if (st == TP_OK) st = cuda_status(cudaMemcpy(mg->fdL[d], lam.data(), sizeof(double) * N1, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+    const long long tot = fd_total(mg->fd);
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->fdT0, sizeof(double) * tot), "tp_mg_create: coarse solve");
+    if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->fdT1, sizeof(double) * tot), "tp_mg_create: coarse solve");
+  }
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->partial, sizeof(double) * kMaxMulti * dot_blocks(mg->lv.back().ndofs)), "tp_mg_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->dots, sizeof(double) * kMaxMulti), "tp_mg_create: scratch");
+  // smoother eigenvalue bounds
+  for (int l = 1; l < nl && st == TP_OK; ++l) {
+    if (o.lmax > 0) {
+      mg->lv[l].lmax = o.lmax;
+    } else {
+      double est = 0.0;
+      st = estimate_lmax(mg, l, o.power_iters, 0, &est);
+      mg->lv[l].lmax = o.safety * est;
+    }
+  }
+  if (st == TP_OK) st = cuda_status(cudaDeviceSynchronize(), "tp_mg_create");
+  if (st != TP_OK) {
+    tp_mg_destroy(mg);
+    return st;
+  }
+  *out = mg;
+  return TP_OK;
+}
+
+tp_status tp_mg_get_info(tp_mg mg, tp_mg_info_t* info) {
+  if (!mg || !info) { set_error("tp_mg_get_info: NULL argument"); return TP_ERR_INVALID_ARG; }
+  memset(info, 0, sizeof(*info));
+  info->levels = (int)mg->lv.size();
+  info->precision = mg->prec;
+  for (int l = 0; l < info->levels && l < TP_MAX_LEVELS; ++l) {
+    info->cells[l][0] = mg->lv[l].nc[0];
+    info->cells[l][1] = mg->lv[l].nc[1];
+    info->cells[l][2] = mg->lv[l].nc[2];
+    info->ndofs[l] = mg->lv[l].ndofs;
+    info->lmax[l] = mg->lv[l].lmax;
+  }
+  return TP_OK;
+}
+
+tp_status tp_mg_level_op(tp_mg mg, int level, tp_op* op) {
+  if (!mg || !op || level < 0 || level >= (int)mg->lv.size()) { set_error("tp_mg_level_op: bad argument"); return TP_ERR_INVALID_ARG; }
+  *op = mg->lv[level].op;
+  return TP_OK;
+}
+
+static tp_status check_level(tp_mg mg, int level, const void* a, const void* b, const char* who, int min_level) {
+  if (!mg || !a || !b) { set_error("%s: NULL argument", who); return TP_ERR_INVALID_ARG; }
+  if (level < min_level || level >= (int)mg->lv.size()) { set_error("%s: level %d out of range", who, level); return TP_ERR_INVALID_ARG; }
+  if (((uintptr_t)a & 15) || ((uintptr_t)b & 15)) { set_error("%s: vectors must be 16-byte aligned", who); return TP_ERR_INVALID_ARG; }
+  return TP_OK;
+}
+
+tp_status tp_vcycle(tp_mg mg, void* x, const void* b, void* stream) {
+  tp_status st = check_level(mg, (int)(mg ? mg->lv.size() - 1 : 0), x, b, "tp_vcycle", 0);
+  if (st != TP_OK) return st;
+  return cuda_status(mg_vcycle(mg, (int)mg->lv.size() - 1, x, b, 0, (cudaStream_t)stream), "tp_vcycle");
+}
+
+tp_status tp_mg_smooth(tp_mg mg, int level, void* x, const void* b, void* stream) {
+  tp_status st = check_level(mg, level, x, b, "tp_mg_smooth", 1);
+  if (st != TP_OK) return st;
+  return cuda_status(mg_smooth(mg, level, x, b, 0, (cudaStream_t)stream), "tp_mg_smooth");
+}
+
+tp_status tp_mg_restrict(tp_mg mg, int level, void* coarse, const void* fine, void* stream) {
+  tp_status st = check_level(mg, level, coarse, fine, "tp_mg_restrict", 1);
+  if (st != TP_OK) return st;
+  return cuda_status(mg_restrict(mg, level, coarse, fine, (cudaStream_t)stream), "tp_mg_restrict");
+}
+
+tp_status tp_mg_prolongate_add(tp_mg mg, int level, void* fine, const void* coarse, void* stream) {
+  tp_status st = check_level(mg, level, fine, coarse, "tp_mg_prolongate_add", 1);
+  if (st != TP_OK) return st;
+  return cuda_status(mg_prolong_add(mg, level, fine, coarse, (cudaStream_t)stream), "tp_mg_prolongate_add");
+}
+
+tp_status tp_mg_coarse_solve(tp_mg mg, void* x, const void* b, void* stream) {
+  tp_status st = check_level(mg, 0, x, b, "tp_mg_coarse_solve", 0);
+  if (st != TP_OK) return st;
+  return cuda_status(mg_coarse_solve(mg, x, b, (cudaStream_t)stream), "tp_mg_coarse_solve");
+}
+
+}  // extern "C"

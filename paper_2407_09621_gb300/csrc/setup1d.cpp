@@ -162,3 +162,125 @@ Dir1D make_dir1d(const Ref1D& r, double h, int penalty_mode) {
 }
 
 }  // namespace tp
+
+namespace tp {
+
+// Global 1D DG mass M and SIPG stiffness L on nc cells of width h (dense,
+// N = nc*n square, row-major): the 1D factors of Eq. (9). L = interior
+// diagonal blocks, rank-2 neighbour blocks
+//   L^{c,c+1} = -g v1 v0^T - v1 d0^T/(2h) + d1 v0^T/(2h),  L^{c+1,c} = its transpose,
+// and boundary corrections (v0 d0^T + d0 v0^T)/(2h) at the low end,
+// -(v1 d1^T + d1 v1^T)/(2h) at the high end.
+void global_1d(const Ref1D& r, const Dir1D& d, int nc, std::vector<double>& M, std::vector<double>& L) {
+  const int n = r.n, N = nc * n;
+  M.assign((size_t)N * N, 0.0);
+  L.assign((size_t)N * N, 0.0);
+  const double hh = 0.5 / d.h;
+  for (int c = 0; c < nc; ++c)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        M[(size_t)(c * n + i) * N + c * n + j] = d.M[i * n + j];
+        L[(size_t)(c * n + i) * N + c * n + j] = d.L[i * n + j];
+      }
+  for (int c = 0; c + 1 < nc; ++c)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double v1i = i == n - 1, v0j = j == 0;
+        const double val = -d.gamma * v1i * v0j - v1i * r.d0[j] * hh + r.d1[i] * v0j * hh;
+        L[(size_t)(c * n + i) * N + (c + 1) * n + j] = val;
+        L[(size_t)((c + 1) * n + j) * N + c * n + i] = val;
+      }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double v0i = i == 0, v0j = j == 0, v1i = i == n - 1, v1j = j == n - 1;
+      L[(size_t)i * N + j] += (v0i * r.d0[j] + r.d0[i] * v0j) * hh;
+      const size_t o = (size_t)(N - n);
+      L[(o + i) * N + o + j] -= (v1i * r.d1[j] + r.d1[i] * v1j) * hh;
+    }
+}
+
+// Generalized symmetric-definite eigenproblem L V = M V diag(lam), V^T M V = I,
+// by Cholesky M = C C^T and cyclic Jacobi rotations on C^{-1} L C^{-T}.
+// Returns false if M is not positive definite. V is row-major N x N with
+// eigenvector k in column k.
+bool gen_eig(int N, const std::vector<double>& M, const std::vector<double>& L, std::vector<double>& lam,
+             std::vector<double>& V) {
+  std::vector<double> C((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = M[(size_t)i * N + j];
+      for (int k = 0; k < j; ++k) s -= C[(size_t)i * N + k] * C[(size_t)j * N + k];
+      if (i == j) {
+        if (!(s > 0)) return false;
+        C[(size_t)i * N + i] = std::sqrt(s);
+      } else {
+        C[(size_t)i * N + j] = s / C[(size_t)j * N + j];
+      }
+    }
+  // S = C^{-1} L C^{-T}: first X = C^{-1} L (forward substitution per column), then S = C^{-1} X^T
+  std::vector<double> X((size_t)N * N), S((size_t)N * N);
+  auto fwd = [&](const std::vector<double>& B, std::vector<double>& out) {  // out = C^{-1} B
+    for (int col = 0; col < N; ++col)
+      for (int i = 0; i < N; ++i) {
+        double s = B[(size_t)i * N + col];
+        for (int k = 0; k < i; ++k) s -= C[(size_t)i * N + k] * out[(size_t)k * N + col];
+        out[(size_t)i * N + col] = s / C[(size_t)i * N + i];
+      }
+  };
+  fwd(L, X);
+  std::vector<double> Xt((size_t)N * N);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) Xt[(size_t)i * N + j] = X[(size_t)j * N + i];
+  fwd(Xt, S);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double a = 0.5 * (S[(size_t)i * N + j] + S[(size_t)j * N + i]);
+      S[(size_t)i * N + j] = S[(size_t)j * N + i] = a;
+    }
+  std::vector<double> Q((size_t)N * N, 0.0);
+  for (int i = 0; i < N; ++i) Q[(size_t)i * N + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < N; ++i)
+      for (int j = 0; j < N; ++j)
+        (i == j ? diag : off) += S[(size_t)i * N + j] * S[(size_t)i * N + j];
+    if (off <= 1e-30 * diag) break;
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        const double apq = S[(size_t)p * N + q];
+        if (apq == 0.0) continue;
+        const double app = S[(size_t)p * N + p], aqq = S[(size_t)q * N + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < N; ++k) {  // rows p, q
+          const double skp = S[(size_t)k * N + p], skq = S[(size_t)k * N + q];
+          S[(size_t)k * N + p] = c * skp - s * skq;
+          S[(size_t)k * N + q] = s * skp + c * skq;
+        }
+        for (int k = 0; k < N; ++k) {  // columns p, q
+          const double spk = S[(size_t)p * N + k], sqk = S[(size_t)q * N + k];
+          S[(size_t)p * N + k] = c * spk - s * sqk;
+          S[(size_t)q * N + k] = s * spk + c * sqk;
+        }
+        for (int k = 0; k < N; ++k) {
+          const double qkp = Q[(size_t)k * N + p], qkq = Q[(size_t)k * N + q];
+          Q[(size_t)k * N + p] = c * qkp - s * qkq;
+          Q[(size_t)k * N + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  lam.assign(N, 0.0);
+  for (int i = 0; i < N; ++i) lam[i] = S[(size_t)i * N + i];
+  // V = C^{-T} Q (back substitution per column)
+  V.assign((size_t)N * N, 0.0);
+  for (int col = 0; col < N; ++col)
+    for (int i = N - 1; i >= 0; --i) {
+      double s = Q[(size_t)i * N + col];
+      for (int k = i + 1; k < N; ++k) s -= C[(size_t)k * N + i] * V[(size_t)k * N + col];
+      V[(size_t)i * N + col] = s / C[(size_t)i * N + i];
+    }
+  return true;
+}
+
+}  // namespace tp

@@ -27,6 +27,7 @@ tp_status cuda_status(int err, const char* what) {
 }
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t prepare_apply_cc(const tp_op_s* op);
 
 size_t elem_bytes(tp_precision p) {
   switch (p) {
@@ -130,20 +131,9 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   for (int d = 0; d < 3; ++d) op->dir[d] = make_dir1d(op->ref, hs[d], o.penalty);
   tp_status st = cuda_status(cudaGetDevice(&op->device), "cudaGetDevice");
   if (st != TP_OK) { delete op; return st; }
-  OpConst<double> c64;
-  fill_const(c64, op);
-  st = cuda_status(cudaMalloc(&op->dconst64, sizeof(c64)), "cudaMalloc(op constants)");
-  if (st == TP_OK) st = cuda_status(cudaMemcpy(op->dconst64, &c64, sizeof(c64), cudaMemcpyHostToDevice), "cudaMemcpy");
-  if (st == TP_OK) {
-    if (p == TP_FP64) {
-      op->dconst = op->dconst64;
-    } else {
-      OpConst<float> c32;
-      fill_const(c32, op);
-      st = cuda_status(cudaMalloc(&op->dconst, sizeof(c32)), "cudaMalloc(op constants)");
-      if (st == TP_OK) st = cuda_status(cudaMemcpy(op->dconst, &c32, sizeof(c32), cudaMemcpyHostToDevice), "cudaMemcpy");
-    }
-  }
+  fill_const(op->c64, op);
+  fill_const(op->c32, op);
+  st = cuda_status(prepare_apply_cc(op), "apply kernel set-up");
   if (st != TP_OK) {
     tp_op_destroy(op);
     return st;
@@ -167,8 +157,6 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
 
 tp_status tp_op_destroy(tp_op op) {
   if (!op) return TP_OK;
-  if (op->dconst && op->dconst != op->dconst64) cudaFree(op->dconst);
-  if (op->dconst64) cudaFree(op->dconst64);
   if (op->hx) cudaFree(op->hx);
   if (op->hy) cudaFree(op->hy);
   delete op;

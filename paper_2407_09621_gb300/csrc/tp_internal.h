@@ -35,9 +35,13 @@ struct Dir1D {
 };
 
 Dir1D make_dir1d(const Ref1D& r, double h, int penalty_mode);
+void global_1d(const Ref1D& r, const Dir1D& d, int nc, std::vector<double>& M, std::vector<double>& L);
+bool gen_eig(int N, const std::vector<double>& M, const std::vector<double>& L, std::vector<double>& lam,
+             std::vector<double>& V);
 
-// Device-side constant block shared by all apply kernels, templated on the
-// compute type. Lives in device global memory, owned by the operator.
+// 1D operator data shared by the apply kernels, templated on the compute
+// type. Passed by value as a __grid_constant__ kernel parameter (about 3 KB
+// for double), so the coefficients are read from the constant bank.
 template <typename T>
 struct OpConst {
   T M[3][kMaxN * kMaxN];
@@ -62,9 +66,10 @@ struct tp_op_s {
   tp_precision prec;
   tp_op_opts opts;
   long long ncells, ndofs;
-  void* dconst = nullptr;     // OpConst<double> or OpConst<float> on the device
-  void* dconst64 = nullptr;   // OpConst<double> (always present)
+  tp::OpConst<double> c64;    // host copies of the kernel-parameter constants
+  tp::OpConst<float> c32;
   int device = 0;
+  const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
   // host-buffer path (tp_apply_host): library-owned staging
   void* hx = nullptr; void* hy = nullptr;
   size_t hbytes = 0;

@@ -1,0 +1,208 @@
+"""GPU parity of the multigrid steps, the V-cycle and the FGMRES solve against
+the CPU oracle (oracle/mg.py, oracle/solve.py).
+
+Each step of Algorithm 2 is compared element by element with the oracle on
+the same seeded inputs and the same explicit smoother bound lmax (an input
+of both sides); the solve is compared with the exact discrete solution by
+fast diagonalization and by the L2 error rule (within 1% of the FP64 solve's
+discretization error, or at the round-off floor when that error is below
+1e-10)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.mg import VCycle, prolongation, chebyshev, jacobi_diagonal, fgmres
+from oracle.sipg import Mesh, BlockOperator
+from oracle.solve import FastDiag, rhs_sine, l2_error, sine_exact
+from tp_synth import uniform_vector
+from tests.gpu_util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+DT = {"fp64": torch.float64, "fp32": torch.float32}
+TOLS = {"fp64": 1e-12, "fp32": 1e-5}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class GpuMG:
+    def __init__(self, nc, k, prec, lmax=0.0, coarse_cells=1, degree=3):
+        from paper_2407_09621_gb300 import _lib
+        self.lib = _lib
+        self.mesh = _lib.tp_mesh_create(nc, nc, nc)
+        self.op = _lib.tp_dg_laplace_create(self.mesh, k, _lib.TP_FP64)
+        self.mg = _lib.tp_mg_create(self.op, degree=degree, lmax=lmax, coarse_cells=coarse_cells,
+                                    precision=PREC[prec])
+        self.info = _lib.tp_mg_get_info(self.mg)
+        self.dtype = DT[prec]
+
+    def vec(self, x64):
+        return torch.from_numpy(np.ascontiguousarray(x64)).to("cuda", self.dtype)
+
+    def close(self):
+        self.lib.tp_mg_destroy(self.mg)
+        self.lib.tp_op_destroy(self.op)
+        self.lib.tp_mesh_destroy(self.mesh)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 7])
+def test_transfer_matches_oracle(prec, k):
+    g = GpuMG(4, k, prec, lmax=3.0, coarse_cells=1)
+    try:
+        L = g.info["levels"]
+        for level in (L - 1, L - 2):
+            ncc = g.info["cells"][level - 1][0]
+            P = prolongation(k, ncc, ncc, ncc)
+            fine = uniform_vector(P.shape[0], seed=level)
+            coarse = uniform_vector(P.shape[1], seed=level + 50)
+            dc = torch.empty(P.shape[1], dtype=g.dtype, device="cuda")
+            g.lib.tp_mg_restrict(g.mg, level, dc.data_ptr(), g.vec(fine).data_ptr())
+            df = g.vec(fine)
+            g.lib.tp_mg_prolongate_add(g.mg, level, df.data_ptr(), g.vec(coarse).data_ptr())
+            torch.cuda.synchronize()
+            assert rel_l2(dc.double().cpu().numpy(), P.T @ fine) < TOLS[prec]
+            assert rel_l2(df.double().cpu().numpy(), fine + P @ coarse) < TOLS[prec]
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("k,nc", [(1, 2), (3, 2), (7, 1), (2, 3)])
+def test_coarse_solve_matches_fast_diagonalization(k, nc):
+    g = GpuMG(nc, k, "fp64", lmax=3.0, coarse_cells=8)
+    try:
+        assert g.info["levels"] == 1
+        b = uniform_vector(nc ** 3 * (k + 1) ** 3, seed=9)
+        x = torch.empty(len(b), dtype=torch.float64, device="cuda")
+        g.lib.tp_mg_coarse_solve(g.mg, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        assert rel_l2(x.cpu().numpy(), FastDiag(k, nc, nc, nc).solve(b)) < 1e-11
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 3, 6])
+def test_smoother_matches_oracle(prec, k):
+    nc, lmax = 4, 2.8
+    g = GpuMG(nc, k, prec, lmax=lmax, coarse_cells=2)
+    try:
+        fl = g.info["levels"] - 1
+        n = g.info["ndofs"][fl]
+        b, x0 = uniform_vector(n, seed=1), uniform_vector(n, seed=2)
+        x = g.vec(x0)
+        g.lib.tp_mg_smooth(g.mg, fl, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        A = BlockOperator(Mesh(nc, nc, nc), k)
+        ref = chebyshev(A.apply, 1.0 / jacobi_diagonal(k, nc, nc, nc), b, x0, lmax, 3, 15.0)
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-12 if prec == "fp64" else 2e-5)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,nc,cnc", [(3, 8, 1), (2, 8, 2), (7, 4, 1), (1, 16, 4)])
+def test_vcycle_matches_oracle(prec, k, nc, cnc):
+    lmax = 2.9 if k > 1 else 4.9
+    g = GpuMG(nc, k, prec, lmax=lmax, coarse_cells=cnc)
+    try:
+        n = g.info["ndofs"][-1]
+        b, x0 = uniform_vector(n, seed=3), uniform_vector(n, seed=4)
+        x = g.vec(x0)
+        g.lib.tp_vcycle(g.mg, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        mg = VCycle(k, nc, coarse_nc=cnc)
+        mg.lmax = [None] + [lmax] * (len(mg.levels) - 1)
+        ref = mg.vcycle(len(mg.levels) - 1, b, x0)
+        assert len(mg.levels) == g.info["levels"]
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-11 if prec == "fp64" else 5e-5)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("k", [1, 3, 7])
+def test_lmax_estimate_bounds_the_spectrum(k):
+    import scipy.sparse.linalg as spla
+    nc = 4
+    g = GpuMG(nc, k, "fp64", lmax=0.0, coarse_cells=2)
+    try:
+        est = g.info["lmax"][-1] / 1.1
+        A = BlockOperator(Mesh(nc, nc, nc), k)
+        dinv = 1.0 / jacobi_diagonal(k, nc, nc, nc)
+        n = len(dinv)
+        op = spla.LinearOperator((n, n), matvec=lambda v: np.sqrt(dinv) * A.apply(np.sqrt(dinv) * v))
+        exact = spla.eigsh(op, k=1, which="LA", tol=1e-8)[0][0]
+        assert 0.9 * exact <= est <= exact * (1 + 1e-6)
+        assert g.info["lmax"][-1] >= 0.99 * exact
+    finally:
+        g.close()
+
+
+def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4):
+    from paper_2407_09621_gb300 import _lib
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    mg = _lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec]) if mg_prec else None
+    solver = _lib.tp_fgmres_create(op, mg, 30)
+    try:
+        b = torch.from_numpy(rhs_sine(k, nc, nc, nc)).cuda()
+        x = torch.zeros_like(b)
+        st, info = _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), rtol, maxit)
+        torch.cuda.synchronize()
+        return x.cpu().numpy(), info
+    finally:
+        _lib.tp_solver_destroy(solver)
+        if mg:
+            _lib.tp_mg_destroy(mg)
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
+
+
+@pytest.mark.parametrize("mg_prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,nc", [(3, 16), (2, 16), (7, 8)])
+def test_fgmres_solution_matches_exact_discrete_solution(mg_prec, k, nc):
+    x, info = _solve(nc, k, mg_prec, lmax=2.9 if k > 1 else 4.9, coarse_cells=2)
+    assert info["converged"] == 1
+    assert info["true_rel_residual"] < 2e-10
+    u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+    assert rel_l2(x, u) < 1e-8
+    # same preconditioned iteration count as the oracle's FGMRES within two steps
+    mg = VCycle(k, nc, coarse_nc=2)
+    mg.lmax = [None] + [2.9 if k > 1 else 4.9] * (len(mg.levels) - 1)
+    A = BlockOperator(Mesh(nc, nc, nc), k)
+    _, its, _ = fgmres(A.apply, mg, rhs_sine(k, nc, nc, nc), rtol=1e-10)
+    assert abs(info["iterations"] - its) <= 2
+
+
+def test_fgmres_without_preconditioner_reports_not_converged():
+    from paper_2407_09621_gb300 import _lib
+    mesh = _lib.tp_mesh_create(4, 4, 4)
+    op = _lib.tp_dg_laplace_create(mesh, 3, _lib.TP_FP64)
+    solver = _lib.tp_fgmres_create(op, None, 10)
+    try:
+        b = torch.from_numpy(rhs_sine(3, 4, 4, 4)).cuda()
+        x = torch.zeros_like(b)
+        st, info = _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), 1e-12, 5, raise_on_error=False)
+        assert st == _lib.TP_ERR_NOT_CONVERGED and info["iterations"] == 5 and info["converged"] == 0
+        assert len(info["history"]) == 6 and info["history"][-1] < 1.0
+    finally:
+        _lib.tp_solver_destroy(solver)
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
+
+
+def _l2_rule(e_mixed, e_fp64):
+    if e_fp64 > 1e-10:
+        return abs(e_mixed - e_fp64) <= 0.01 * e_fp64
+    return e_mixed <= max(1.01 * e_fp64, 1e-11)
+
+
+@pytest.mark.parametrize("k,nc", [(3, 64), (7, 32)])
+def test_config3_mixed_solve_discretization_error(k, nc):
+    # Poisson problem of Sec. 7.2 at full size: FP32 V-cycle inside FP64 FGMRES;
+    # L2 error against the exact solution matches that of the exact discrete solution
+    x, info = _solve(nc, k, "fp32")
+    assert info["converged"] == 1
+    u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+    e_mixed = l2_error(x, k, nc, nc, nc, sine_exact)
+    e_exact = l2_error(u, k, nc, nc, nc, sine_exact)
+    assert _l2_rule(e_mixed, e_exact), (e_mixed, e_exact)
