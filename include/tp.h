@@ -105,6 +105,25 @@ tp_status tp_apply(tp_op op, void* y, const void* x, void* stream);
  * until tp_op_destroy. Errors as tp_apply, plus TP_ERR_OOM. */
 tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream);
 
+/* y = A x with HOST vectors, allocating no device memory. The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, such as a
+ * process whose device memory is all handed out by its own fixed pool or
+ * budget, or a caller that must not meet the allocator's latency or its
+ * out-of-memory failure mid-run. (tp_dg_laplace_create allocates no device
+ * memory either, so such a caller can build the operator and use this.)
+ * Staging goes through one static device array of 2*TP_NOALLOC_MAX_BYTES
+ * bytes (x half, y half) that every GPU loading the library holds until the
+ * process exits; vectors larger than TP_NOALLOC_MAX_BYTES bytes are rejected
+ * with TP_ERR_INVALID_ARG before any GPU work. The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. Every
+ * call shares the array: calls that overlap on the GPU (other threads, other
+ * streams) race and must be serialized by the caller. Each call overwrites
+ * both halves completely, so nothing carries over. Synchronizes `stream`
+ * before returning. Errors as tp_apply_host (never TP_ERR_OOM). */
+#define TP_NOALLOC_MAX_BYTES (8 * 1024 * 1024)
+tp_status tp_apply_host_noalloc(tp_op op, void* y_host, const void* x_host, void* stream);
+
 
 /* ------------------------------------------------------------------ multigrid
  * Geometric multigrid V-cycle of Algorithm 2 (Sec. 7.1) on the operator's box:

@@ -237,3 +237,13 @@ def tp_fgmres_solve(solver, x_ptr, b_ptr, rtol=1e-10, maxit=200, stream=0, raise
 
 def tp_solver_destroy(solver):
     _check(lib.tp_solver_destroy(solver))
+
+
+# ---------------------------------------------------------------- host apply without device allocation
+TP_NOALLOC_MAX_BYTES = 8 * 1024 * 1024
+lib.tp_apply_host_noalloc.restype = ctypes.c_int
+lib.tp_apply_host_noalloc.argtypes = [_vp, _vp, _vp, _vp]
+
+
+def tp_apply_host_noalloc(op, y_ptr, x_ptr, stream=0):
+    _check(lib.tp_apply_host_noalloc(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))

@@ -1,0 +1,48 @@
+"""tp_apply_host_noalloc: the host-buffer apply for callers that cannot call
+cudaMalloc (their device memory is all taken by their own fixed pool, or they
+must not meet the allocator mid-run). It stages through a static device array
+instead of allocating, so its results must equal those of tp_apply_host,
+which allocates its staging buffers. Two calls in a row check that nothing
+left in the shared array from one call leaks into the next. This file is
+collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from tp_synth import uniform_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,dims,k", [("fp64", (4, 3, 5), 3), ("fp32", (6, 6, 6), 2), ("fp64", (8, 8, 8), 7)])
+def test_noalloc_matches_allocating_host_apply(prec, dims, k):
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    op = DGLaplace(*dims, k, prec)
+    try:
+        assert op.ndofs * op.info["elem_bytes"] <= _lib.TP_NOALLOC_MAX_BYTES
+        for seed in (11, 12):  # two calls in a row, different inputs
+            x = torch.from_numpy(uniform_vector(op.ndofs, seed=seed)).to(op.dtype).pin_memory()
+            y_ref = torch.empty_like(x).pin_memory()
+            y_new = torch.full_like(x, float("nan")).pin_memory()
+            _lib.tp_apply_host(op.op, y_ref.data_ptr(), x.data_ptr(), 0)
+            _lib.tp_apply_host_noalloc(op.op, y_new.data_ptr(), x.data_ptr(), 0)
+            a, b = y_new.double().numpy(), y_ref.double().numpy()
+            tol = 1e-12 if prec == "fp64" else 1e-5
+            assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b)
+    finally:
+        op.close()
+
+
+def test_noalloc_rejects_vectors_beyond_the_limit():
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    op = DGLaplace(32, 32, 32, 3, "fp64")  # 2,097,152 doubles = 16 MiB > 8 MiB
+    try:
+        x = torch.zeros(op.ndofs, dtype=torch.float64)
+        y = torch.zeros_like(x)
+        st = _lib.lib.tp_apply_host_noalloc(op.op, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(x.data_ptr()), None)
+        assert st == _lib.TP_ERR_INVALID_ARG
+        assert "limit" in _lib.tp_last_error()
+    finally:
+        op.close()
