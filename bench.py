@@ -195,6 +195,44 @@ def secondary(stream):
     return out
 
 
+def solve_bench(k, nc, rtol=1e-10):
+    """Sec. 7.2 Poisson solve: FP64 FGMRES(30) with a FP32 (mixed) or FP64 V-cycle preconditioner.
+
+    Setup (hierarchy, eigenvalue estimates, Krylov storage) is outside the timed region; the timed
+    region is one tp_fgmres_solve from x0 = 0 (it synchronizes). Errors: L2 error of each solution
+    against the exact u, computed on the GPU by tp_l2_error_sines."""
+    import torch
+    from paper_2407_09621_gb300 import _lib
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    ndofs = _lib.tp_op_get_info(op)["ndofs"]
+    b = torch.empty(ndofs, dtype=torch.float64, device="cuda")
+    _lib.tp_rhs_sines(op, b.data_ptr())
+    out = {"k": k, "cells": f"{nc}^3", "dofs": ndofs, "rtol": rtol, "restart": 30}
+    for name, prec in (("mixed_fp32_vcycle", _lib.TP_FP32), ("fp64_vcycle", _lib.TP_FP64)):
+        mg = _lib.tp_mg_create(op, precision=prec)
+        solver = _lib.tp_fgmres_create(op, mg, 30)
+        x = torch.zeros_like(b)
+        _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), rtol, 2, raise_on_error=False)  # warm-up
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), rtol, 300, raise_on_error=False)
+        dt = time.perf_counter() - t0
+        err = _lib.tp_l2_error_sines(op, x.data_ptr())
+        out[name] = {"seconds": dt, "iterations": info["iterations"], "converged": info["converged"],
+                     "true_rel_residual": info["true_rel_residual"], "l2_error": err, "status": st}
+        _lib.tp_solver_destroy(solver)
+        _lib.tp_mg_destroy(mg)
+        del x
+    e64, emx = out["fp64_vcycle"]["l2_error"], out["mixed_fp32_vcycle"]["l2_error"]
+    out["speedup_mixed_vs_fp64"] = out["fp64_vcycle"]["seconds"] / out["mixed_fp32_vcycle"]["seconds"]
+    out["l2_within_rule"] = (abs(emx - e64) <= 0.01 * e64) if e64 > 1e-10 else (emx <= max(1.01 * e64, 1e-11))
+    _lib.tp_op_destroy(op)
+    _lib.tp_mesh_destroy(mesh)
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -262,6 +300,7 @@ def run_ours(args):
     if rank != 0:
         return
     extra = None if args.no_extra else secondary(stream)
+    solves = None if args.no_extra else [solve_bench(3, 128), solve_bench(7, 64)]
     cpu = oracle_sample() if world == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -281,6 +320,7 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clk,
         "extra": extra,
+        "solve": solves,
     }
     print(json.dumps(line), flush=True)
     op.close()

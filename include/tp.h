@@ -224,6 +224,24 @@ tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, double rtol, 
                           void* stream);
 tp_status tp_solver_destroy(tp_solver s);
 
+/* ------------------------------------------------------------------ Poisson problem data
+ * Manufactured problems of Sec. 7.2: u = sum_m a[m] sin(p pi x/lx) sin(q pi y/ly) sin(r pi z/lz)
+ * with (p, q, r) = pqr[3m..3m+2] >= 1, 1 <= nmodes <= 16; on the unit cube the
+ * single mode a = 1, (1, 1, 1) is the paper's u = sin(pi x) sin(pi y) sin(pi z).
+ * u vanishes on the boundary (g = 0 in Eq. (1)). a and pqr are HOST arrays. */
+
+/* b = load vector of f = -Laplace u (b_a = int f phi_a), DEVICE FP64 vector in
+ * the operator's layout, computed per mode as a tensor product of 1D load
+ * vectors (30-point Gauss per cell). Allocates and frees small device
+ * buffers; synchronizes `stream`. */
+tp_status tp_rhs_sines(tp_op op, double* b, int nmodes, const double* a, const int* pqr, void* stream);
+
+/* *err = || u_h - u ||_L2 for the DEVICE FP64 coefficient vector u_h, by
+ * per-cell tensor Gauss quadrature with k+4 points per direction (FP64).
+ * Allocates a scratch array of ncells doubles; synchronizes `stream`. */
+tp_status tp_l2_error_sines(tp_op op, const double* u_h, int nmodes, const double* a, const int* pqr, double* err,
+                            void* stream);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* tp_last_error(void);
 

@@ -247,3 +247,30 @@ lib.tp_apply_host_noalloc.argtypes = [_vp, _vp, _vp, _vp]
 
 def tp_apply_host_noalloc(op, y_ptr, x_ptr, stream=0):
     _check(lib.tp_apply_host_noalloc(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))
+
+
+# ---------------------------------------------------------------- Poisson problem data
+lib.tp_rhs_sines.restype = ctypes.c_int
+lib.tp_rhs_sines.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]
+lib.tp_l2_error_sines.restype = ctypes.c_int
+lib.tp_l2_error_sines.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _vp]
+
+
+def _modes_arrays(modes):
+    a = (ctypes.c_double * len(modes))(*[float(m[0]) for m in modes])
+    pqr = (ctypes.c_int * (3 * len(modes)))(*[int(v) for m in modes for v in m[1:4]])
+    return a, pqr
+
+
+def tp_rhs_sines(op, b_ptr, modes=((1.0, 1, 1, 1),), stream=0):
+    """modes: sequence of (a, p, q, r)."""
+    a, pqr = _modes_arrays(modes)
+    _check(lib.tp_rhs_sines(op, _vp(b_ptr), len(modes), a, pqr, _vp(stream)))
+
+
+def tp_l2_error_sines(op, u_ptr, modes=((1.0, 1, 1, 1),), stream=0):
+    a, pqr = _modes_arrays(modes)
+    out = ctypes.c_double()
+    _check(lib.tp_l2_error_sines(op, _vp(u_ptr), len(modes), a, pqr, ctypes.byref(out), _vp(stream)))
+    return out.value

@@ -206,3 +206,27 @@ def test_config3_mixed_solve_discretization_error(k, nc):
     e_mixed = l2_error(x, k, nc, nc, nc, sine_exact)
     e_exact = l2_error(u, k, nc, nc, nc, sine_exact)
     assert _l2_rule(e_mixed, e_exact), (e_mixed, e_exact)
+
+
+@pytest.mark.parametrize("k,nc", [(1, 3), (3, 4), (7, 2)])
+def test_rhs_and_l2_error_match_oracle(k, nc):
+    from oracle.solve import rhs_modes
+    from paper_2407_09621_gb300 import _lib
+    modes = [(0.7, 1, 2, 3), (-0.4, 3, 1, 1)]
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    try:
+        n = _lib.tp_op_get_info(op)["ndofs"]
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        _lib.tp_rhs_sines(op, b.data_ptr(), modes)
+        ref = rhs_modes(k, nc, nc, nc, modes)
+        assert rel_l2(b.cpu().numpy(), ref) < 1e-13
+        u = FastDiag(k, nc, nc, nc).solve(ref)
+        exact = lambda X, Y, Z: sum(a * np.sin(p * np.pi * X) * np.sin(q * np.pi * Y) * np.sin(r * np.pi * Z)
+                                    for a, p, q, r in modes)
+        e_gpu = _lib.tp_l2_error_sines(op, torch.from_numpy(u).cuda().data_ptr(), modes)
+        e_ref = l2_error(u, k, nc, nc, nc, exact)
+        assert abs(e_gpu - e_ref) <= 1e-10 * e_ref
+    finally:
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
