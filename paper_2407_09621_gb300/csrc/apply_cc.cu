@@ -1,27 +1,34 @@
 // Sum-factorized SIPG Laplace apply on the FMA pipes ("CUDA-core" kernel).
 //
-// Sec. 2.1: v = A u = sum_K P_K^T A_K P_K u, evaluated cell by cell with the
-// Kronecker form of Eq. (9). With the global 1D factors, A u is
-//   M_z (M_y (L_x u) + L_y (M_x u)) + L_z (M_y (M_x u)),
-// where L_d is block tridiagonal. The diagonal block of L_d is the interior
-// one for every cell; the off-diagonal blocks and the boundary-face
-// corrections are rank 2 in the normal direction:
-//   L^{c,c+1} w = v1 (-g w_0 - (d0.w)/(2h)) + d1 (w_0/(2h))
-//   L^{c,c-1} w = v0 (-g w_{n-1} + (d1.w)/(2h)) + d0 (-w_{n-1}/(2h))
-//   boundary at the low end  (own line u): v0 ((d0.u)/(2h)) + d0 (u_0/(2h))
-//   boundary at the high end (own line u): v1 (-(d1.u)/(2h)) + d1 (-u_{n-1}/(2h))
-// (v0, v1 are unit vectors because Gauss-Lobatto nodes include the end
-// points). Each face of a cell therefore contributes two n x n arrays
-// (alpha, beta) that are expanded along the normal after the tangential
-// masses of the directions already contracted have been applied to them.
+// Sec. 2.1, Eq. (9): with the global 1D factors (M block diagonal, L block
+// tridiagonal with the face terms) the operator is
+//   A = L_z(x)M_y(x)M_x + M_z(x)L_y(x)M_x + M_z(x)M_y(x)L_x
+//     = (M_z(x)M_y(x)M_x) * [ (M^-1 L)_x + (M^-1 L)_y + (M^-1 L)_z ],
+// the same matrix written with one mass tensor on the left. Evaluated this
+// way a cell needs six n x n contractions instead of seven, and the face
+// terms need no tangential mass (they enter before the mass tensor):
+//   w = sum_d (M_d^-1 L_d) u  along each direction d (three contractions),
+//   v = M_z M_y M_x w          (three contractions).
+// M^-1 L is block tridiagonal like L. Its diagonal block G = M^-1 L_int is
+// the same for every cell; its neighbour blocks and the boundary-face
+// corrections are rank 2 along the normal, because Gauss-Lobatto value traces
+// are unit vectors (v0 = e_0, v1 = e_{n-1}):
+//   high neighbour:  s = w_0,     sd = d0.w  ->  s*P1 + sd*P2
+//   low neighbour:   s = w_{n-1}, sd = d1.w  ->  s*Q1 + sd*Q2
+//   high boundary:   s = u_{n-1}, sd = d1.u  ->  s*B1 + sd*B2   (own line u)
+//   low boundary:    s = u_0,     sd = d0.u  ->  s*C1 + sd*C2
+// with P1 = M^-1(-g v1 + d1/2h), P2 = -M^-1 v1/2h, Q1 = M^-1(-g v0 - d0/2h),
+// Q2 = M^-1 v0/2h, B1 = -M^-1 d1/2h, B2 = -M^-1 v1/2h, C1 = M^-1 d0/2h,
+// C2 = M^-1 v0/2h (g the penalty, h the cell width normal to the face).
 //
-// Work layout: n^2 threads per cell, CPB cells per block. In each
-// contraction phase a thread owns one line of the cell along the contracted
-// direction (x, then y, then z), so every 1D-matrix coefficient is the same
-// for the whole warp: the matrices are a __grid_constant__ kernel parameter
-// and enter the FMAs as constant-bank operands. Lines move between phases
-// through shared memory. TS = storage type of the vectors, TC = arithmetic
-// type.
+// Work layout: n^2 threads per cell, CPB cells per block. In every phase a
+// thread owns one line of its cell along the direction being contracted, so
+// all threads of a warp apply the same 1D coefficients at the same time: the
+// 1D data is a __grid_constant__ kernel parameter and the coefficients are
+// constant-bank operands of the FMAs. Phases: (A) x- and y-lines of
+// w_x = G_x u + x faces and w_y = G_y u + y faces; (B) z-lines: w = w_x + w_y
+// + G_z u + z faces, then M_z w in registers; (C) y-lines: M_y; (D) x-lines:
+// M_x and the store. TS = storage type of the vectors, TC = arithmetic type.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -53,11 +60,62 @@ __host__ __device__ constexpr int cc_cells_per_block() { return (128 / (N * N)) 
 
 template <typename TC, int N>
 __host__ __device__ constexpr size_t cc_smem_bytes() {
-  return sizeof(TC) * cc_cells_per_block<N>() * (4 * N * N * N + 20 * N * N);
+  return sizeof(TC) * cc_cells_per_block<N>() * 4 * N * N * N;
 }
 
-// Face f: 0 = x-, 1 = x+, 2 = y-, 3 = y+, 4 = z-, 5 = z+; face arrays 2f = alpha, 2f+1 = beta.
-// Face-point order inside an array (slow, fast): x faces (l, j), y faces (l, i), z faces (j, i).
+// Adds the two faces of direction d to the line accumulator acc[] of a line whose own
+// values are u[] (nodes 0..N-1 along d). src_lo / src_hi: the neighbour's line or nullptr
+// at the boundary; `step` is the stride of the line inside a cell.
+template <typename TS, typename TC, int N>
+__device__ __forceinline__ void add_faces(TC (&acc)[N], const TC (&u)[N], const TS* src_lo, const TS* src_hi,
+                                          int step, const OpConst<TC>& P, int d) {
+  // high face
+  if (src_hi) {
+    TC w[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = load_as<TS, TC>(src_hi + m * step);
+    TC sd = P.d0[0] * w[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d0[m], w[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][0][i], w[0], fma(P.E[d][1][i], sd, acc[i]));
+  } else {
+    TC sd = P.d1[0] * u[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d1[m], u[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][4][i], u[N - 1], fma(P.E[d][5][i], sd, acc[i]));
+  }
+  // low face
+  if (src_lo) {
+    TC w[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = load_as<TS, TC>(src_lo + m * step);
+    TC sd = P.d1[0] * w[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d1[m], w[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][2][i], w[N - 1], fma(P.E[d][3][i], sd, acc[i]));
+  } else {
+    TC sd = P.d0[0] * u[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d0[m], u[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][6][i], u[0], fma(P.E[d][7][i], sd, acc[i]));
+  }
+}
+
+template <typename TC, int N>
+__device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A, const TC (&in)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    TC s = A[i * kMaxN] * in[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) s = fma(A[i * kMaxN + m], in[m], s);
+    out[i] = s;
+  }
+}
+
 template <typename TS, typename TC, int N>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N>())
 apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ OpConst<TC> P,
@@ -67,13 +125,11 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
-  const int cs = tid / N2, t = tid % N2;
-  TC* sU = base + cs * N3;                   // u, later c1
-  TC* sA = base + (CPB + cs) * N3;           // a = M_x u
-  TC* sB = base + (2 * CPB + cs) * N3;       // b = L_x u + x faces
-  TC* sC = base + (3 * CPB + cs) * N3;       // c2 = M_y a
-  TC* sF = base + 4 * CPB * N3 + cs * 12 * N2;                // raw face arrays (12), later z arrays final
-  TC* sT = base + 4 * CPB * N3 + CPB * 12 * N2 + cs * 8 * N2;  // y/z face arrays after M_x
+  const int cs = tid / N2, t = tid % N2, p = t / N, q = t % N;
+  TC* sU = base + cs * N3;                  // u
+  TC* sX = base + (CPB + cs) * N3;          // w_x, later M_y M_z w
+  TC* sY = base + (2 * CPB + cs) * N3;      // w_y
+  TC* sZ = base + (3 * CPB + cs) * N3;      // M_z w
 
   const long long cell = (long long)blockIdx.x * CPB + cs;
   const bool valid = cell < ncells;
@@ -81,160 +137,78 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
   const int cy = valid ? (int)((cell / nx) % ny) : 0;
   const int cz = valid ? (int)(cell / ((long long)nx * ny)) : 0;
   const TS* xc = x + (valid ? cell : 0) * N3;
+  const long long sy = (long long)nx * N3, sz = (long long)nx * ny * N3;
 
-  // ---- gather u (coalesced) and the raw traces of the six faces at face point t = (p, q)
+  // ---- gather u (coalesced)
 #pragma unroll
   for (int l = 0; l < N; ++l) sU[l * N2 + t] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
+  __syncthreads();
+
+  // ---- (A) x-line (l=p, j=q) and y-line (l=p, i=q)
   {
-    const int p = t / N, q = t % N;
+    TC u[N], w[N];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int co = d == 0 ? cx : (d == 1 ? cy : cz);
-      const int ncd = d == 0 ? nx : (d == 1 ? ny : nz);
-      const long long std_ = d == 0 ? 1LL : (d == 1 ? (long long)nx : (long long)nx * ny);
-      const int off = d == 0 ? p * N2 + q * N : (d == 1 ? p * N2 + q : p * N + q);
-      const int step = d == 0 ? 1 : (d == 1 ? N : N2);
-      const TC g = P.gamma[d], hh = P.half_inv_h[d];
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const bool nb = valid && (side ? (co < ncd - 1) : (co > 0));
-        const TS* src = (nb ? xc + (side ? std_ : -std_) * N3 : xc) + off;
-        TC w[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) w[m] = valid ? load_as<TS, TC>(src + m * step) : TC(0);
-        // value trace s and derivative trace sd of the line at the face
-        const TC s = (side == nb) ? w[0] : w[N - 1];
-        TC sd = TC(0);
-        if (side == nb) {
-#pragma unroll
-          for (int m = 0; m < N; ++m) sd = fma(P.d0[m], w[m], sd);
-        } else {
-#pragma unroll
-          for (int m = 0; m < N; ++m) sd = fma(P.d1[m], w[m], sd);
-        }
-        TC alpha, beta;
-        if (nb) {
-          alpha = side ? fma(-g, s, -hh * sd) : fma(-g, s, hh * sd);
-          beta = side ? hh * s : -hh * s;
-        } else {
-          alpha = side ? -hh * sd : hh * sd;
-          beta = side ? -hh * s : hh * s;
-        }
-        sF[(4 * d + 2 * side) * N2 + t] = alpha;
-        sF[(4 * d + 2 * side + 1) * N2 + t] = beta;
-      }
+    for (int m = 0; m < N; ++m) u[m] = sU[p * N2 + q * N + m];
+    contract<TC, N>(w, P.G[0], u);
+    if (valid) {
+      const TS* lo = cx > 0 ? xc - N3 + p * N2 + q * N : nullptr;
+      const TS* hi = cx < nx - 1 ? xc + N3 + p * N2 + q * N : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, 1, P, 0);
     }
+#pragma unroll
+    for (int i = 0; i < N; ++i) sX[p * N2 + q * N + i] = w[i];
+#pragma unroll
+    for (int m = 0; m < N; ++m) u[m] = sU[p * N2 + m * N + q];
+    contract<TC, N>(w, P.G[1], u);
+    if (valid) {
+      const TS* lo = cy > 0 ? xc - sy + p * N2 + q : nullptr;
+      const TS* hi = cy < ny - 1 ? xc + sy + p * N2 + q : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, N, P, 1);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) sY[p * N2 + j * N + q] = w[j];
   }
   __syncthreads();
 
-  // ---- M_x along the fast index of the y- and z-face arrays (8 arrays x N rows)
-  for (int w = t; w < 8 * N; w += N2) {
-    const int q = w / N, r = w % N;
-    TC row[N];
-#pragma unroll
-    for (int m = 0; m < N; ++m) row[m] = sF[(4 + q) * N2 + r * N + m];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      TC s = TC(0);
-#pragma unroll
-      for (int m = 0; m < N; ++m) s = fma(P.M[0][i * kMaxN + m], row[m], s);
-      sT[q * N2 + r * N + i] = s;
-    }
-  }
-  __syncthreads();
-
-  // ---- x contraction on x-line (l, j): a = M_x u, b = L_x u + x-face terms
+  // ---- (B) z-line (j=p, i=q): w = w_x + w_y + G_z u + z faces; then M_z w
   {
-    const int l = t / N, j = t % N;
-    TC u[N];
+    TC u[N], w[N], v[N];
 #pragma unroll
-    for (int m = 0; m < N; ++m) u[m] = sU[l * N2 + j * N + m];
-    const TC am = sF[0 * N2 + t], bm = sF[1 * N2 + t], ap = sF[2 * N2 + t], bp = sF[3 * N2 + t];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-      TC sa = TC(0), sb = TC(0);
-#pragma unroll
-      for (int m = 0; m < N; ++m) {
-        sa = fma(P.M[0][i * kMaxN + m], u[m], sa);
-        sb = fma(P.L[0][i * kMaxN + m], u[m], sb);
-      }
-      sb = fma(P.d1[i], bp, sb);
-      sb = fma(P.d0[i], bm, sb);
-      if (i == N - 1) sb += ap;
-      if (i == 0) sb += am;
-      sA[l * N2 + j * N + i] = sa;
-      sB[l * N2 + j * N + i] = sb;
+    for (int m = 0; m < N; ++m) u[m] = sU[m * N2 + t];
+    contract<TC, N>(w, P.G[2], u);
+    if (valid) {
+      const TS* lo = cz > 0 ? xc - sz + t : nullptr;
+      const TS* hi = cz < nz - 1 ? xc + sz + t : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, N2, P, 2);
     }
-  }
-  // ---- M_y along the slow index of the z-face arrays (4 arrays x N columns)
-  for (int w = t; w < 4 * N; w += N2) {
-    const int q = w / N, i = w % N;
-    TC col[N];
 #pragma unroll
-    for (int pp = 0; pp < N; ++pp) col[pp] = sT[(4 + q) * N2 + pp * N + i];
+    for (int l = 0; l < N; ++l) w[l] += sX[l * N2 + t] + sY[l * N2 + t];
+    contract<TC, N>(v, P.M[2], w);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      TC s = TC(0);
-#pragma unroll
-      for (int pp = 0; pp < N; ++pp) s = fma(P.M[1][j * kMaxN + pp], col[pp], s);
-      sF[(8 + q) * N2 + j * N + i] = s;
-    }
+    for (int l = 0; l < N; ++l) sZ[l * N2 + t] = v[l];
   }
   __syncthreads();
 
-  // ---- y contraction on y-line (l, i): c1 = M_y b + L_y a + y-face terms, c2 = M_y a
+  // ---- (C) y-line (l=p, i=q): M_y
   {
-    const int l = t / N, i = t % N;
-    TC a[N], b[N];
+    TC w[N], v[N];
 #pragma unroll
-    for (int pp = 0; pp < N; ++pp) {
-      a[pp] = sA[l * N2 + pp * N + i];
-      b[pp] = sB[l * N2 + pp * N + i];
-    }
-    const TC am = sT[0 * N2 + t], bm = sT[1 * N2 + t], ap = sT[2 * N2 + t], bp = sT[3 * N2 + t];
+    for (int m = 0; m < N; ++m) w[m] = sZ[p * N2 + m * N + q];
+    contract<TC, N>(v, P.M[1], w);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-      TC s1 = TC(0), s2 = TC(0);
-#pragma unroll
-      for (int pp = 0; pp < N; ++pp) {
-        s1 = fma(P.M[1][j * kMaxN + pp], b[pp], s1);
-        s1 = fma(P.L[1][j * kMaxN + pp], a[pp], s1);
-        s2 = fma(P.M[1][j * kMaxN + pp], a[pp], s2);
-      }
-      s1 = fma(P.d1[j], bp, s1);
-      s1 = fma(P.d0[j], bm, s1);
-      if (j == N - 1) s1 += ap;
-      if (j == 0) s1 += am;
-      sU[l * N2 + j * N + i] = s1;
-      sC[l * N2 + j * N + i] = s2;
-    }
+    for (int j = 0; j < N; ++j) sX[p * N2 + j * N + q] = v[j];
   }
   __syncthreads();
 
-  // ---- z contraction on z-line (j, i) = t: v = M_z c1 + L_z c2 + z-face terms; scatter
+  // ---- (D) x-line (l=p, j=q): M_x and scatter
   if (valid) {
-    TC c1[N], c2[N];
+    TC w[N], v[N];
 #pragma unroll
-    for (int pp = 0; pp < N; ++pp) {
-      c1[pp] = sU[pp * N2 + t];
-      c2[pp] = sC[pp * N2 + t];
-    }
-    const TC am = sF[8 * N2 + t], bm = sF[9 * N2 + t], ap = sF[10 * N2 + t], bp = sF[11 * N2 + t];
-    TS* yc = y + cell * N3;
+    for (int m = 0; m < N; ++m) w[m] = sX[p * N2 + q * N + m];
+    contract<TC, N>(v, P.M[0], w);
+    TS* yc = y + cell * N3 + p * N2 + q * N;
 #pragma unroll
-    for (int l = 0; l < N; ++l) {
-      TC s = TC(0);
-#pragma unroll
-      for (int pp = 0; pp < N; ++pp) {
-        s = fma(P.M[2][l * kMaxN + pp], c1[pp], s);
-        s = fma(P.L[2][l * kMaxN + pp], c2[pp], s);
-      }
-      s = fma(P.d1[l], bp, s);
-      s = fma(P.d0[l], bm, s);
-      if (l == N - 1) s += ap;
-      if (l == 0) s += am;
-      store_as<TS, TC>(yc + l * N2 + t, s);
-    }
+    for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, v[i]);
   }
 }
 

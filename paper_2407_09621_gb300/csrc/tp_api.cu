@@ -43,25 +43,50 @@ template <typename T>
 static void fill_const(OpConst<T>& c, const tp_op_s* op) {
   memset(&c, 0, sizeof(c));
   const int n = op->n;
+  const std::vector<double>& d0 = op->ref.d0;
+  const std::vector<double>& d1 = op->ref.d1;
   for (int d = 0; d < 3; ++d) {
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        c.M[d][i * kMaxN + j] = (T)op->dir[d].M[i * n + j];
-        c.L[d][i * kMaxN + j] = (T)op->dir[d].L[i * n + j];
+    const Dir1D& D = op->dir[d];
+    const std::vector<double> Minv = invert(n, D.M);
+    const double g = D.gamma, hh = 0.5 / D.h;
+    // M^-1 applied to the trace vectors: columns n-1 and 0 of M^-1 are M^-1 v1 and M^-1 v0
+    std::vector<double> mv0(n), mv1(n), md0(n), md1(n);
+    for (int i = 0; i < n; ++i) {
+      mv0[i] = Minv[i * n + 0];
+      mv1[i] = Minv[i * n + n - 1];
+      md0[i] = md1[i] = 0.0;
+      for (int m = 0; m < n; ++m) {
+        md0[i] += Minv[i * n + m] * d0[m];
+        md1[i] += Minv[i * n + m] * d1[m];
       }
-    c.gamma[d] = (T)op->dir[d].gamma;
-    c.half_inv_h[d] = (T)(0.5 / op->dir[d].h);
+    }
+    for (int i = 0; i < n; ++i) {
+      for (int j = 0; j < n; ++j) {
+        double gij = 0.0;
+        for (int m = 0; m < n; ++m) gij += Minv[i * n + m] * D.L[m * n + j];
+        c.M[d][i * kMaxN + j] = (T)D.M[i * n + j];
+        c.G[d][i * kMaxN + j] = (T)gij;
+      }
+      c.E[d][0][i] = (T)(-g * mv1[i] + hh * md1[i]);  // P1: high neighbour, value trace
+      c.E[d][1][i] = (T)(-hh * mv1[i]);               // P2: high neighbour, derivative trace
+      c.E[d][2][i] = (T)(-g * mv0[i] - hh * md0[i]);  // Q1: low neighbour, value trace
+      c.E[d][3][i] = (T)(hh * mv0[i]);                // Q2: low neighbour, derivative trace
+      c.E[d][4][i] = (T)(-hh * md1[i]);               // B1: high boundary, own value trace
+      c.E[d][5][i] = (T)(-hh * mv1[i]);               // B2: high boundary, own derivative trace
+      c.E[d][6][i] = (T)(hh * md0[i]);                // C1: low boundary, own value trace
+      c.E[d][7][i] = (T)(hh * mv0[i]);                // C2: low boundary, own derivative trace
+    }
   }
   for (int i = 0; i < n; ++i) {
-    c.d0[i] = (T)op->ref.d0[i];
-    c.d1[i] = (T)op->ref.d1[i];
+    c.d0[i] = (T)d0[i];
+    c.d1[i] = (T)d1[i];
   }
 }
 
-// algorithmic flops per DoF of the sum-factorized apply (FMA = 2 flops):
-// 7 n x n contractions (7n^4 FMAs per cell) + 6 derivative traces (n^3 each)
-// + tangential masses on face arrays (y: 4 n^3, z: 8 n^3) + 6 normal expansions (n^3)
-double apply_flops_per_dof(int n) { return 2.0 * (7.0 * n + 24.0); }
+// algorithmic flops per DoF of the sum-factorized apply in the inverse-mass form
+// (FMA = 2 flops): 6 n x n contractions (12n), 6 derivative traces (12), 6 faces x two
+// dense expansion vectors (24), summing the three directions (2).
+double apply_flops_per_dof(int n) { return 12.0 * n + 38.0; }
 
 }  // namespace tp
 

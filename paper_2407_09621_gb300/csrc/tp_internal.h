@@ -36,18 +36,22 @@ struct Dir1D {
 
 Dir1D make_dir1d(const Ref1D& r, double h, int penalty_mode);
 void global_1d(const Ref1D& r, const Dir1D& d, int nc, std::vector<double>& M, std::vector<double>& L);
+// inverse of a small dense n x n row-major matrix (Gauss-Jordan, partial pivoting)
+std::vector<double> invert(int n, const std::vector<double>& A);
 bool gen_eig(int N, const std::vector<double>& M, const std::vector<double>& L, std::vector<double>& lam,
              std::vector<double>& V);
 
-// 1D operator data shared by the apply kernels, templated on the compute
-// type. Passed by value as a __grid_constant__ kernel parameter (about 3 KB
-// for double), so the coefficients are read from the constant bank.
+// 1D operator data of the apply kernel, templated on the compute type.
+// Passed by value as a __grid_constant__ kernel parameter (4.7 KB for
+// double), so the coefficients are read from the constant bank. Per
+// direction d: M = h M-hat, G = M^-1 L_int, and the face expansion vectors
+// E[d][0..7] = P1, P2, Q1, Q2, B1, B2, C1, C2 (see apply_cc.cu).
 template <typename T>
 struct OpConst {
   T M[3][kMaxN * kMaxN];
-  T L[3][kMaxN * kMaxN];
+  T G[3][kMaxN * kMaxN];
   T d0[kMaxN], d1[kMaxN];
-  T gamma[3], half_inv_h[3];
+  T E[3][8][kMaxN];
 };
 
 void set_error(const char* fmt, ...);
