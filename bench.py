@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 128)")
     p.add_argument("--k", type=int, default=None, help="degree (default 3)")
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
+    p.add_argument("--solve-only", action="store_true",
+                   help="only the Sec. 7.2 Poisson solves at --k/--cells (for profiler captures)")
     return p.parse_args()
 
 
@@ -179,17 +181,19 @@ def secondary(stream):
     from paper_2407_09621_gb300 import DGLaplace
     from tp_synth import uniform_vector
     out = []
-    for k, nc, prec in [(7, 64, "fp64"), (3, 80, "fp32"), (3, 80, "fp16"), (3, 80, "bf16"),
-                        (7, 40, "fp32"), (7, 40, "fp16")]:
-        op = DGLaplace(nc, nc, nc, k, prec)
+    CC, TC = 1, 2
+    runs = [(7, 64, "fp64", CC, 0), (3, 80, "fp32", CC, 0), (3, 80, "fp16", CC, 0), (3, 80, "bf16", CC, 0),
+            (7, 40, "fp32", CC, 0), (7, 40, "fp16", CC, 0),
+            (3, 80, "fp16", TC, 0), (3, 80, "bf16", TC, 0), (3, 80, "fp32", TC, 1), (2, 107, "fp16", TC, 0)]
+    for k, nc, prec, kern, ec in runs:
+        op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec)
         x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
         y = torch.empty_like(x)
         per, _ = time_applies(op, y, x, 10, 3, stream)
         ms = statistics.mean(per)
-        out.append({"k": k, "cells": f"{nc}^3", "precision": prec, "dofs": op.ndofs, "ms": ms,
-                    "gdofs": op.ndofs / ms / 1e6,
-                    "hbm_gbs": 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6,
-                    "tflops": op.info["flops_per_dof"] * op.ndofs / ms / 1e9})
+        out.append({"k": k, "cells": f"{nc}^3", "precision": prec, "kernel": "tensor" if kern == TC else "cuda_core",
+                    "ec": ec, "dofs": op.ndofs, "ms": ms, "gdofs": op.ndofs / ms / 1e6,
+                    "hbm_gbs": 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6})
         op.close()
         del x, y
     return out
@@ -245,6 +249,9 @@ def run_ours(args):
 
     nc = args.cells or NC
     kdeg = args.k or K_DEG
+    if args.solve_only:
+        print(json.dumps({"solve_only": True, **solve_bench(kdeg, nc)}), flush=True)
+        return
     op = DGLaplace(nc, nc, nc, kdeg, args.prec)
     ndofs = op.ndofs
     if args.kernel_only:

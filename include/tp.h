@@ -56,8 +56,20 @@ typedef enum { TP_KERNEL_AUTO = 0, TP_KERNEL_CUDA_CORE = 1, TP_KERNEL_TENSOR = 2
 typedef struct {
   int penalty;  /* tp_penalty */
   int kernel;   /* tp_kernel */
-  int ec;       /* 1: error-corrected half-precision products (Algorithm 1) where supported */
+  int ec;       /* 1: error-corrected half-precision products (Algorithm 1), tensor kernel only */
+  int tc_type;  /* operand type of the tensor kernel: TP_FP16 (default) or TP_BF16; for FP16/BF16
+                   vectors it must equal the vector type */
 } tp_op_opts;
+
+/* Tensor kernel (TP_KERNEL_TENSOR): `mma.sync` m16n8k16 with FP32 accumulation for
+ * degrees k = 2, 3 (n <= 4, cells padded to 4^3): per cell W = K3 u with
+ * K3 = G_z(+)G_y(+)G_x and V = (M_z(x)M_y(x)M_x) W as dense 64 x 64 products, the
+ * rank-2 face terms added to W on the FMA pipes in FP32 between them. Vectors may
+ * be FP16/BF16 (operands = storage) or FP32 (operands rounded to tc_type; with
+ * ec = 1 every operand is split as in Algorithm 1: a = a_h + da*2^-s with
+ * s = 11 for FP16 and 8 for BF16, and a*b = a_h b_h + (da b_h + a_h db)*2^-s).
+ * BF16 vectors always use the split (8 significand bits are too few for the
+ * 5e-3 per-apply tolerance otherwise). */
 
 typedef struct tp_mesh_s* tp_mesh;
 typedef struct tp_op_s* tp_op;
@@ -151,6 +163,10 @@ typedef struct {
   int coarse_cells;  /* stop coarsening once no direction has more cells (default 4) */
   int precision;     /* TP_FP64 or TP_FP32 (default) */
   int power_iters;   /* power iterations for the lmax estimate (default 20) */
+  int kernel;        /* apply kernel of the level operators: TP_KERNEL_CUDA_CORE (default) or
+                        TP_KERNEL_TENSOR (FP32 vectors, k = 2, 3; other levels/degrees fall back) */
+  int ec;            /* tensor kernel with Algorithm 1 error correction */
+  int tc_type;       /* tensor operand type: TP_FP16 (default) or TP_BF16 */
 } tp_mg_opts;
 
 typedef struct {

@@ -39,7 +39,8 @@ lib = ctypes.CDLL(LIB_PATH)
 
 
 class tp_op_opts(ctypes.Structure):
-    _fields_ = [("penalty", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int)]
+    _fields_ = [("penalty", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
+                ("tc_type", ctypes.c_int)]
 
 
 class tp_op_info_t(ctypes.Structure):
@@ -96,9 +97,10 @@ def tp_mesh_destroy(mesh):
     _check(lib.tp_mesh_destroy(mesh))
 
 
-def tp_dg_laplace_create(mesh, k, precision, penalty=TP_PENALTY_CONFIG, kernel=TP_KERNEL_AUTO, ec=0):
+def tp_dg_laplace_create(mesh, k, precision, penalty=TP_PENALTY_CONFIG, kernel=TP_KERNEL_AUTO, ec=0,
+                         tc_type=TP_FP16):
     h = _vp()
-    opts = tp_op_opts(penalty, kernel, ec)
+    opts = tp_op_opts(penalty, kernel, ec, tc_type)
     _check(lib.tp_dg_laplace_create(ctypes.byref(h), mesh, k, precision, ctypes.byref(opts)))
     return h
 
@@ -134,7 +136,8 @@ TP_MAX_LEVELS = 16
 class tp_mg_opts(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("ratio", ctypes.c_double), ("safety", ctypes.c_double),
                 ("lmax", ctypes.c_double), ("coarse_cells", ctypes.c_int), ("precision", ctypes.c_int),
-                ("power_iters", ctypes.c_int)]
+                ("power_iters", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
+                ("tc_type", ctypes.c_int)]
 
 
 class tp_mg_info_t(ctypes.Structure):
@@ -171,9 +174,9 @@ for _name, (_res, _args) in _sig2.items():
 
 
 def tp_mg_create(op, degree=3, ratio=15.0, safety=1.1, lmax=0.0, coarse_cells=4, precision=TP_FP32,
-                 power_iters=20):
+                 power_iters=20, kernel=TP_KERNEL_CUDA_CORE, ec=0, tc_type=TP_FP16):
     h = _vp()
-    o = tp_mg_opts(degree, ratio, safety, lmax, coarse_cells, precision, power_iters)
+    o = tp_mg_opts(degree, ratio, safety, lmax, coarse_cells, precision, power_iters, kernel, ec, tc_type)
     _check(lib.tp_mg_create(ctypes.byref(h), op, ctypes.byref(o)))
     return h
 

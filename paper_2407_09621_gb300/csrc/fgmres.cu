@@ -19,7 +19,7 @@
 
 namespace tp {
 tp_status cuda_status(int err, const char* what);
-cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s);
 int mg_finest_level(const tp_mg_s* mg);
 tp_precision mg_precision(const tp_mg_s* mg);
@@ -125,7 +125,7 @@ cudaError_t norm_to_host(Ctx& c, const double* w, double* out) {
 
 // out = b - A x
 cudaError_t residual64(Ctx& c, double* out, const double* b, const double* x) {
-  cudaError_t e = launch_apply_cc(c.s->A, c.s->w, x, c.st);
+  cudaError_t e = launch_apply(c.s->A, c.s->w, x, c.st);
   const double coef[2] = {1.0, -1.0};
   const double* v[2] = {b, c.s->w};
   if (e == cudaSuccess) e = multi_axpy<double>(c.s->n, out, 0.0, v, coef, 2, c.st);
@@ -189,7 +189,7 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
       } else {
         e = cudaMemcpyAsync(s->Z[j], s->V[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st);
       }
-      if (e == cudaSuccess) e = launch_apply_cc(s->A, s->w, s->Z[j], c.st);
+      if (e == cudaSuccess) e = launch_apply(s->A, s->w, s->Z[j], c.st);
       // classical Gram-Schmidt, two passes
       if (e == cudaSuccess) e = dots_to_host(c, s->w, j + 1, h.data());
       if (e == cudaSuccess) {

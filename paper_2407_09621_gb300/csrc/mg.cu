@@ -23,7 +23,7 @@
 namespace tp {
 
 tp_status cuda_status(int err, const char* what);
-cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 size_t elem_bytes(tp_precision p);
 
 template <typename T>
@@ -390,7 +390,7 @@ cudaError_t mg_coarse_solve(const tp_mg_s* mg, void* x, const void* b, cudaStrea
 // r = b - A x  (t is scratch)
 static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, const void* b, const void* x, void* t,
                             cudaStream_t s) {
-  cudaError_t e = launch_apply_cc(L.op, t, x, s);
+  cudaError_t e = launch_apply(L.op, t, x, s);
   if (e != cudaSuccess) return e;
   const double c[2] = {1.0, -1.0};
   if (mg->prec == TP_FP64) {
@@ -416,7 +416,7 @@ cudaError_t mg_smooth(const tp_mg_s* mg, int l, void* x, const void* b, int x_ze
   if (e != cudaSuccess) return e;
   e = cheb_update(mg, L, x, L.r, L.d, nullptr, 0.0, 1.0 / theta, x_zero, s);
   for (int it = 1; it < mg->opts.degree && e == cudaSuccess; ++it) {
-    e = launch_apply_cc(L.op, L.t, L.d, s);
+    e = launch_apply(L.op, L.t, L.d, s);
     if (e != cudaSuccess) break;
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     e = cheb_update(mg, L, x, L.r, L.d, L.t, rho_new * rho, 2.0 * rho_new / delta, 0, s);
@@ -451,7 +451,7 @@ static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, do
   double rho = 0.0, h[2];
   // L.d = x, L.t = A x, L.r = D x then D^{-1} A x
   for (int it = 0; it < iters; ++it) {
-    cudaError_t e = launch_apply_cc(L.op, L.t, L.d, s);
+    cudaError_t e = launch_apply(L.op, L.t, L.d, s);
     if (e == cudaSuccess) e = dinv(mg, L, L.r, L.d, 1.0, 0, s);
     if (e == cudaSuccess) {
       if (f64) {
@@ -544,7 +544,7 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   if (!out) { set_error("tp_mg_create: out is NULL"); return TP_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!finest) { set_error("tp_mg_create: operator is NULL"); return TP_ERR_INVALID_ARG; }
-  tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20};
+  tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20, TP_KERNEL_CUDA_CORE, 0, TP_FP16};
   if (opts) o = *opts;
   if (o.degree < 1 || o.degree > 16 || !(o.ratio > 1.0) || !(o.safety > 0) || o.coarse_cells < 1 ||
       (o.precision != TP_FP64 && o.precision != TP_FP32) || o.power_iters < 1 || o.lmax < 0) {
@@ -576,13 +576,16 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   mg->lv.resize(nl);
   const size_t eb = elem_bytes(mg->prec);
   tp_status st = TP_OK;
-  tp_op_opts oo{finest->opts.penalty, TP_KERNEL_CUDA_CORE, 0};
+  tp_op_opts oo{finest->opts.penalty, o.kernel, o.ec, o.tc_type};
   for (int l = 0; l < nl && st == TP_OK; ++l) {
     tp_mg_level& L = mg->lv[l];
     const auto& sz = sizes[nl - 1 - l];
     L.nc[0] = sz[0]; L.nc[1] = sz[1]; L.nc[2] = sz[2];
     tp_mesh_s m{sz[0], sz[1], sz[2], finest->mesh.lx, finest->mesh.ly, finest->mesh.lz};
-    st = tp_dg_laplace_create(&L.op, &m, mg->k, mg->prec, &oo);
+    tp_op_opts lo = oo;
+    if (lo.kernel == TP_KERNEL_TENSOR && (mg->prec == TP_FP64 || mg->k < 2 || mg->k > 3)) lo.kernel = TP_KERNEL_CUDA_CORE;
+    if (lo.kernel != TP_KERNEL_TENSOR) lo.ec = 0;
+    st = tp_dg_laplace_create(&L.op, &m, mg->k, mg->prec, &lo);
     if (st != TP_OK) break;
     L.ndofs = L.op->ndofs;
     const size_t bytes = (size_t)L.ndofs * eb;

@@ -18,7 +18,7 @@
 namespace tp {
 
 tp_status cuda_status(int err, const char* what);
-cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 size_t elem_bytes(tp_precision p);
 
 // Two halves: x staging, then y staging. Held by every GPU that loads the
@@ -76,7 +76,7 @@ extern "C" tp_status tp_apply_host_noalloc(tp_op op, void* y_host, const void* x
   unsigned char* dy = dx + TP_NOALLOC_MAX_BYTES;
   cudaStream_t s = (cudaStream_t)stream;
   st = cuda_status(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host_noalloc H2D");
-  if (st == TP_OK) st = cuda_status(launch_apply_cc(op, dy, dx, s), "tp_apply_host_noalloc launch");
+  if (st == TP_OK) st = cuda_status(launch_apply(op, dy, dx, s), "tp_apply_host_noalloc launch");
   if (st == TP_OK)
     st = cuda_status(cudaMemcpyAsync(y_host, dy, bytes, cudaMemcpyDeviceToHost, s), "tp_apply_host_noalloc D2H");
   if (st == TP_OK) st = cuda_status(cudaStreamSynchronize(s), "tp_apply_host_noalloc sync");

@@ -28,6 +28,13 @@ tp_status cuda_status(int err, const char* what) {
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_cc(const tp_op_s* op);
+cudaError_t launch_apply_tc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t prepare_apply_tc(tp_op_s* op);
+
+// the apply kernel family chosen at creation
+cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  return op->opts.kernel == TP_KERNEL_TENSOR ? launch_apply_tc(op, y, x, s) : launch_apply_cc(op, y, x, s);
+}
 
 size_t elem_bytes(tp_precision p) {
   switch (p) {
@@ -123,7 +130,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: unknown precision %d", (int)p);
     return TP_ERR_INVALID_ARG;
   }
-  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0};
+  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16};
   if (opts) o = *opts;
   if (o.penalty != TP_PENALTY_CONFIG && o.penalty != TP_PENALTY_PAPER) {
     set_error("tp_dg_laplace_create: unknown penalty mode %d", o.penalty);
@@ -133,11 +140,23 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: unknown kernel family %d", o.kernel);
     return TP_ERR_INVALID_ARG;
   }
+  if (o.tc_type != TP_FP16 && o.tc_type != TP_BF16) {
+    set_error("tp_dg_laplace_create: tc_type must be TP_FP16 or TP_BF16");
+    return TP_ERR_INVALID_ARG;
+  }
   if (o.kernel == TP_KERNEL_TENSOR) {
-    set_error("tp_dg_laplace_create: tensor-core kernel not available for this precision/degree");
+    if (k < 2 || k > 3 || p == TP_FP64) {
+      set_error("tp_dg_laplace_create: the tensor kernel supports k = 2, 3 with FP32, FP16 or BF16 vectors");
+      return TP_ERR_UNSUPPORTED;
+    }
+    if ((p == TP_FP16 || p == TP_BF16) && o.tc_type != (int)p) o.tc_type = p;
+    // BF16 keeps 8 significand bits: without the split of Algorithm 1 the five roundings of the
+    // tensor path (input, K3, W, M3, output) exceed the 5e-3 per-apply tolerance
+    if (p == TP_BF16) o.ec = 1;
+  } else if (o.ec) {
+    set_error("tp_dg_laplace_create: error correction needs the tensor kernel");
     return TP_ERR_UNSUPPORTED;
   }
-  if (o.ec) { set_error("tp_dg_laplace_create: error correction needs the tensor-core kernel"); return TP_ERR_UNSUPPORTED; }
   const long long ncells = (long long)m->nx * m->ny * m->nz;
   const long long n3 = (long long)(k + 1) * (k + 1) * (k + 1);
   if (ncells > (1LL << 62) / n3) { set_error("tp_dg_laplace_create: DoF count overflows"); return TP_ERR_INVALID_ARG; }
@@ -148,7 +167,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   op->n = k + 1;
   op->prec = p;
   op->opts = o;
-  op->opts.kernel = TP_KERNEL_CUDA_CORE;
+  if (op->opts.kernel == TP_KERNEL_AUTO) op->opts.kernel = TP_KERNEL_CUDA_CORE;
   op->ncells = ncells;
   op->ndofs = ncells * n3;
   op->ref = make_ref1d(k);
@@ -158,7 +177,8 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   if (st != TP_OK) { delete op; return st; }
   fill_const(op->c64, op);
   fill_const(op->c32, op);
-  st = cuda_status(prepare_apply_cc(op), "apply kernel set-up");
+  st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_apply_tc(op) : prepare_apply_cc(op),
+                   "apply kernel set-up");
   if (st != TP_OK) {
     tp_op_destroy(op);
     return st;
@@ -184,6 +204,7 @@ tp_status tp_op_destroy(tp_op op) {
   if (!op) return TP_OK;
   if (op->hx) cudaFree(op->hx);
   if (op->hy) cudaFree(op->hy);
+  if (op->tc_mats) cudaFree(op->tc_mats);
   delete op;
   return TP_OK;
 }
@@ -201,7 +222,7 @@ static tp_status check_vectors(tp_op op, const void* y, const void* x, const cha
 tp_status tp_apply(tp_op op, void* y, const void* x, void* stream) {
   tp_status st = check_vectors(op, y, x, "tp_apply");
   if (st != TP_OK) return st;
-  return cuda_status(launch_apply_cc(op, y, x, (cudaStream_t)stream), "tp_apply launch");
+  return cuda_status(launch_apply(op, y, x, (cudaStream_t)stream), "tp_apply launch");
 }
 
 tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream) {
@@ -221,7 +242,7 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
   }
   cudaStream_t s = (cudaStream_t)stream;
   tp_status st = cuda_status(cudaMemcpyAsync(op->hx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host H2D");
-  if (st == TP_OK) st = cuda_status(launch_apply_cc(op, op->hy, op->hx, s), "tp_apply_host launch");
+  if (st == TP_OK) st = cuda_status(launch_apply(op, op->hy, op->hx, s), "tp_apply_host launch");
   if (st == TP_OK) st = cuda_status(cudaMemcpyAsync(y_host, op->hy, bytes, cudaMemcpyDeviceToHost, s), "tp_apply_host D2H");
   if (st == TP_OK) st = cuda_status(cudaStreamSynchronize(s), "tp_apply_host sync");
   return st;

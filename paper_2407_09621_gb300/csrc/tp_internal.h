@@ -73,6 +73,8 @@ struct tp_op_s {
   tp::OpConst<double> c64;    // host copies of the kernel-parameter constants
   tp::OpConst<float> c32;
   int device = 0;
+  void* tc_mats = nullptr;    // tensor kernel operand matrices (device)
+  int tc_blocks_per_sm = 1, sm_count = 1;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
   // host-buffer path (tp_apply_host): library-owned staging
   void* hx = nullptr; void* hy = nullptr;
