@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 128)")
     p.add_argument("--k", type=int, default=None, help="degree (default 3)")
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
+    p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
+    p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
     p.add_argument("--solve-only", action="store_true",
                    help="only the Sec. 7.2 Poisson solves at --k/--cells (for profiler captures)")
     return p.parse_args()
@@ -252,7 +254,7 @@ def run_ours(args):
     if args.solve_only:
         print(json.dumps({"solve_only": True, **solve_bench(kdeg, nc)}), flush=True)
         return
-    op = DGLaplace(nc, nc, nc, kdeg, args.prec)
+    op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=2 if args.tensor else 0, ec=1 if args.ec else 0)
     ndofs = op.ndofs
     if args.kernel_only:
         x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)

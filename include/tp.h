@@ -240,6 +240,47 @@ tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, double rtol, 
                           void* stream);
 tp_status tp_solver_destroy(tp_solver s);
 
+/* ------------------------------------------------------------------ batched solves
+ * Many independent Poisson problems of Sec. 7.2 type (manufactured sine-mode
+ * solutions, see below) with uneven sizes and degrees solved together on one GPU:
+ * every problem gets its own FP64 operator, low-precision multigrid and FGMRES at
+ * set-up; the solves then run concurrently, `streams` host worker threads with one
+ * CUDA stream each taking problems largest-first from a shared queue, every
+ * preconditioner application being one launch of the V-cycle's captured CUDA graph. */
+typedef struct {
+  int nx, ny, nz;      /* cells of the unit-cube mesh */
+  int k;               /* degree 1..7 */
+  int nmodes;          /* manufactured solution sum_m a[m] sin(p pi x) sin(q pi y) sin(r pi z) */
+  const double* a;     /* HOST, nmodes coefficients */
+  const int* pqr;      /* HOST, 3*nmodes wave numbers >= 1 */
+  double* x;           /* DEVICE FP64 output vector (ndofs) or NULL (solution discarded) */
+} tp_batch_problem;
+
+typedef struct {
+  int mg_precision;    /* TP_FP32 (default) or TP_FP64 */
+  int kernel;          /* level-operator kernel, as tp_mg_opts.kernel */
+  int ec;              /* as tp_mg_opts.ec */
+  int restart;         /* FGMRES restart (default 30) */
+  double rtol;         /* relative residual target (default 1e-10) */
+  int maxit;           /* per problem (default 300) */
+  int streams;         /* concurrent worker streams (default 8; 1 = one after another) */
+} tp_batch_opts;
+
+typedef struct {
+  int iterations, converged, status;  /* status: tp_status of that problem's solve */
+  double true_rel_residual;
+  double l2_error;                    /* || u_h - u ||_L2 against the manufactured solution */
+  double seconds;                     /* wall time of that problem's solve */
+} tp_batch_result;
+
+/* Solves all problems (set-up and error evaluation are not part of *total_seconds,
+ * the wall time of the concurrent solve phase). results: `count` entries, filled in
+ * order. Allocates and frees all per-problem objects; blocks until done. Errors:
+ * TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, or the first failing solve's status;
+ * problems that only miss the tolerance report TP_ERR_NOT_CONVERGED in their result. */
+tp_status tp_batch_solve(const tp_batch_problem* probs, int count, const tp_batch_opts* opts,
+                         tp_batch_result* results, double* total_seconds);
+
 /* ------------------------------------------------------------------ Poisson problem data
  * Manufactured problems of Sec. 7.2: u = sum_m a[m] sin(p pi x/lx) sin(q pi y/ly) sin(r pi z/lz)
  * with (p, q, r) = pqr[3m..3m+2] >= 1, 1 <= nmodes <= 16; on the unit cube the

@@ -277,3 +277,48 @@ def tp_l2_error_sines(op, u_ptr, modes=((1.0, 1, 1, 1),), stream=0):
     out = ctypes.c_double()
     _check(lib.tp_l2_error_sines(op, _vp(u_ptr), len(modes), a, pqr, ctypes.byref(out), _vp(stream)))
     return out.value
+
+
+# ---------------------------------------------------------------- batched solves
+class tp_batch_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("k", ctypes.c_int),
+                ("nmodes", ctypes.c_int), ("a", ctypes.POINTER(ctypes.c_double)),
+                ("pqr", ctypes.POINTER(ctypes.c_int)), ("x", _vp)]
+
+
+class tp_batch_opts(ctypes.Structure):
+    _fields_ = [("mg_precision", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
+                ("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("streams", ctypes.c_int)]
+
+
+class tp_batch_result(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("l2_error", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+lib.tp_batch_solve.restype = ctypes.c_int
+lib.tp_batch_solve.argtypes = [ctypes.POINTER(tp_batch_problem), ctypes.c_int, ctypes.POINTER(tp_batch_opts),
+                               ctypes.POINTER(tp_batch_result), ctypes.POINTER(ctypes.c_double)]
+
+
+def tp_batch_solve(problems, mg_precision=TP_FP32, kernel=TP_KERNEL_CUDA_CORE, ec=0, restart=30, rtol=1e-10,
+                   maxit=300, streams=8):
+    """problems: list of dicts {cells: (nx, ny, nz) or int, k, modes: [(a, p, q, r), ...], x_ptr (optional)}.
+    Returns (list of result dicts, total solve seconds)."""
+    n = len(problems)
+    arr = (tp_batch_problem * n)()
+    keep = []
+    for i, p in enumerate(problems):
+        c = p["cells"]
+        nx, ny, nz = (c, c, c) if isinstance(c, int) else c
+        a, pqr = _modes_arrays(p["modes"])
+        keep += [a, pqr]
+        arr[i] = tp_batch_problem(nx, ny, nz, p["k"], len(p["modes"]), a, pqr, _vp(p.get("x_ptr") or 0))
+    opts = tp_batch_opts(mg_precision, kernel, ec, restart, rtol, maxit, streams)
+    res = (tp_batch_result * n)()
+    total = ctypes.c_double()
+    _check(lib.tp_batch_solve(arr, n, ctypes.byref(opts), res, ctypes.byref(total)))
+    out = [{f: getattr(r, f) for f, _ in tp_batch_result._fields_} for r in res]
+    return out, total.value

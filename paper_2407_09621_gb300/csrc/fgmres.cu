@@ -39,6 +39,9 @@ struct tp_solver_s {
   double* partial = nullptr;
   double* dots = nullptr;
   std::vector<double> history;
+  // the preconditioner V-cycle (fixed input pb, output px) captured once as a CUDA graph
+  cudaGraphExec_t vcycle_graph = nullptr;
+  bool graph_tried = false;
 };
 
 using namespace tp;
@@ -51,6 +54,34 @@ static void solver_free(tp_solver_s* s) {
   if (s->px) cudaFree(s->px);
   if (s->partial) cudaFree(s->partial);
   if (s->dots) cudaFree(s->dots);
+  if (s->vcycle_graph) cudaGraphExecDestroy(s->vcycle_graph);
+}
+
+// Captures the V-cycle on a private stream (capture is not possible on the legacy default
+// stream); returns false if capture is unavailable, in which case launches stay direct.
+static bool capture_vcycle(tp_solver_s* s) {
+  s->graph_tried = true;
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return false;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    const cudaError_t e = tp::mg_vcycle(s->mg, tp::mg_finest_level(s->mg), s->px, s->pb, 1, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    ok = e == cudaSuccess && e2 == cudaSuccess && g != nullptr;
+  }
+  if (ok) ok = cudaGraphInstantiate(&s->vcycle_graph, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();  // clear a failed capture
+  if (!ok) s->vcycle_graph = nullptr;
+  return ok;
+}
+
+static cudaError_t run_vcycle(tp_solver_s* s, cudaStream_t st) {
+  if (!s->graph_tried) capture_vcycle(s);
+  if (s->vcycle_graph) return cudaGraphLaunch(s->vcycle_graph, st);
+  return tp::mg_vcycle(s->mg, tp::mg_finest_level(s->mg), s->px, s->pb, 1, st);
 }
 
 extern "C" {
@@ -176,14 +207,13 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
       // z_j = M^{-1} v_j
       if (s->mg) {
-        const int fl = mg_finest_level(s->mg);
         if (mg_precision(s->mg) == TP_FP64) {
           e = convert<double, double>(n, (double*)s->pb, s->V[j], pscale, c.st);
-          if (e == cudaSuccess) e = mg_vcycle(s->mg, fl, s->px, s->pb, 1, c.st);
+          if (e == cudaSuccess) e = run_vcycle(s, c.st);
           if (e == cudaSuccess) e = convert<double, double>(n, s->Z[j], (const double*)s->px, 1.0 / pscale, c.st);
         } else {
           e = convert<float, double>(n, (float*)s->pb, s->V[j], pscale, c.st);
-          if (e == cudaSuccess) e = mg_vcycle(s->mg, fl, s->px, s->pb, 1, c.st);
+          if (e == cudaSuccess) e = run_vcycle(s, c.st);
           if (e == cudaSuccess) e = convert<double, float>(n, s->Z[j], (const float*)s->px, 1.0 / pscale, c.st);
         }
       } else {
@@ -278,3 +308,11 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
   }
   return status;
 }
+
+namespace tp {
+// Captures the preconditioner's V-cycle graph ahead of the first solve (used by batched
+// set-up so that capture happens outside the timed, multi-threaded solve phase).
+void fgmres_prepare(tp_solver_s* s) {
+  if (s && s->mg && !s->graph_tried) capture_vcycle(s);
+}
+}  // namespace tp
