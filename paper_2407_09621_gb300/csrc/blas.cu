@@ -163,3 +163,100 @@ template cudaError_t convert<double, double>(long long, double*, const double*, 
 template cudaError_t convert<float, float>(long long, float*, const float*, double, cudaStream_t);
 
 }  // namespace tp
+
+namespace tp {
+
+// w = w - sum_q coef[q] v_q (coef on the DEVICE), then, in the same pass, partial dot products of the
+// updated w with every v_q (if with_dots) and with itself: partial[q * gridDim.x + block], q = 0..nq
+// (q = nq is |w|^2).
+template <typename T, int Q>
+__global__ void __launch_bounds__(kRedThreads) multi_axpy_dot_partial(long long n, T* w, MultiPtr<T> v,
+                                                                       const double* __restrict__ coef, int nq,
+                                                                       int with_dots, double* __restrict__ partial) {
+  __shared__ double red[Q + 1][kRedThreads / 32];
+  double c[Q], acc[Q + 1];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) c[q] = q < nq ? coef[q] : 0.0;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) acc[q] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double wi = to_d(w[i]);
+    double vi[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      vi[q] = q < nq ? to_d(v.p[q][i]) : 0.0;
+      wi = fma(-c[q], vi[q], wi);
+    }
+    w[i] = (T)wi;
+    if (with_dots) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) acc[q] = fma(wi, vi[q], acc[q]);
+    }
+    acc[Q] = fma(wi, wi, acc[Q]);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q <= Q; ++q) {
+    double s = acc[q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[q][wid] = s;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x <= nq) {
+    const int q = (int)threadIdx.x == nq ? Q : (int)threadIdx.x;
+    double s = 0.0;
+    for (int k = 0; k < kRedThreads / 32; ++k) s += red[q][k];
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out = in / sqrt(*nrm2) (nrm2 on the device)
+template <typename T>
+__global__ void scale_inv_sqrt_kernel(long long n, T* __restrict__ out, const T* __restrict__ in,
+                                      const double* __restrict__ nrm2) {
+  const double s = 1.0 / sqrt(*nrm2);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)(s * to_d(in[i]));
+}
+
+template <typename T>
+cudaError_t multi_axpy_dot(long long n, T* w, const T* const* v, const double* coef_dev, int nq, int with_dots,
+                           double* partial, double* out, cudaStream_t s) {
+  if (nq > kMaxMulti) {
+    // longer bases: axpy chunk by chunk, then one dot/norm pass
+    for (int q0 = 0; q0 < nq; q0 += kMaxMulti) {
+      const int m = nq - q0 < kMaxMulti ? nq - q0 : kMaxMulti;
+      MultiPtr<T> mp;
+      for (int q = 0; q < m; ++q) mp.p[q] = v[q0 + q];
+      multi_axpy_dot_partial<T, kMaxMulti><<<dot_blocks(n), kRedThreads, 0, s>>>(n, w, mp, coef_dev + q0, m, 0,
+                                                                                 partial);
+    }
+    cudaError_t e = with_dots ? multi_dot<T>(n, w, v, nq, partial, out, s) : cudaSuccess;
+    if (e != cudaSuccess) return e;
+    const T* self[1] = {w};
+    return multi_dot<T>(n, w, self, 1, partial, out + nq, s);
+  }
+  const int blocks = dot_blocks(n);
+  MultiPtr<T> mp;
+  for (int q = 0; q < nq; ++q) mp.p[q] = v[q];
+  if (nq <= 4)
+    multi_axpy_dot_partial<T, 4><<<blocks, kRedThreads, 0, s>>>(n, w, mp, coef_dev, nq, with_dots, partial);
+  else if (nq <= 8)
+    multi_axpy_dot_partial<T, 8><<<blocks, kRedThreads, 0, s>>>(n, w, mp, coef_dev, nq, with_dots, partial);
+  else
+    multi_axpy_dot_partial<T, kMaxMulti><<<blocks, kRedThreads, 0, s>>>(n, w, mp, coef_dev, nq, with_dots, partial);
+  reduce_partials<<<1, kRedThreads, 0, s>>>(partial, blocks, nq + 1, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scale_inv_sqrt(long long n, T* out, const T* in, const double* nrm2_dev, cudaStream_t s) {
+  scale_inv_sqrt_kernel<T><<<stream_blocks(n), 256, 0, s>>>(n, out, in, nrm2_dev);
+  return cudaGetLastError();
+}
+
+template cudaError_t multi_axpy_dot<double>(long long, double*, const double* const*, const double*, int, int,
+                                            double*, double*, cudaStream_t);
+template cudaError_t scale_inv_sqrt<double>(long long, double*, const double*, const double*, cudaStream_t);
+
+}  // namespace tp

@@ -110,8 +110,8 @@ tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart) {
     st = cuda_status(cudaMalloc(&s->pb, pbytes), "tp_fgmres_create: preconditioner vectors");
     if (st == TP_OK) st = cuda_status(cudaMalloc(&s->px, pbytes), "tp_fgmres_create: preconditioner vectors");
   }
-  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->partial, sizeof(double) * kMaxMulti * dot_blocks(s->n)), "tp_fgmres_create: scratch");
-  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->dots, sizeof(double) * (restart + 2)), "tp_fgmres_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->partial, sizeof(double) * (kMaxMulti + 1) * dot_blocks(s->n)), "tp_fgmres_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->dots, sizeof(double) * 3 * (restart + 2)), "tp_fgmres_create: scratch");
   if (st != TP_OK) {
     solver_free(s);
     delete s;
@@ -220,24 +220,24 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
         e = cudaMemcpyAsync(s->Z[j], s->V[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st);
       }
       if (e == cudaSuccess) e = launch_apply(s->A, s->w, s->Z[j], c.st);
-      // classical Gram-Schmidt, two passes
-      if (e == cudaSuccess) e = dots_to_host(c, s->w, j + 1, h.data());
-      if (e == cudaSuccess) {
-        std::vector<double> neg(j + 1);
-        for (int i = 0; i <= j; ++i) neg[i] = -h[i];
-        std::vector<const double*> v(s->V.begin(), s->V.begin() + j + 1);
-        e = multi_axpy<double>(n, s->w, 1.0, v.data(), neg.data(), j + 1, c.st);
-      }
-      if (e == cudaSuccess) e = dots_to_host(c, s->w, j + 1, h2.data());
-      if (e == cudaSuccess) {
-        std::vector<double> neg(j + 1);
-        for (int i = 0; i <= j; ++i) { neg[i] = -h2[i]; h[i] += h2[i]; }
-        std::vector<const double*> v(s->V.begin(), s->V.begin() + j + 1);
-        e = multi_axpy<double>(n, s->w, 1.0, v.data(), neg.data(), j + 1, c.st);
-      }
-      double hn = 0.0;
-      if (e == cudaSuccess) e = norm_to_host(c, s->w, &hn);
+      // classical Gram-Schmidt with one re-orthogonalization pass; the coefficients stay on the
+      // device (h at dots[0..j], h2 at dots[m+1..], |w|^2 after pass 3), one host read per step:
+      //   pass 1: h = V^T w;  pass 2: w -= V h, h2 = V^T w;  pass 3: w -= V h2, |w|^2;  v_{j+1} = w/|w|
+      std::vector<const double*> vj(s->V.begin(), s->V.begin() + j + 1);
+      double* d_h = s->dots;
+      double* d_h2 = s->dots + (m + 1);
+      double* d_n = s->dots + 2 * (m + 1);
+      if (e == cudaSuccess) e = multi_dot<double>(n, s->w, vj.data(), j + 1, s->partial, d_h, c.st);
+      if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h, j + 1, 1, s->partial, d_h2, c.st);
+      if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h2, j + 1, 0, s->partial, d_n, c.st);
+      if (e == cudaSuccess) e = scale_inv_sqrt<double>(n, s->V[j + 1], s->w, d_n + j + 1, c.st);
+      std::vector<double> hostd(3 * (m + 2));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hostd.data(), s->dots, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, c.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
       if (e != cudaSuccess) break;
+      for (int i = 0; i <= j; ++i) h[i] = hostd[i] + hostd[m + 1 + i];
+      const double hn = std::sqrt(hostd[2 * (m + 1) + j + 1]);
       for (int i = 0; i <= j; ++i) Hij(i, j) = h[i];
       Hij(j + 1, j) = hn;
       bool finite = std::isfinite(hn);
@@ -246,11 +246,6 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
         set_error("tp_fgmres_solve: non-finite value in the Arnoldi process (iteration %d)", its);
         status = TP_ERR_NONFINITE;
         break;
-      }
-      if (hn > 0) {
-        const double c1[1] = {1.0 / hn};
-        const double* v[1] = {s->w};
-        e = multi_axpy<double>(n, s->V[j + 1], 0.0, v, c1, 1, c.st);
       }
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);

@@ -38,6 +38,17 @@ struct TransferParams {
   T P[2][kMaxN * kMaxN];  // P[c][i*kMaxN + j] = phi_j((c + x_i)/2)
 };
 
+// 1/d. In FP64 a division costs many instructions of the slow FP64 pipe; instead the FP32
+// reciprocal seeds two Newton-Raphson steps r <- r + r(1 - d r) (each doubles the correct bits:
+// 24 -> 48 -> full precision).
+__device__ __forceinline__ float recip(float d) { return 1.0f / d; }
+__device__ __forceinline__ double recip(double d) {
+  double r = (double)(1.0f / (float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
 // D^{-1} at DoF (cell, l, j, i)
 template <typename T, int N>
 __device__ __forceinline__ T jacobi_inv(const JacobiParams<T>& J, long long idx) {
@@ -54,7 +65,7 @@ __device__ __forceinline__ T jacobi_inv(const JacobiParams<T>& J, long long idx)
   if (cz == 0 && l == 0) lz += J.lo[2];
   if (cz == J.nz - 1 && l == N - 1) lz += J.hi[2];
   const T mx = J.Md[0][i], my = J.Md[1][j], mz = J.Md[2][l];
-  return T(1) / (lz * my * mx + mz * ly * mx + mz * my * lx);
+  return recip(lz * my * mx + mz * ly * mx + mz * my * lx);
 }
 
 // Chebyshev update: if t: r -= t;  d = c1*d + c2*D^{-1} r (c1 == 0: d is not read);  x = (x_zero ? 0 : x) + d
@@ -652,7 +663,7 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
     if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->fdT0, sizeof(double) * tot), "tp_mg_create: coarse solve");
     if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->fdT1, sizeof(double) * tot), "tp_mg_create: coarse solve");
   }
-  if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->partial, sizeof(double) * kMaxMulti * dot_blocks(mg->lv.back().ndofs)), "tp_mg_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->partial, sizeof(double) * (kMaxMulti + 1) * dot_blocks(mg->lv.back().ndofs)), "tp_mg_create: scratch");
   if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->dots, sizeof(double) * kMaxMulti), "tp_mg_create: scratch");
   // smoother eigenvalue bounds
   for (int l = 1; l < nl && st == TP_OK; ++l) {

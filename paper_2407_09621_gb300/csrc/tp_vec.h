@@ -30,6 +30,17 @@ cudaError_t multi_dot(long long n, const T* w, const T* const* v, int nq, double
 template <typename T>
 cudaError_t multi_axpy(long long n, T* w, double beta, const T* const* v, const double* c, int nq, cudaStream_t s);
 
+// w -= sum_q coef_dev[q] v[q] (coefficients read on the device), and in the same pass
+// out[q] = v[q].w_new (if with_dots, else 0) for q < nq and out[nq] = |w_new|^2.
+// `partial` must hold (min(nq, kMaxMulti) + 1) * dot_blocks(n) doubles; out has nq + 1 entries.
+template <typename T>
+cudaError_t multi_axpy_dot(long long n, T* w, const T* const* v, const double* coef_dev, int nq, int with_dots,
+                           double* partial, double* out, cudaStream_t s);
+
+// out = in / sqrt(*nrm2_dev)
+template <typename T>
+cudaError_t scale_inv_sqrt(long long n, T* out, const T* in, const double* nrm2_dev, cudaStream_t s);
+
 // out = scale * in (with conversion).
 template <typename TO, typename TI>
 cudaError_t convert(long long n, TO* out, const TI* in, double scale, cudaStream_t s);
