@@ -278,7 +278,9 @@ def run_ours(args):
         x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)
         y = torch.empty_like(x)
         per, total_ms = time_applies(op, y, x, args.steps, args.warmup, torch.cuda.current_stream())
+        op.check()
         print(json.dumps({"kernel_only": True, "k": kdeg, "cells": nc, "prec": args.prec, "dofs": ndofs,
+                          "tensor_path": op.info["tensor_path"], "ec": int(args.ec),
                           "ms_per_apply": statistics.mean(per), "gdofs": ndofs / statistics.mean(per) / 1e6}))
         op.close()
         return

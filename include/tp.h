@@ -61,7 +61,13 @@ typedef struct {
                    vectors it must equal the vector type */
 } tp_op_opts;
 
-/* Tensor kernel (TP_KERNEL_TENSOR): `mma.sync` m16n8k16 with FP32 accumulation for
+/* Tensor kernel (TP_KERNEL_TENSOR). For k = 3 with FP16/BF16 vectors it runs on the
+ * Blackwell tensor cores (tcgen05.mma, operands staged by TMA, FP32 accumulators in
+ * TMEM): each cell row of the output is the sum of seven dense 64 x 64 blocks of
+ * Eq. (2)/(9) (the interior diagonal block and one per face neighbour) applied to
+ * the cell's and its six neighbours' coefficients, boundary faces through a ghost
+ * row; with ec = 1 (always for BF16) the blocks are split as in Algorithm 1 into
+ * a second accumulator. Otherwise `mma.sync` m16n8k16 with FP32 accumulation for
  * degrees k = 2, 3 (n <= 4, cells padded to 4^3): per cell W = K3 u with
  * K3 = G_z(+)G_y(+)G_x and V = (M_z(x)M_y(x)M_x) W as dense 64 x 64 products, the
  * rank-2 face terms added to W on the FMA pipes in FP32 between them. Vectors may
@@ -82,6 +88,7 @@ typedef struct {
   int kernel;             /* tp_kernel family tp_apply will launch */
   size_t elem_bytes;      /* bytes per vector entry */
   double flops_per_dof;   /* algorithmic flops per DoF of one tp_apply (FMA = 2) */
+  int tensor_path;        /* tensor kernel only: 2 = tcgen05 (TMA + TMEM), 1 = mma.sync; else 0 */
 } tp_op_info_t;
 
 /* Uniform Cartesian mesh of [0,lx]x[0,ly]x[0,lz] with nx*ny*nz cells
@@ -135,6 +142,14 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
  * before returning. Errors as tp_apply_host (never TP_ERR_OOM). */
 #define TP_NOALLOC_MAX_BYTES (8 * 1024 * 1024)
 tp_status tp_apply_host_noalloc(tp_op op, void* y_host, const void* x_host, void* stream);
+
+/* Device status of the op's kernels. The tcgen05 apply (k = 3 with FP16/BF16
+ * vectors on the tensor kernel) bounds every wait on its barriers; a wait that
+ * gives up stores a nonzero code in a device word owned by the op and the
+ * launch stops issuing work. This call synchronizes the device, reads and
+ * clears that word, and returns TP_ERR_TIMEOUT (code in tp_last_error()) if it
+ * was set, else TP_OK. Errors: TP_ERR_INVALID_ARG (NULL op), TP_ERR_CUDA. */
+tp_status tp_op_check(tp_op op);
 
 
 /* ------------------------------------------------------------------ multigrid

@@ -46,7 +46,8 @@ class tp_op_opts(ctypes.Structure):
 class tp_op_info_t(ctypes.Structure):
     _fields_ = [("ncells", ctypes.c_longlong), ("ndofs", ctypes.c_longlong), ("k", ctypes.c_int),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
-                ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double)]
+                ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double),
+                ("tensor_path", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -250,6 +251,14 @@ lib.tp_apply_host_noalloc.argtypes = [_vp, _vp, _vp, _vp]
 
 def tp_apply_host_noalloc(op, y_ptr, x_ptr, stream=0):
     _check(lib.tp_apply_host_noalloc(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))
+
+
+lib.tp_op_check.restype = ctypes.c_int
+lib.tp_op_check.argtypes = [_vp]
+
+
+def tp_op_check(op):
+    _check(lib.tp_op_check(op))
 
 
 # ---------------------------------------------------------------- Poisson problem data

@@ -30,10 +30,20 @@ cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStrea
 cudaError_t prepare_apply_cc(const tp_op_s* op);
 cudaError_t launch_apply_tc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_tc(tp_op_s* op);
+bool umma_supported(const tp_op_s* op);
+cudaError_t prepare_apply_umma(tp_op_s* op);
+cudaError_t launch_apply_umma(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 
 // the apply kernel family chosen at creation
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
-  return op->opts.kernel == TP_KERNEL_TENSOR ? launch_apply_tc(op, y, x, s) : launch_apply_cc(op, y, x, s);
+  if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc(op, y, x, s);
+  return op->use_umma ? launch_apply_umma(op, y, x, s) : launch_apply_tc(op, y, x, s);
+}
+
+// Tensor family: tcgen05 (TMA, TMEM) for k = 3 with FP16/BF16 vectors, mma.sync otherwise.
+static cudaError_t prepare_tensor(tp_op_s* op) {
+  op->use_umma = umma_supported(op);
+  return op->use_umma ? prepare_apply_umma(op) : prepare_apply_tc(op);
 }
 
 size_t elem_bytes(tp_precision p) {
@@ -177,7 +187,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   if (st != TP_OK) { delete op; return st; }
   fill_const(op->c64, op);
   fill_const(op->c32, op);
-  st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_apply_tc(op) : prepare_apply_cc(op),
+  st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
                    "apply kernel set-up");
   if (st != TP_OK) {
     tp_op_destroy(op);
@@ -197,7 +207,21 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->kernel = op->opts.kernel;
   info->elem_bytes = elem_bytes(op->prec);
   info->flops_per_dof = apply_flops_per_dof(op->n);
+  info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->use_umma ? 2 : 1);
   return TP_OK;
+}
+
+tp_status tp_op_check(tp_op op) {
+  if (!op) { set_error("tp_op_check: NULL op"); return TP_ERR_INVALID_ARG; }
+  tp_status st = cuda_status(cudaDeviceSynchronize(), "tp_op_check sync");
+  if (st != TP_OK || !op->umma_err) return st;
+  int code = 0;
+  st = cuda_status(cudaMemcpy(&code, op->umma_err, sizeof(int), cudaMemcpyDeviceToHost), "tp_op_check read");
+  if (st != TP_OK) return st;
+  if (code == 0) return TP_OK;
+  cudaMemset(op->umma_err, 0, sizeof(int));
+  set_error("tp_op_check: a bounded wait of the tcgen05 apply gave up (code %d)", code);
+  return TP_ERR_TIMEOUT;
 }
 
 tp_status tp_op_destroy(tp_op op) {
@@ -205,6 +229,8 @@ tp_status tp_op_destroy(tp_op op) {
   if (op->hx) cudaFree(op->hx);
   if (op->hy) cudaFree(op->hy);
   if (op->tc_mats) cudaFree(op->tc_mats);
+  if (op->umma_mats) cudaFree(op->umma_mats);
+  if (op->umma_err) cudaFree(op->umma_err);
   delete op;
   return TP_OK;
 }

@@ -54,6 +54,16 @@ struct OpConst {
   T E[3][8][kMaxN];
 };
 
+// Kernel parameters of the Blackwell tensor-core apply (apply_umma.cu).
+struct UmmaParams {
+  int nx, ny, nz;
+  long long ncells;
+  float out_scale;  // 1 / (power-of-two scale of the stored block matrices)
+  float lo_scale;   // 2^-s of Algorithm 1
+  float gh[3][4];   // high-side ghost functional for w_1 per direction
+  float gl[3][4];   // low-side ghost functional for w_{n-2}
+};
+
 void set_error(const char* fmt, ...);
 tp_status cuda_status(int err, const char* what);
 
@@ -75,6 +85,10 @@ struct tp_op_s {
   int device = 0;
   void* tc_mats = nullptr;    // tensor kernel operand matrices (device)
   int tc_blocks_per_sm = 1, sm_count = 1;
+  bool use_umma = false;        // tensor kernel runs on tcgen05 (k = 3, FP16/BF16 vectors)
+  void* umma_mats = nullptr;    // its seven block matrices (and low parts) on the device
+  int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)
+  tp::UmmaParams umma_params;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
   // host-buffer path (tp_apply_host): library-owned staging
   void* hx = nullptr; void* hy = nullptr;

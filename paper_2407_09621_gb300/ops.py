@@ -48,6 +48,10 @@ class DGLaplace:
         _lib.tp_apply_host(self.op, y.data_ptr(), x.data_ptr(), s)
         return y
 
+    def check(self):
+        """Synchronize and raise TPError if a bounded device wait of this operator gave up."""
+        _lib.tp_op_check(self.op)
+
     def close(self):
         if getattr(self, "op", None):
             _lib.tp_op_destroy(self.op)

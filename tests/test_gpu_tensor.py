@@ -30,7 +30,7 @@ def _apply_tc(dims, k, prec, x64, ec=0, tc_type=TP_FP16):
         x = to_device(x64, prec)
         y = torch.empty_like(x)
         op.apply(y, x)
-        torch.cuda.synchronize()
+        op.check()
         return to_host64(y)
     finally:
         op.close()
@@ -123,3 +123,31 @@ def test_solve_with_tensor_vcycle(ec):
         _lib.tp_mg_destroy(mg)
         _lib.tp_op_destroy(op)
         _lib.tp_mesh_destroy(mesh)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("dims", [(9, 7, 11), (16, 16, 16), (40, 40, 20), (2, 130, 3)])
+def test_tcgen05_apply_tiles(prec, dims):
+    """k = 3 with half-precision vectors runs on tcgen05: tiles of 128 cells, a ragged last
+    tile (693 cells), exact tiles (4096), more tiles than SMs (250 tiles, persistent loop),
+    and a y-stride that is not a multiple of the tile (2 x 130 x 3)."""
+    from paper_2407_09621_gb300 import DGLaplace
+    op = DGLaplace(*dims, 3, prec, kernel=TENSOR)
+    try:
+        assert op.info["tensor_path"] == 2
+    finally:
+        op.close()
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * 64, seed=41)
+    y = _apply_tc(dims, 3, prec, x)
+    assert rel_l2(y, BlockOperator(m, 3).apply(x)) < 5e-3
+
+
+@pytest.mark.parametrize("k,prec,path", [(2, "fp16", 1), (3, "fp32", 1), (3, "fp16", 2), (3, "bf16", 2)])
+def test_tensor_path_selection(k, prec, path):
+    from paper_2407_09621_gb300 import DGLaplace
+    op = DGLaplace(3, 3, 3, k, prec, kernel=TENSOR)
+    try:
+        assert op.info["tensor_path"] == path
+    finally:
+        op.close()
