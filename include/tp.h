@@ -61,7 +61,9 @@ typedef struct {
                    vectors it must equal the vector type */
 } tp_op_opts;
 
-/* Tensor kernel (TP_KERNEL_TENSOR). For k = 3 with FP16/BF16 vectors it runs on the
+/* Tensor kernel (TP_KERNEL_TENSOR). With FP64 vectors (k = 3 and k = 7 only) the six 1D
+ * contractions per cell run as `mma.sync.m8n8k4.f64` (DMMA) and the face terms on the FMA
+ * pipe, FP64 throughout. For k = 3 with FP16/BF16 vectors it runs on the
  * Blackwell tensor cores (tcgen05.mma, operands staged by TMA, FP32 accumulators in
  * TMEM): each cell row of the output is the sum of seven dense 64 x 64 blocks of
  * Eq. (2)/(9) (the interior diagonal block and one per face neighbour) applied to
@@ -88,7 +90,8 @@ typedef struct {
   int kernel;             /* tp_kernel family tp_apply will launch */
   size_t elem_bytes;      /* bytes per vector entry */
   double flops_per_dof;   /* algorithmic flops per DoF of one tp_apply (FMA = 2) */
-  int tensor_path;        /* tensor kernel only: 2 = tcgen05 (TMA + TMEM), 1 = mma.sync; else 0 */
+  int tensor_path;        /* tensor kernel only: 1 = mma.sync f16/bf16, 2 = tcgen05 (TMA + TMEM),
+                             3 = mma.sync f64 (DMMA); 0 for the CUDA-core kernel */
 } tp_op_info_t;
 
 /* Uniform Cartesian mesh of [0,lx]x[0,ly]x[0,lz] with nx*ny*nz cells

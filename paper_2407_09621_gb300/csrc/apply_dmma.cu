@@ -1,0 +1,169 @@
+// FP64 tensor-core (DMMA) SIPG apply for k = 3 and k = 7: the six n x n contractions of the
+// inverse-mass form (apply_cc.cu)
+//   w = sum_d (M_d^-1 L_d) u + face terms,   v = (M_z (x) M_y (x) M_x) w
+// run as `mma.sync.m8n8k4.f64` products, the rank-2 face terms on the FMA pipe.
+//
+// A contraction along direction d maps the n^2 lines of a cell (rows) times the 1D matrix
+// (Sec. 3: a small dense GEMM per tensor direction): D[line][i] = sum_m U[line][m] G[i][m], in
+// groups of 8 lines (M = 8), K = 4 input nodes per step, N = 8 output nodes (for n = 4 the upper
+// four columns are zero and are dropped). Each thread keeps its B fragments (the 1D matrices)
+// in registers for the whole kernel; A fragments are read from the cell tensor in shared
+// memory, which holds u, w and one temporary per cell. One warp per cell, no block-wide
+// barriers.
+//
+// On this part DMMA and DFMA issue to the same FP64 pipe (DMMA measured at 1.05 TFLOP/s, DFMA
+// at 1.19-1.25), so this kernel is the tensor-core comparator of the FP64 apply, not its
+// fastest form.
+#include "apply_common.cuh"
+
+namespace tp {
+
+namespace dmma {
+
+template <int N>
+__host__ __device__ constexpr int cells_per_block() { return N == 8 ? 4 : 8; }
+
+template <int N>
+__host__ __device__ constexpr size_t smem_bytes() { return sizeof(double) * 3 * N * N * N * cells_per_block<N>(); }
+
+// Offset of node m of line r along direction D in a cell tensor with index (l*N + j)*N + i:
+// D = 0 (x): r = l*N + j; D = 1 (y): r = l*N + i; D = 2 (z): r = j*N + i.
+template <int N, int D>
+__device__ __forceinline__ int off(int r, int m) {
+  if (D == 0) return r * N + m;
+  if (D == 1) return (r / N) * N * N + m * N + (r % N);
+  return m * N * N + r;
+}
+
+__device__ __forceinline__ void mma_f64(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+// dst[line][i] (+)= sum_m src[line][m] A[i][m] along direction D for all N^2 lines of one cell.
+// bf[ks] is this lane's B fragment A[lane/4][4 ks + lane%4] (0 for rows >= N).
+template <int N, int D, bool ACC>
+__device__ __forceinline__ void contract_dmma(double* dst, const double* src, const double (&bf)[N / 4], int lane) {
+  constexpr int G = N * N / 8;
+  const int rr = lane >> 2, cc = lane & 3, i0 = 2 * cc;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int r = g * 8 + rr;
+    double c0 = 0.0, c1 = 0.0;
+    if (ACC && i0 < N) {
+      c0 = dst[off<N, D>(r, i0)];
+      c1 = dst[off<N, D>(r, i0 + 1)];
+    }
+#pragma unroll
+    for (int ks = 0; ks < N / 4; ++ks) mma_f64(c0, c1, src[off<N, D>(r, ks * 4 + cc)], bf[ks]);
+    if (i0 < N) {
+      dst[off<N, D>(r, i0)] = c0;
+      dst[off<N, D>(r, i0 + 1)] = c1;
+    }
+  }
+}
+
+// Face terms of direction D for the lines this lane owns, added into sW.
+template <int N, int D>
+__device__ __forceinline__ void faces_dmma(double* sW, const double* sU, const double* xc, bool has_lo, bool has_hi,
+                                           long long nb, const OpConst<double>& P, int lane) {
+  constexpr int step = D == 0 ? 1 : (D == 1 ? N : N * N);
+  for (int r = lane; r < N * N; r += 32) {
+    double u[N], acc[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+      u[m] = sU[off<N, D>(r, m)];
+      acc[m] = 0.0;
+    }
+    const double* own = xc + off<N, D>(r, 0);
+    add_faces<double, double, N>(acc, u, has_lo ? own - nb : nullptr, has_hi ? own + nb : nullptr, step, P, D);
+#pragma unroll
+    for (int m = 0; m < N; ++m) sW[off<N, D>(r, m)] += acc[m];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(32 * cells_per_block<N>())
+apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __grid_constant__ OpConst<double> P,
+                  int nx, int ny, int nz, long long ncells) {
+  constexpr int CPB = cells_per_block<N>(), N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* sU = reinterpret_cast<double*>(smem_raw) + warp * 3 * N3;
+  double* sW = sU + N3;
+  double* sT = sW + N3;
+  const long long cell = (long long)blockIdx.x * CPB + warp;
+  if (cell >= ncells) return;  // whole warp; the kernel has no block-wide barrier
+  const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((long long)nx * ny));
+  const double* xc = x + cell * N3;
+
+  // B fragments of the six 1D matrices: lane holds A[lane/4][4 ks + lane%4]
+  double bG[3][N / 4], bM[3][N / 4];
+  {
+    const int io = lane >> 2, mk = lane & 3;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int ks = 0; ks < N / 4; ++ks) {
+        bG[d][ks] = io < N ? P.G[d][io * kMaxN + ks * 4 + mk] : 0.0;
+        bM[d][ks] = io < N ? P.M[d][io * kMaxN + ks * 4 + mk] : 0.0;
+      }
+  }
+  for (int e = lane; e < N3; e += 32) sU[e] = __ldg(xc + e);
+  __syncwarp();
+
+  // w = G_x u + G_y u + G_z u on the tensor cores
+  contract_dmma<N, 0, false>(sW, sU, bG[0], lane);
+  __syncwarp();
+  contract_dmma<N, 1, true>(sW, sU, bG[1], lane);
+  __syncwarp();
+  contract_dmma<N, 2, true>(sW, sU, bG[2], lane);
+  __syncwarp();
+  // + the face terms of the six faces (FMA pipe)
+  faces_dmma<N, 0>(sW, sU, xc, cx > 0, cx < nx - 1, N3, P, lane);
+  __syncwarp();
+  faces_dmma<N, 1>(sW, sU, xc, cy > 0, cy < ny - 1, (long long)nx * N3, P, lane);
+  __syncwarp();
+  faces_dmma<N, 2>(sW, sU, xc, cz > 0, cz < nz - 1, (long long)nx * ny * N3, P, lane);
+  __syncwarp();
+  // v = M_x M_y M_z w, the last contraction stored straight to y
+  contract_dmma<N, 2, false>(sT, sW, bM[2], lane);
+  __syncwarp();
+  contract_dmma<N, 1, false>(sW, sT, bM[1], lane);
+  __syncwarp();
+  contract_dmma<N, 0, false>(y + cell * N3, sW, bM[0], lane);
+}
+
+template <int N>
+static cudaError_t launch_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  constexpr int CPB = cells_per_block<N>();
+  const long long blocks = (op->ncells + CPB - 1) / CPB;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  apply_dmma_kernel<N><<<(unsigned)blocks, 32 * CPB, smem_bytes<N>(), s>>>(
+      static_cast<const double*>(x), static_cast<double*>(y), op->c64, op->mesh.nx, op->mesh.ny, op->mesh.nz,
+      op->ncells);
+  return cudaGetLastError();
+}
+
+}  // namespace dmma
+
+bool dmma_supported(const tp_op_s* op) { return op->prec == TP_FP64 && (op->n == 4 || op->n == 8); }
+
+cudaError_t prepare_apply_dmma(const tp_op_s* op) {
+  if (op->n == 4)
+    return cudaFuncSetAttribute(dmma::apply_dmma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dmma::smem_bytes<4>());
+  if (op->n == 8)
+    return cudaFuncSetAttribute(dmma::apply_dmma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dmma::smem_bytes<8>());
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_dmma(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  if (op->n == 4) return dmma::launch_n<4>(op, y, x, s);
+  if (op->n == 8) return dmma::launch_n<8>(op, y, x, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tp

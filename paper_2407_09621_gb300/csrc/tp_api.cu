@@ -31,17 +31,22 @@ cudaError_t prepare_apply_cc(const tp_op_s* op);
 cudaError_t launch_apply_tc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_tc(tp_op_s* op);
 bool umma_supported(const tp_op_s* op);
+bool dmma_supported(const tp_op_s* op);
+cudaError_t prepare_apply_dmma(const tp_op_s* op);
+cudaError_t launch_apply_dmma(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_umma(tp_op_s* op);
 cudaError_t launch_apply_umma(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 
 // the apply kernel family chosen at creation
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
   if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc(op, y, x, s);
+  if (op->prec == TP_FP64) return launch_apply_dmma(op, y, x, s);
   return op->use_umma ? launch_apply_umma(op, y, x, s) : launch_apply_tc(op, y, x, s);
 }
 
 // Tensor family: tcgen05 (TMA, TMEM) for k = 3 with FP16/BF16 vectors, mma.sync otherwise.
 static cudaError_t prepare_tensor(tp_op_s* op) {
+  if (op->prec == TP_FP64) return dmma_supported(op) ? prepare_apply_dmma(op) : cudaErrorInvalidValue;
   op->use_umma = umma_supported(op);
   return op->use_umma ? prepare_apply_umma(op) : prepare_apply_tc(op);
 }
@@ -154,9 +159,18 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: tc_type must be TP_FP16 or TP_BF16");
     return TP_ERR_INVALID_ARG;
   }
-  if (o.kernel == TP_KERNEL_TENSOR) {
-    if (k < 2 || k > 3 || p == TP_FP64) {
-      set_error("tp_dg_laplace_create: the tensor kernel supports k = 2, 3 with FP32, FP16 or BF16 vectors");
+  if (o.kernel == TP_KERNEL_TENSOR && p == TP_FP64) {
+    if (k != 3 && k != 7) {
+      set_error("tp_dg_laplace_create: the FP64 tensor (DMMA) kernel supports k = 3 and k = 7");
+      return TP_ERR_UNSUPPORTED;
+    }
+    if (o.ec) {
+      set_error("tp_dg_laplace_create: error correction applies to half-precision operands, not FP64");
+      return TP_ERR_UNSUPPORTED;
+    }
+  } else if (o.kernel == TP_KERNEL_TENSOR) {
+    if (k < 2 || k > 3) {
+      set_error("tp_dg_laplace_create: the half-precision tensor kernels support k = 2, 3");
       return TP_ERR_UNSUPPORTED;
     }
     if ((p == TP_FP16 || p == TP_BF16) && o.tc_type != (int)p) o.tc_type = p;
@@ -207,7 +221,7 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->kernel = op->opts.kernel;
   info->elem_bytes = elem_bytes(op->prec);
   info->flops_per_dof = apply_flops_per_dof(op->n);
-  info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->use_umma ? 2 : 1);
+  info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
   return TP_OK;
 }
 

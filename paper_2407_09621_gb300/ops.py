@@ -20,12 +20,14 @@ class DGLaplace:
 
     def __init__(self, nx, ny, nz, k, precision="fp64", penalty=_lib.TP_PENALTY_CONFIG,
                  kernel=_lib.TP_KERNEL_AUTO, ec=0, lengths=(1.0, 1.0, 1.0), tc_type=_lib.TP_FP16):
+        self.op = self.mesh = None
         self.prec, self.dtype = PRECISIONS[precision]
         self.mesh = _lib.tp_mesh_create(nx, ny, nz, *lengths)
         try:
             self.op = _lib.tp_dg_laplace_create(self.mesh, k, self.prec, penalty, kernel, ec, tc_type)
         except Exception:
-            _lib.tp_mesh_destroy(self.mesh)
+            mesh, self.mesh = self.mesh, None
+            _lib.tp_mesh_destroy(mesh)
             raise
         self.info = _lib.tp_op_get_info(self.op)
         self.ndofs = self.info["ndofs"]

@@ -55,3 +55,13 @@ def test_create_without_gpu_fails_loudly():
         assert e.value.status in (_lib.TP_ERR_CUDA, _lib.TP_ERR_OOM)
     finally:
         _lib.tp_mesh_destroy(m)
+
+
+def test_failed_operator_creation_releases_mesh_once():
+    """A rejected configuration raises TPError and leaves no handle to be freed twice."""
+    import gc
+    from paper_2407_09621_gb300 import DGLaplace, TPError
+    for _ in range(3):
+        with pytest.raises(TPError):
+            DGLaplace(2, 2, 2, 4, "fp64", kernel=2)  # FP64 tensor kernel: k = 3, 7 only
+        gc.collect()

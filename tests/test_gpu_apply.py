@@ -161,3 +161,55 @@ def test_config2_precision_sweep_sampled(prec, k, nc):
     cells = sample_cells(m.ncells, 512, seed=2, nx=nc, ny=nc, nz=nc)
     ref = BlockOperator(m, k).rows(x, cells)
     assert rel_l2(y.reshape(m.ncells, -1)[cells], ref) < TOL[prec]
+
+
+# ---------------------------------------------------------------- FP64 tensor-core (DMMA) kernel
+TENSOR = 2
+
+
+@pytest.mark.parametrize("k", [3, 7])
+@pytest.mark.parametrize("dims", [(1, 1, 1), (5, 3, 4), (9, 2, 1), (2, 1, 11)])
+def test_fp64_dmma_ragged_meshes(k, dims):
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * (k + 1) ** 3, seed=50 + k)
+    y = _gpu_apply(dims, k, "fp64", x, kernel=TENSOR)
+    assert rel_l2(y, BlockOperator(m, k).apply(x)) < TOL["fp64"]
+
+
+def test_fp64_dmma_full_matrix_paper_penalty_anisotropic():
+    dims, k = (4, 3, 5), 3
+    m = Mesh(*dims, 1.0, 0.5, 2.0)
+    A = assemble(m, k, "paper")
+    x = uniform_vector(A.shape[0], seed=8)
+    y = _gpu_apply(dims, k, "fp64", x, kernel=TENSOR, penalty=1, lengths=(1.0, 0.5, 2.0))
+    assert rel_l2(y, A @ x) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("k,nc", [(3, 128), (7, 64)])
+def test_config1_full_size_fp64_dmma(k, nc):
+    """The 134M-DoF configurations on the DMMA kernel: rank-1 closed form of Eq. (9) on every
+    entry, and agreement with the CUDA-core kernel on a random vector."""
+    from paper_2407_09621_gb300 import DGLaplace
+    dims = (nc, nc, nc)
+    op = DGLaplace(*dims, k, "fp64", kernel=TENSOR)
+    try:
+        assert op.info["tensor_path"] == 3
+    finally:
+        op.close()
+    xs, ys = _rank1_vectors(k, nc, seed=17)
+    y2 = _gpu_apply(dims, k, "fp64", xs, kernel=TENSOR)
+    assert rel_l2(y2, ys) < TOL["fp64"]
+    del xs, ys, y2
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * (k + 1) ** 3, seed=0)
+    cells = sample_cells(m.ncells, 1024, seed=3, nx=nc, ny=nc, nz=nc)
+    y = _gpu_apply(dims, k, "fp64", x, kernel=TENSOR)
+    ref = BlockOperator(m, k).rows(x, cells)
+    assert rel_l2(y.reshape(m.ncells, -1)[cells], ref) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 5, 6])
+def test_fp64_dmma_other_degrees_rejected(k):
+    from paper_2407_09621_gb300 import DGLaplace, TPError
+    with pytest.raises(TPError):
+        DGLaplace(2, 2, 2, k, "fp64", kernel=TENSOR)
