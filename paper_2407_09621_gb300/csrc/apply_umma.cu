@@ -16,12 +16,24 @@
 // (g the penalty, h the cell width, d0/d1 the basis derivatives at the ends). Every cell then
 // uses the same seven blocks.
 //
-// Per block of 128 threads (one block per SM, persistent over tiles of 128 cells): thread 0
-// issues the seven TMA loads and the 28 tcgen05.mma (M=128, N=64, K=16, FP32 accumulator in
-// TMEM); all threads patch ghost rows and read the accumulator back (tcgen05.ld, one cell row per
-// thread) to store 128-byte output rows. The next tile's TMA loads overlap the epilogue. With
-// error correction the block matrices are split as in Algorithm 1 into a second accumulator.
-// Every wait is bounded: on a timeout the kernel records an error code and stops issuing work.
+// One CTA per SM, persistent over tiles of 128 cells, warp-specialized so that loads, products
+// and stores of consecutive tiles overlap:
+//   warp 0      TMA producer: streams the seven input tiles of every output tile through a ring
+//               of 16 KB shared-memory slots (zero fill outside the mesh);
+//   warp 1      MMA issuer: per slot four tcgen05.mma (M = 128, N = 64, K = 16) into one of two
+//               TMEM accumulators, then tcgen05.commit releases the slot;
+//   warps 2-5   ghost patches: for tiles that hold boundary cells, read the own tile's rows and
+//               write the ghost rows into the neighbour slots before the MMA reads them;
+//   warps 6-9   epilogue: tcgen05.ld of the finished accumulator (one cell row per thread),
+//               scale, round to the storage type and store.
+// Algorithm 1 error correction splits each block matrix into a high part and the rounded
+// remainder; both products accumulate into the same FP32 accumulator. The input vector is
+// already in the operand type, so only the matrix needs the split (two products instead of
+// three), and because the matrices are normalized by a power of two (largest entry in
+// [32, 64)) the remainder needs no 2^s scaling: remainders below the FP16 normal range lose at
+// most 2^-25 in absolute value against entries of order 32.
+// Every wait is bounded: on a timeout the kernel records an error code, the other roles stop at
+// their next wait, in-flight copies and products are drained (bounded) and TMEM is released.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -43,24 +55,73 @@ namespace umma {
 constexpr int kRows = 128;            // cells per tile (UMMA M)
 constexpr int kTileBytes = kRows * 128;
 constexpr int kMatBytes = 64 * 128;   // one 64 x 64 16-bit block matrix
+constexpr int kThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-5 patches, warps 6-9 epilogue
+constexpr int kWaitLimit = 1 << 22;
 
 using Params = UmmaParams;
 
+template <bool EC>
+__host__ __device__ constexpr int nmat() { return EC ? 14 : 7; }
+// ring slots that fit beside the block matrices in 227 KB of shared memory
+template <bool EC>
+__host__ __device__ constexpr int nslots() { return EC ? 7 : 10; }
+template <bool EC>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kTileBytes + 8 * (3 * nslots<EC>() + 5) + 16;
+}
+
 __device__ __forceinline__ uint32_t s2u(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t phase, int* err, int code) {
-  for (int it = 0; it < (1 << 24); ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(phase)
-        : "memory");
-    if (ok) return true;
-    if (it > 64) __nanosleep(32);
+__device__ __forceinline__ bool try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait (about one second, and at most kWaitLimit polls) for the phase of `bar` with
+// the given parity. Gives up early when another role has raised the abort flag; on its own
+// timeout it raises the flag and records `code`.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort, int* err, int code) {
+  if (try_wait(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (int it = 0; it < kWaitLimit; ++it) {
+    if (try_wait(bar, parity)) return true;
+    if ((it & 31) == 31) {
+      if (*abort) return false;
+      if (now_ns() - t0 > 1000000000ull) break;
+      __nanosleep(64);
+    }
   }
+  *abort = 1;
   atomicExch(err, code);
   return false;
+}
+
+// Bounded wait that ignores the abort flag (draining work already issued).
+__device__ __forceinline__ void drain_bar(uint32_t bar, uint32_t parity, int* err, int code) {
+  const uint64_t t0 = now_ns();
+  for (int it = 0; it < kWaitLimit; ++it) {
+    if (try_wait(bar, parity)) return;
+    if ((it & 31) == 31) {
+      if (now_ns() - t0 > 1000000000ull) break;
+      __nanosleep(64);
+    }
+  }
+  atomicExch(err, code);
+}
+
+__device__ __forceinline__ void arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
 // UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
@@ -141,36 +202,66 @@ __device__ __forceinline__ void write_ghost(unsigned char* tile, int r, const fl
   }
 }
 
+// Which of the seven input tiles of the tile starting at cell c0 need ghost patches: bit b
+// (1..6 = x-, x+, y-, y+, z-, z+) if a cell of the tile lies on that side of the mesh, bit 0 if
+// any does (the patch warps then also read the own tile).
+__device__ __forceinline__ uint32_t tile_bmask(long long c0, const Params& P) {
+  const long long c1 = (c0 + kRows < P.ncells ? c0 + kRows : P.ncells) - 1;
+  const long long nx = P.nx, ny = P.ny, nxy = nx * ny;
+  uint32_t m = 0;
+  if ((c1 / nx) * nx >= c0) m |= 1u << 1;                 // cx == 0
+  if (((c1 + 1) / nx) * nx >= c0 + 1) m |= 1u << 2;       // cx == nx-1
+  const long long q0 = c0 / nx, q1 = c1 / nx;             // rows of cells along y (all slabs)
+  if ((q1 / ny) * ny >= q0) m |= 1u << 3;                 // cy == 0
+  if (((q1 + 1) / ny) * ny >= q0 + 1) m |= 1u << 4;       // cy == ny-1
+  if (c0 < nxy) m |= 1u << 5;                             // cz == 0
+  if (c1 >= (long long)(P.nz - 1) * nxy) m |= 1u << 6;    // cz == nz-1
+  return m ? (m | 1u) : 0u;
+}
+
 template <typename TO, bool EC>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, const TO* __restrict__ mats,
                   const __grid_constant__ Params P, int* __restrict__ err) {
-  constexpr int NMAT = EC ? 14 : 7;
-  constexpr uint32_t TCOLS = EC ? 128 : 64;
+  constexpr int NMAT = nmat<EC>(), S = nslots<EC>();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sB = base;                          // NMAT block matrices, [out n][in k], swizzled
-  unsigned char* sA = base + NMAT * kMatBytes;       // 7 input tiles (own, x-, x+, y-, y+, z-, z+)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 7 * kTileBytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
-  int* sflag = reinterpret_cast<int*>(tslot + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const uint32_t bar_tma = s2u(&bars[0]), bar_mma = s2u(&bars[1]);
-  const long long sy = P.nx, sz = (long long)P.nx * P.ny;
-  const long long offs[7] = {0, -1, 1, -sy, sy, -sz, sz};
+  unsigned char* sB = base;                      // NMAT block matrices, [out n][in k], swizzled
+  unsigned char* sA = base + NMAT * kMatBytes;   // S input-tile slots
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kTileBytes);
+  // full[S] (TMA landed), ready[S] (ghost rows written), empty[S] (MMAs done with the slot),
+  // accf[2] (accumulator complete), acce[2] (accumulator read), drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 5);
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t bar0 = s2u(bars);
+  auto full = [&](int s) { return bar0 + 8u * s; };
+  auto ready = [&](int s) { return bar0 + 8u * (S + s); };
+  auto empty = [&](int s) { return bar0 + 8u * (2 * S + s); };
+  auto accf = [&](int a) { return bar0 + 8u * (3 * S + a); };
+  auto acce = [&](int a) { return bar0 + 8u * (3 * S + 2 + a); };
+  const uint32_t drain = bar0 + 8u * (3 * S + 4);
 
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_tma));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_mma));
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(ready(s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
+    }
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(a)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(acce(a)));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    *sflag = 0;
+    *abort = 0;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(TCOLS));
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(128));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   // block matrices -> shared, swizzled
-  for (int e = tid; e < NMAT * 64 * 8; e += 128) {
+  for (int e = tid; e < NMAT * 64 * 8; e += kThreads) {
     const int m = e >> 9, n = (e >> 3) & 63, c = e & 7;
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(mats + ((size_t)m * 64 + n) * 64) + c);
     *reinterpret_cast<uint4*>(sB + m * kMatBytes + sw_off(n, c)) = v;
@@ -179,109 +270,150 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-
   const long long ntiles = (P.ncells + kRows - 1) / kRows;
-  // idesc: D F32, A/B F16 (0) or BF16 (1), K-major, N = 64, M = 128
-  const uint32_t fmt = std::is_same<TO, __nv_bfloat16>::value ? 1u : 0u;
-  const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-  auto issue_tma = [&](long long t) {
-    if (tid == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar_tma), "r"(7 * kTileBytes)
-                   : "memory");
-      const long long c0 = t * kRows;
-#pragma unroll
-      for (int b = 0; b < 7; ++b) {
-        const int row = (int)(c0 + offs[b]);  // may be negative or past the end: zero fill
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-            ::"r"(s2u(sA + b * kTileBytes)), "l"((uint64_t)&tmx), "r"(0), "r"(row), "r"(bar_tma)
-            : "memory");
-      }
-    }
-  };
+  const long long sy = P.nx, sz = (long long)P.nx * P.ny;
 
-  uint32_t phase = 0;
-  bool ok = true;
-  if (blockIdx.x < ntiles) issue_tma(blockIdx.x);
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const long long c0 = t * kRows;
-    ok = __syncthreads_and(wait_bar(bar_tma, phase, err, 1)) != 0;
-    if (!ok) {
-      wait_bar(bar_tma, phase, err, 4);  // let copies in flight land before the block leaves
-      break;
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      const long long offs[7] = {0, -1, 1, -sy, sy, -sz, sz};
+      int slot = 0;
+      uint32_t ph = 0, issued = 0, iph = 0;  // per-slot: issued at least once, parity of the last issue
+      bool ok = true;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int b = 0; b < 7; ++b) {
+          if (!(ok = wait_bar(empty(slot), ph ^ 1u, abort, err, 1))) break;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(slot)), "r"(kTileBytes)
+                       : "memory");
+          const int row = (int)(t * kRows + offs[b]);  // may be negative or past the end: zero fill
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+              ::"r"(s2u(sA + slot * kTileBytes)), "l"((uint64_t)&tmx), "r"(0), "r"(row), "r"(full(slot))
+              : "memory");
+          issued |= 1u << slot;
+          iph = (iph & ~(1u << slot)) | (ph << slot);
+          if (++slot == S) { slot = 0; ph ^= 1u; }
+        }
+      }
+      // let every copy in flight land before the CTA can leave
+      for (int s = 0; s < S; ++s)
+        if (issued >> s & 1u) drain_bar(full(s), (iph >> s) & 1u, err, 5);
     }
-    // ---- ghost rows for boundary faces (thread = tile row)
-    {
-      const long long cell = c0 + tid;
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t fmt = std::is_same<TO, __nv_bfloat16>::value ? 1u : 0u;
+      // D F32, A/B F16 (0) or BF16 (1), both K-major, N = 64, M = 128
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+      int slot = 0, it = 0;
+      uint32_t ph = 0, rdy = 0;  // rdy: per-slot parity of the ready barriers (used only when patched)
+      bool ok = true;
+      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        const int a = it & 1;
+        if (!(ok = wait_bar(acce(a), ((it >> 1) & 1) ^ 1u, abort, err, 2))) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const uint32_t bm = tile_bmask(t * kRows, P);
+        const uint32_t dt = tmem + 64u * a;
+        for (int b = 0; b < 7; ++b) {
+          if (bm >> b & 1u) {
+            ok = wait_bar(ready(slot), (rdy >> slot) & 1u, abort, err, 3);
+            rdy ^= 1u << slot;
+          } else {
+            ok = wait_bar(full(slot), ph, abort, err, 3);
+          }
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t ad = sw128_desc(s2u(sA + slot * kTileBytes) + ks * 32);
+            const uint64_t bd = sw128_desc(s2u(sB + b * kMatBytes) + ks * 32);
+            const uint32_t acc = (b | ks) != 0;
+            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                         ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            if (EC) {
+              const uint64_t bl = sw128_desc(s2u(sB + (7 + b) * kMatBytes) + ks * 32);
+              asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                           ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc), "r"(1u));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(slot))
+                       : "memory");
+          if (++slot == S) { slot = 0; ph ^= 1u; }
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(accf(a))
+                     : "memory");
+      }
+      // every product issued so far has finished before TMEM is released
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(drain)
+                   : "memory");
+      drain_bar(drain, 0, err, 6);
+    }
+  } else if (warp < 6) {
+    // ---------------------------------------------------------------- ghost patches
+    const int row = tid - 64;
+    int slot = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const uint32_t bm = tile_bmask(t * kRows, P);
+      if (!bm) {
+        slot += 7;
+        while (slot >= S) { slot -= S; ph ^= 1u; }
+        continue;
+      }
+      const long long cell = t * kRows + row;
+      bool bnd[6] = {false, false, false, false, false, false};
       if (cell < P.ncells) {
         const int cx = (int)(cell % P.nx), cy = (int)((cell / P.nx) % P.ny), cz = (int)(cell / sz);
-        const bool bnd[6] = {cx == 0, cx == P.nx - 1, cy == 0, cy == P.ny - 1, cz == 0, cz == P.nz - 1};
-        if (bnd[0] | bnd[1] | bnd[2] | bnd[3] | bnd[4] | bnd[5]) {
-          float u[64];
+        bnd[0] = cx == 0; bnd[1] = cx == P.nx - 1;
+        bnd[2] = cy == 0; bnd[3] = cy == P.ny - 1;
+        bnd[4] = cz == 0; bnd[5] = cz == P.nz - 1;
+      }
+      const bool any = bnd[0] | bnd[1] | bnd[2] | bnd[3] | bnd[4] | bnd[5];
+      float u[64];
+      if (!(ok = wait_bar(full(slot), ph, abort, err, 4))) break;
+      if (any) {
+        const unsigned char* own = sA + slot * kTileBytes;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const uint4 v = *reinterpret_cast<const uint4*>(sA + sw_off(tid, c));
-            const TO* h = reinterpret_cast<const TO*>(&v);
+        for (int c = 0; c < 8; ++c) {
+          const uint4 v = *reinterpret_cast<const uint4*>(own + sw_off(row, c));
+          const TO* h = reinterpret_cast<const TO*>(&v);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) u[c * 8 + q] = to_f<TO>(h[q]);
-          }
-#pragma unroll
-          for (int f = 0; f < 6; ++f)
-            if (bnd[f]) write_ghost<TO>(sA + (1 + f) * kTileBytes, tid, u, f >> 1, f & 1, P);
+          for (int q = 0; q < 8; ++q) u[c * 8 + q] = to_f<TO>(h[q]);
         }
       }
-    }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    // ---- 7 blocks x 4 k-steps into TMEM (and the low parts into the second accumulator)
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      arrive(ready(slot));
+      if (++slot == S) { slot = 0; ph ^= 1u; }
 #pragma unroll
-      for (int b = 0; b < 7; ++b)
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ad = sw128_desc(s2u(sA + b * kTileBytes) + ks * 32);
-          const uint64_t bd = sw128_desc(s2u(sB + b * kMatBytes) + ks * 32);
-          const uint32_t acc = (b | ks) != 0;
-          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                       ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          if (EC) {
-            const uint64_t bl = sw128_desc(s2u(sB + (7 + b) * kMatBytes) + ks * 32);
-            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(tmem + 64), "l"(ad), "l"(bl), "r"(idesc), "r"(acc));
-          }
+      for (int b = 1; b < 7; ++b) {
+        if (bm >> b & 1u) {
+          if (!(ok = wait_bar(full(slot), ph, abort, err, 4))) break;
+          if (bnd[b - 1]) write_ghost<TO>(sA + slot * kTileBytes, row, u, (b - 1) >> 1, (b - 1) & 1, P);
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          arrive(ready(slot));
         }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar_mma)
-                   : "memory");
+        if (++slot == S) { slot = 0; ph ^= 1u; }
+      }
     }
-    ok = __syncthreads_and(wait_bar(bar_mma, phase, err, 2)) != 0;
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok) {
-      // the MMAs may still be running: wait (bounded) before anything is released
-      wait_bar(bar_mma, phase, err, 3);
-      break;
-    }
-    phase ^= 1;
-    // the input tiles are free: start the next tile's loads under the epilogue
-    if (t + gridDim.x < ntiles) issue_tma(t + gridDim.x);
-    // ---- epilogue: one cell row per thread
-    {
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q4 = warp & 3;  // this warp may read TMEM lanes 32*q4 .. 32*q4+31
+    const int row = 32 * q4 + lane;
+    int it = 0;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int a = it & 1;
+      // warp-uniform decision: the TMEM loads below are .sync.aligned
+      if (!__all_sync(0xffffffffu, wait_bar(accf(a), (it >> 1) & 1, abort, err, 7))) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       uint32_t r[64];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * a;
       TP_LD32(r, 0, ta);
       TP_LD32(r, 32, ta + 32);
-      float v[64];
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-      for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c]);
-      if (EC) {
-        TP_LD32(r, 0, ta + 64);
-        TP_LD32(r, 32, ta + 96);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-        for (int c = 0; c < 64; ++c) v[c] = fmaf(__uint_as_float(r[c]), P.lo_scale, v[c]);
-      }
-      const long long cell = c0 + tid;
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      arrive(acce(a));
+      const long long cell = t * kRows + row;
       if (cell < P.ncells) {
         uint4* dst = reinterpret_cast<uint4*>(y + cell * 64);
 #pragma unroll
@@ -289,22 +421,17 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
           uint4 o;
           TO* h = reinterpret_cast<TO*>(&o);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(v[c * 8 + q] * P.out_scale);
+          for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
           dst[c] = o;
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
   }
-  if (!ok && tid == 0) *sflag = 1;
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
-}
-
-template <typename TO, bool EC>
-size_t smem_bytes() {
-  return 1024 + (EC ? 14 : 7) * kMatBytes + 7 * kTileBytes + 64;
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128));
+  }
 }
 
 }  // namespace umma
@@ -379,13 +506,13 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   int e2;
   std::frexp(amax / 32.0, &e2);
   const double sc = std::ldexp(1.0, -e2);  // largest stored entry in [32, 64)
-  const double lo = std::is_same<TO, __half>::value ? 2048.0 : 256.0;
+  // Algorithm 1 split of the (normalized) block matrices: high part and rounded remainder
   std::vector<TO> hm((EC ? 14 : 7) * 4096);
   for (int e = 0; e < 7 * 4096; ++e) {
-    const float v = (float)(B[e] * sc);
-    const TO h = host_to<TO>(v);
+    const double v = B[e] * sc;
+    const TO h = host_to<TO>((float)v);
     hm[e] = h;
-    if (EC) hm[7 * 4096 + e] = host_to<TO>((float)((v - host_from<TO>(h)) * lo));
+    if (EC) hm[7 * 4096 + e] = host_to<TO>((float)(v - (double)host_from<TO>(h)));
   }
   cudaError_t err = cudaMalloc(&op->umma_mats, hm.size() * sizeof(TO));
   if (err == cudaSuccess) err = cudaMemcpy(op->umma_mats, hm.data(), hm.size() * sizeof(TO), cudaMemcpyHostToDevice);
@@ -397,7 +524,7 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   P.nx = op->mesh.nx; P.ny = op->mesh.ny; P.nz = op->mesh.nz;
   P.ncells = op->ncells;
   P.out_scale = (float)(1.0 / sc);
-  P.lo_scale = (float)(1.0 / lo);
+  P.lo_scale = 1.0f;
   const Ref1D& R = op->ref;
   for (int d = 0; d < 3; ++d) {
     const double g2h = 2.0 * op->dir[d].gamma * op->dir[d].h;
@@ -412,7 +539,7 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   if (err != cudaSuccess) return err;
   op->sm_count = sms > 0 ? sms : 1;
   return cudaFuncSetAttribute(umma::apply_umma_kernel<TO, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)umma::smem_bytes<TO, EC>());
+                              (int)umma::smem_bytes<EC>());
 }
 
 template <typename TO, bool EC>
@@ -431,7 +558,7 @@ static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cuda
     return cudaErrorInvalidValue;
   const long long tiles = (op->ncells + umma::kRows - 1) / umma::kRows;
   const int grid = (int)(tiles < op->sm_count ? tiles : op->sm_count);
-  umma::apply_umma_kernel<TO, EC><<<grid, 128, umma::smem_bytes<TO, EC>(), s>>>(
+  umma::apply_umma_kernel<TO, EC><<<grid, umma::kThreads, umma::smem_bytes<EC>(), s>>>(
       tm, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), op->umma_params, op->umma_err);
   return cudaGetLastError();
 }

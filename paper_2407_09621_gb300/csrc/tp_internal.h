@@ -59,7 +59,7 @@ struct UmmaParams {
   int nx, ny, nz;
   long long ncells;
   float out_scale;  // 1 / (power-of-two scale of the stored block matrices)
-  float lo_scale;   // 2^-s of Algorithm 1
+  float lo_scale;   // scale of the low-part products (1: they share the accumulator)
   float gh[3][4];   // high-side ghost functional for w_1 per direction
   float gl[3][4];   // low-side ghost functional for w_{n-2}
 };
