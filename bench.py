@@ -33,6 +33,18 @@ WORKLOAD = "SIPG DG-Laplace apply y=Ax, FP64, k=3, 128^3 cells (134,217,728 DoFs
 SLAB = (128, 128, 8)  # oracle sample: same k and per-DoF work, 8,388,608 DoFs
 
 
+def _measured_peaks():
+    """HBM copy bandwidth and bf16 GEMM rate measured on this GPU type (MEASURED_PEAKS.json)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+PEAKS = _measured_peaks()
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -100,14 +112,30 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def profile_traffic(kernel_src, summary):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel is unchanged since."""
+# the device-code sources of each kernel whose ncu counters a profile summary records
+KERNEL_SOURCES = {
+    "apply_cc": ["apply_cc.cu", "apply_common.cuh"],
+    "apply_umma": ["apply_umma.cu"],
+    "apply_dmma": ["apply_dmma.cu", "apply_common.cuh"],
+}
+
+
+def kernel_sha256(kernel):
+    """sha256 over the source files of one kernel (in a fixed order)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2407_09621_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profile_traffic(kernel, summary):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel's sources are unchanged since."""
     path = os.path.join(ROOT, "profiles", summary)
-    src = os.path.join(ROOT, "paper_2407_09621_gb300", "csrc", kernel_src)
-    if not (os.path.exists(path) and os.path.exists(src)):
+    if not os.path.exists(path):
         return None
     text = open(path).read()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = kernel_sha256(kernel)
     m_h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     m_t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not (m_h and m_t) or m_h.group(1) != h:
@@ -184,18 +212,29 @@ def secondary(stream):
     from tp_synth import uniform_vector
     out = []
     CC, TC = 1, 2
-    runs = [(7, 64, "fp64", CC, 0), (3, 80, "fp32", CC, 0), (3, 80, "fp16", CC, 0), (3, 80, "bf16", CC, 0),
+    runs = [(7, 64, "fp64", CC, 0), (3, 128, "fp64", TC, 0), (7, 64, "fp64", TC, 0),
+            (3, 80, "fp32", CC, 0), (3, 80, "fp16", CC, 0), (3, 80, "bf16", CC, 0),
             (7, 40, "fp32", CC, 0), (7, 40, "fp16", CC, 0),
-            (3, 80, "fp16", TC, 0), (3, 80, "bf16", TC, 0), (3, 80, "fp32", TC, 1), (2, 107, "fp16", TC, 0)]
+            (3, 80, "fp16", TC, 0), (3, 80, "fp16", TC, 1), (3, 80, "bf16", TC, 0),
+            (3, 128, "fp16", TC, 0), (3, 128, "fp16", TC, 1), (3, 128, "bf16", TC, 0),
+            (3, 80, "fp32", TC, 1), (2, 107, "fp16", TC, 0)]
+    paths = {0: "cuda_core", 1: "mma.sync f16/bf16", 2: "tcgen05 (TMA + TMEM)", 3: "mma.sync f64 (DMMA)"}
+    fp64_peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
     for k, nc, prec, kern, ec in runs:
         op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec)
         x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
         y = torch.empty_like(x)
         per, _ = time_applies(op, y, x, 10, 3, stream)
+        op.check()
         ms = statistics.mean(per)
-        out.append({"k": k, "cells": f"{nc}^3", "precision": prec, "kernel": "tensor" if kern == TC else "cuda_core",
-                    "ec": ec, "dofs": op.ndofs, "ms": ms, "gdofs": op.ndofs / ms / 1e6,
-                    "hbm_gbs": 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6})
+        gbs = 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6
+        row = {"k": k, "cells": f"{nc}^3", "precision": prec, "kernel": paths[op.info["tensor_path"]],
+               "ec": ec if prec != "bf16" or kern != TC else 1, "dofs": op.ndofs, "ms": ms,
+               "gdofs": op.ndofs / ms / 1e6, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / PEAKS["hbm_gbs"]}
+        if prec == "fp64":
+            tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
+            row.update({"fp64_tflops": tf, "fp64_frac_of_measured_dfma": tf / fp64_peak})
+        out.append(row)
         op.close()
         del x, y
     return out
@@ -324,7 +363,7 @@ def run_ours(args):
     flops_launch = op.info["flops_per_dof"] * ndofs
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
     peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
-    traffic = profile_traffic("apply_cc.cu", "apply_cc_fp64_k3_128cubed.md")
+    traffic = profile_traffic("apply_cc", "apply_cc_fp64_k3_128cubed.md")
 
     if rank != 0:
         return
