@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
     p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
     p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
+    p.add_argument("--no-tune", action="store_true", help="keep the default apply tile shape (no autotuner)")
     p.add_argument("--solve-only", action="store_true",
                    help="only the Sec. 7.2 Poisson solves at --k/--cells (for profiler captures)")
     return p.parse_args()
@@ -208,7 +209,7 @@ def time_applies(op, y, x, steps, warmup, stream):
 def secondary(stream):
     """A few steps of the other apply configurations (same kernel family), reported beside the headline."""
     import torch
-    from paper_2407_09621_gb300 import DGLaplace
+    from paper_2407_09621_gb300 import DGLaplace, _lib
     from tp_synth import uniform_vector
     out = []
     CC, TC = 1, 2
@@ -221,7 +222,7 @@ def secondary(stream):
     paths = {0: "cuda_core", 1: "mma.sync f16/bf16", 2: "tcgen05 (TMA + TMEM)", 3: "mma.sync f64 (DMMA)"}
     fp64_peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
     for k, nc, prec, kern, ec in runs:
-        op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec)
+        op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec, autotune=1)
         x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
         y = torch.empty_like(x)
         per, _ = time_applies(op, y, x, 10, 3, stream)
@@ -230,7 +231,8 @@ def secondary(stream):
         gbs = 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6
         row = {"k": k, "cells": f"{nc}^3", "precision": prec, "kernel": paths[op.info["tensor_path"]],
                "ec": ec if prec != "bf16" or kern != TC else 1, "dofs": op.ndofs, "ms": ms,
-               "gdofs": op.ndofs / ms / 1e6, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / PEAKS["hbm_gbs"]}
+               "gdofs": op.ndofs / ms / 1e6, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / PEAKS["hbm_gbs"],
+               "tile_cells": op.info["tile_cells"]}
         if prec == "fp64":
             tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
             row.update({"fp64_tflops": tf, "fp64_frac_of_measured_dfma": tf / fp64_peak})
@@ -311,7 +313,8 @@ def run_ours(args):
     if args.solve_only:
         print(json.dumps({"solve_only": True, **solve_bench(kdeg, nc)}), flush=True)
         return
-    op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=2 if args.tensor else 0, ec=1 if args.ec else 0)
+    op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=2 if args.tensor else 0, ec=1 if args.ec else 0,
+                   autotune=0 if args.no_tune else 1)
     ndofs = op.ndofs
     if args.kernel_only:
         x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)
@@ -319,7 +322,7 @@ def run_ours(args):
         per, total_ms = time_applies(op, y, x, args.steps, args.warmup, torch.cuda.current_stream())
         op.check()
         print(json.dumps({"kernel_only": True, "k": kdeg, "cells": nc, "prec": args.prec, "dofs": ndofs,
-                          "tensor_path": op.info["tensor_path"], "ec": int(args.ec),
+                          "tensor_path": op.info["tensor_path"], "ec": int(args.ec), "tile_cells": op.info["tile_cells"],
                           "ms_per_apply": statistics.mean(per), "gdofs": ndofs / statistics.mean(per) / 1e6}))
         op.close()
         return
@@ -378,7 +381,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "k": K_DEG, "cells": [NC, NC, NC], "dofs": ndofs,
                    "l2": "inputs (1.07 GB per vector) larger than L2, no flush", "parallelism": f"replicas x{world}",
-                   "kernel": "apply_cc (FP64 DFMA sum factorization)"},
+                   "kernel": "apply_cc (FP64 DFMA sum factorization)", "tile_cells": op.info["tile_cells"],
+                   "autotune": not args.no_tune},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "FP64 DFMA pipe, measured live by tp_bench_fma_peak (register-only FMA chains)",

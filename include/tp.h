@@ -59,6 +59,10 @@ typedef struct {
   int ec;       /* 1: error-corrected half-precision products (Algorithm 1), tensor kernel only */
   int tc_type;  /* operand type of the tensor kernel: TP_FP16 (default) or TP_BF16; for FP16/BF16
                    vectors it must equal the vector type */
+  int autotune; /* 1: at creation, time the tile shapes of the apply kernel (CUDA-core and DMMA:
+                   cells per thread block, the default halved, kept or doubled) on this device on a
+                   proxy of the mesh (same nx, ny, about 128 MB per vector) and keep the fastest.
+                   Results do not depend on the tile shape. 0 (default): the default shape */
 } tp_op_opts;
 
 /* Tensor kernel (TP_KERNEL_TENSOR). With FP64 vectors (k = 3 and k = 7 only) the six 1D
@@ -92,6 +96,8 @@ typedef struct {
   double flops_per_dof;   /* algorithmic flops per DoF of one tp_apply (FMA = 2) */
   int tensor_path;        /* tensor kernel only: 1 = mma.sync f16/bf16, 2 = tcgen05 (TMA + TMEM),
                              3 = mma.sync f64 (DMMA); 0 for the CUDA-core kernel */
+  int tile_cells;         /* cells per thread block (CUDA-core, DMMA) or per tile (tcgen05) of the
+                             apply launch; 0 for the mma.sync kernel */
 } tp_op_info_t;
 
 /* Uniform Cartesian mesh of [0,lx]x[0,ly]x[0,lz] with nx*ny*nz cells
@@ -282,6 +288,7 @@ typedef struct {
   double rtol;         /* relative residual target (default 1e-10) */
   int maxit;           /* per problem (default 300) */
   int streams;         /* concurrent worker streams (default 8; 1 = one after another) */
+  int autotune;        /* 1: autotune every problem's apply tile shapes (tp_op_opts.autotune) */
 } tp_batch_opts;
 
 typedef struct {

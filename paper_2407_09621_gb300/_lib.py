@@ -40,14 +40,14 @@ lib = ctypes.CDLL(LIB_PATH)
 
 class tp_op_opts(ctypes.Structure):
     _fields_ = [("penalty", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
-                ("tc_type", ctypes.c_int)]
+                ("tc_type", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class tp_op_info_t(ctypes.Structure):
     _fields_ = [("ncells", ctypes.c_longlong), ("ndofs", ctypes.c_longlong), ("k", ctypes.c_int),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double),
-                ("tensor_path", ctypes.c_int)]
+                ("tensor_path", ctypes.c_int), ("tile_cells", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -99,9 +99,9 @@ def tp_mesh_destroy(mesh):
 
 
 def tp_dg_laplace_create(mesh, k, precision, penalty=TP_PENALTY_CONFIG, kernel=TP_KERNEL_AUTO, ec=0,
-                         tc_type=TP_FP16):
+                         tc_type=TP_FP16, autotune=0):
     h = _vp()
-    opts = tp_op_opts(penalty, kernel, ec, tc_type)
+    opts = tp_op_opts(penalty, kernel, ec, tc_type, autotune)
     _check(lib.tp_dg_laplace_create(ctypes.byref(h), mesh, k, precision, ctypes.byref(opts)))
     return h
 
@@ -298,7 +298,7 @@ class tp_batch_problem(ctypes.Structure):
 class tp_batch_opts(ctypes.Structure):
     _fields_ = [("mg_precision", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("streams", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class tp_batch_result(ctypes.Structure):
@@ -313,7 +313,7 @@ lib.tp_batch_solve.argtypes = [ctypes.POINTER(tp_batch_problem), ctypes.c_int, c
 
 
 def tp_batch_solve(problems, mg_precision=TP_FP32, kernel=TP_KERNEL_CUDA_CORE, ec=0, restart=30, rtol=1e-10,
-                   maxit=300, streams=8):
+                   maxit=300, streams=8, autotune=0):
     """problems: list of dicts {cells: (nx, ny, nz) or int, k, modes: [(a, p, q, r), ...], x_ptr (optional)}.
     Returns (list of result dicts, total solve seconds)."""
     n = len(problems)
@@ -325,7 +325,7 @@ def tp_batch_solve(problems, mg_precision=TP_FP32, kernel=TP_KERNEL_CUDA_CORE, e
         a, pqr = _modes_arrays(p["modes"])
         keep += [a, pqr]
         arr[i] = tp_batch_problem(nx, ny, nz, p["k"], len(p["modes"]), a, pqr, _vp(p.get("x_ptr") or 0))
-    opts = tp_batch_opts(mg_precision, kernel, ec, restart, rtol, maxit, streams)
+    opts = tp_batch_opts(mg_precision, kernel, ec, restart, rtol, maxit, streams, autotune)
     res = (tp_batch_result * n)()
     total = ctypes.c_double()
     _check(lib.tp_batch_solve(arr, n, ctypes.byref(opts), res, ctypes.byref(total)))

@@ -21,7 +21,8 @@
 // Q2 = M^-1 v0/2h, B1 = -M^-1 d1/2h, B2 = -M^-1 v1/2h, C1 = M^-1 d0/2h,
 // C2 = M^-1 v0/2h (g the penalty, h the cell width normal to the face).
 //
-// Work layout: n^2 threads per cell, CPB cells per block. In every phase a
+// Work layout: n^2 threads per cell, CPB cells per block (the tile shape: CPB is
+// 128/n^2 halved, kept or doubled, picked per operator by the autotuner in tp_api.cu). In every phase a
 // thread owns one line of its cell along the direction being contracted, so
 // all threads of a warp apply the same 1D coefficients at the same time: the
 // 1D data is a __grid_constant__ kernel parameter and the coefficients are
@@ -37,12 +38,16 @@
 
 namespace tp {
 
-template <int N>
-__host__ __device__ constexpr int cc_cells_per_block() { return (128 / (N * N)) > 0 ? 128 / (N * N) : 1; }
+// cells per block of tile-shape variant V (0: half, 1: the default 128/n^2, 2: double)
+template <int N, int V>
+__host__ __device__ constexpr int cc_cells_per_block() {
+  return V == 0 ? ((128 / (N * N)) / 2 > 0 ? (128 / (N * N)) / 2 : 1)
+                : (V == 1 ? ((128 / (N * N)) > 0 ? 128 / (N * N) : 1) : 2 * ((128 / (N * N)) > 0 ? 128 / (N * N) : 1));
+}
 
-template <typename TC, int N>
+template <typename TC, int N, int V>
 __host__ __device__ constexpr size_t cc_smem_bytes() {
-  return sizeof(TC) * cc_cells_per_block<N>() * 4 * N * N * N;
+  return sizeof(TC) * cc_cells_per_block<N, V>() * 4 * N * N * N;
 }
 
 template <typename TC, int N>
@@ -56,11 +61,11 @@ __device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A,
   }
 }
 
-template <typename TS, typename TC, int N>
-__global__ void __launch_bounds__(N * N * cc_cells_per_block<N>())
+template <typename TS, typename TC, int N, int V>
+__global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
 apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ OpConst<TC> P,
                 int nx, int ny, int nz, long long ncells) {
-  constexpr int CPB = cc_cells_per_block<N>();
+  constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
@@ -152,22 +157,38 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
   }
 }
 
-template <typename TS, typename TC, int N>
-static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
-  constexpr int CPB = cc_cells_per_block<N>();
-  constexpr size_t smem = cc_smem_bytes<TC, N>();
+template <typename TS, typename TC, int N, int V>
+static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  constexpr int CPB = cc_cells_per_block<N, V>();
+  constexpr size_t smem = cc_smem_bytes<TC, N, V>();
   const long long blocks = (op->ncells + CPB - 1) / CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const OpConst<TC>& P = *static_cast<const OpConst<TC>*>(op->hconst(sizeof(TC)));
-  apply_cc_kernel<TS, TC, N><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
+  apply_cc_kernel<TS, TC, N, V><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
       static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, op->ncells);
   return cudaGetLastError();
 }
 
 template <typename TS, typename TC, int N>
+static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  switch (op->tile_variant) {
+    case 0: return launch_cc_v<TS, TC, N, 0>(op, y, x, s);
+    case 2: return launch_cc_v<TS, TC, N, 2>(op, y, x, s);
+  }
+  return launch_cc_v<TS, TC, N, 1>(op, y, x, s);
+}
+
+template <typename TS, typename TC, int N>
 static cudaError_t prepare_cc_n() {
-  return cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)cc_smem_bytes<TC, N>());
+  cudaError_t e = cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cc_smem_bytes<TC, N, 0>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cc_smem_bytes<TC, N, 1>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cc_smem_bytes<TC, N, 2>());
+  return e;
 }
 
 template <typename TS, typename TC>
@@ -207,6 +228,12 @@ static cudaError_t launch_cc_t(const tp_op_s* op, void* y, const void* x, cudaSt
     case 8: return launch_cc_n<TS, TC, 8>(op, y, x, s);
   }
   return cudaErrorInvalidValue;
+}
+
+// cells per block of the CUDA-core launch for n nodes and tile variant v
+int cc_tile_cells(int n, int v) {
+  const int base = (128 / (n * n)) > 0 ? 128 / (n * n) : 1;
+  return v == 0 ? (base / 2 > 0 ? base / 2 : 1) : (v == 1 ? base : 2 * base);
 }
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {

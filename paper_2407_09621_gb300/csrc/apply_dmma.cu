@@ -20,11 +20,12 @@ namespace tp {
 
 namespace dmma {
 
-template <int N>
-__host__ __device__ constexpr int cells_per_block() { return N == 8 ? 4 : 8; }
+// cells (warps) per block of tile-shape variant V: half, default (4 for n = 8, 8 for n = 4), double
+template <int N, int V>
+__host__ __device__ constexpr int cells_per_block() { return (N == 8 ? 4 : 8) * (V == 0 ? 1 : (V == 1 ? 2 : 4)) / 2; }
 
-template <int N>
-__host__ __device__ constexpr size_t smem_bytes() { return sizeof(double) * 3 * N * N * N * cells_per_block<N>(); }
+template <int N, int V>
+__host__ __device__ constexpr size_t smem_bytes() { return sizeof(double) * 3 * N * N * N * cells_per_block<N, V>(); }
 
 // Offset of node m of line r along direction D in a cell tensor with index (l*N + j)*N + i:
 // D = 0 (x): r = l*N + j; D = 1 (y): r = l*N + i; D = 2 (z): r = j*N + i.
@@ -83,11 +84,11 @@ __device__ __forceinline__ void faces_dmma(double* sW, const double* sU, const d
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(32 * cells_per_block<N>())
+template <int N, int V>
+__global__ void __launch_bounds__(32 * cells_per_block<N, V>())
 apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __grid_constant__ OpConst<double> P,
                   int nx, int ny, int nz, long long ncells) {
-  constexpr int CPB = cells_per_block<N>(), N3 = N * N * N;
+  constexpr int CPB = cells_per_block<N, V>(), N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* sU = reinterpret_cast<double*>(smem_raw) + warp * 3 * N3;
@@ -135,28 +136,48 @@ apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __
   contract_dmma<N, 0, false>(y + cell * N3, sW, bM[0], lane);
 }
 
-template <int N>
-static cudaError_t launch_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
-  constexpr int CPB = cells_per_block<N>();
+template <int N, int V>
+static cudaError_t launch_v(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  constexpr int CPB = cells_per_block<N, V>();
   const long long blocks = (op->ncells + CPB - 1) / CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  apply_dmma_kernel<N><<<(unsigned)blocks, 32 * CPB, smem_bytes<N>(), s>>>(
+  apply_dmma_kernel<N, V><<<(unsigned)blocks, 32 * CPB, smem_bytes<N, V>(), s>>>(
       static_cast<const double*>(x), static_cast<double*>(y), op->c64, op->mesh.nx, op->mesh.ny, op->mesh.nz,
       op->ncells);
   return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t launch_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  switch (op->tile_variant) {
+    case 0: return launch_v<N, 0>(op, y, x, s);
+    case 2: return launch_v<N, 2>(op, y, x, s);
+  }
+  return launch_v<N, 1>(op, y, x, s);
+}
+
+template <int N>
+static cudaError_t prepare_n() {
+  cudaError_t e = cudaFuncSetAttribute(apply_dmma_kernel<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<N, 0>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_dmma_kernel<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<N, 1>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(apply_dmma_kernel<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<N, 2>());
+  return e;
 }
 
 }  // namespace dmma
 
 bool dmma_supported(const tp_op_s* op) { return op->prec == TP_FP64 && (op->n == 4 || op->n == 8); }
 
+int dmma_tile_cells(int n, int v) { return (n == 8 ? 4 : 8) * (v == 0 ? 1 : (v == 1 ? 2 : 4)) / 2; }
+
 cudaError_t prepare_apply_dmma(const tp_op_s* op) {
-  if (op->n == 4)
-    return cudaFuncSetAttribute(dmma::apply_dmma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dmma::smem_bytes<4>());
-  if (op->n == 8)
-    return cudaFuncSetAttribute(dmma::apply_dmma_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dmma::smem_bytes<8>());
+  if (op->n == 4) return dmma::prepare_n<4>();
+  if (op->n == 8) return dmma::prepare_n<8>();
   return cudaErrorInvalidValue;
 }
 

@@ -59,7 +59,7 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     set_error("tp_batch_solve: need problems, count >= 1 and a results array");
     return TP_ERR_INVALID_ARG;
   }
-  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8};
+  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0};
   if (opts) o = *opts;
   if (o.streams < 1 || o.streams > 64 || o.restart < 1 || !(o.rtol > 0) || o.maxit < 1) {
     set_error("tp_batch_solve: invalid options (streams 1..64, restart >= 1, rtol > 0, maxit >= 1)");
@@ -73,7 +73,8 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     const tp_batch_problem& p = probs[i];
     Item& it = items[i];
     st = tp_mesh_create(&it.mesh, p.nx, p.ny, p.nz, 1.0, 1.0, 1.0);
-    if (st == TP_OK) st = tp_dg_laplace_create(&it.op, it.mesh, p.k, TP_FP64, nullptr);
+    const tp_op_opts oo{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16, o.autotune};
+    if (st == TP_OK) st = tp_dg_laplace_create(&it.op, it.mesh, p.k, TP_FP64, &oo);
     if (st != TP_OK) break;
     it.ndofs = it.op->ndofs;
     tp_mg_opts mo{3, 15.0, 1.1, 0.0, 4, o.mg_precision, 20, o.kernel, o.ec, TP_FP16};

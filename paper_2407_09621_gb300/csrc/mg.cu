@@ -587,7 +587,7 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   mg->lv.resize(nl);
   const size_t eb = elem_bytes(mg->prec);
   tp_status st = TP_OK;
-  tp_op_opts oo{finest->opts.penalty, o.kernel, o.ec, o.tc_type};
+  tp_op_opts oo{finest->opts.penalty, o.kernel, o.ec, o.tc_type, finest->opts.autotune};
   for (int l = 0; l < nl && st == TP_OK; ++l) {
     tp_mg_level& L = mg->lv[l];
     const auto& sz = sizes[nl - 1 - l];

@@ -44,6 +44,67 @@ cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t
   return op->use_umma ? launch_apply_umma(op, y, x, s) : launch_apply_tc(op, y, x, s);
 }
 
+int cc_tile_cells(int n, int v);
+int dmma_tile_cells(int n, int v);
+size_t elem_bytes(tp_precision p);
+
+// Autotuner of the apply's tile shape (cells per thread block of the CUDA-core and DMMA kernels:
+// the default halved, kept or doubled). Each shape is timed with CUDA events on a proxy of the
+// operator's mesh (same nx and ny, enough z-layers for about 128 MB per vector) after one
+// warm-up launch; the fastest is kept. The per-cell arithmetic does not depend on the shape, so
+// the choice changes no result. Tuning is best effort: if the proxy vectors cannot be
+// allocated the default shape stays.
+static tp_status autotune_apply(tp_op_s* op) {
+  const bool dm = op->opts.kernel == TP_KERNEL_TENSOR && op->prec == TP_FP64;
+  if (op->opts.kernel == TP_KERNEL_TENSOR && !dm) return TP_OK;  // tcgen05 / mma.sync: fixed tiles
+  const long long eb = (long long)elem_bytes(op->prec);
+  const long long n3 = (long long)op->n * op->n * op->n;
+  const long long slab = (long long)op->mesh.nx * op->mesh.ny;
+  long long nz = (128LL << 20) / (slab * n3 * eb);
+  nz = nz < 1 ? 1 : (nz > op->mesh.nz ? op->mesh.nz : nz);
+  tp_op_s proxy = *op;  // shares the constants; owns nothing
+  proxy.hx = proxy.hy = nullptr;
+  proxy.mesh.nz = (int)nz;
+  proxy.ncells = slab * nz;
+  proxy.ndofs = proxy.ncells * n3;
+  const size_t bytes = (size_t)(proxy.ndofs * eb);
+  void *x = nullptr, *y = nullptr;
+  if (cudaMalloc(&x, bytes) != cudaSuccess || cudaMalloc(&y, bytes) != cudaSuccess) {
+    if (x) cudaFree(x);
+    cudaGetLastError();
+    return TP_OK;
+  }
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  tp_status st = cuda_status(cudaMemset(x, 0x3c, bytes), "autotune fill");
+  if (st == TP_OK) st = cuda_status(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "autotune stream");
+  if (st == TP_OK) st = cuda_status(cudaEventCreate(&e0), "autotune event");
+  if (st == TP_OK) st = cuda_status(cudaEventCreate(&e1), "autotune event");
+  float best = 0.f;
+  int best_v = op->tile_variant;
+  for (int v = 0; v < 3 && st == TP_OK; ++v) {
+    proxy.tile_variant = v;
+    st = cuda_status(launch_apply(&proxy, y, x, s), "autotune launch");
+    if (st == TP_OK) st = cuda_status(cudaEventRecord(e0, s), "autotune event");
+    for (int r = 0; r < 3 && st == TP_OK; ++r) st = cuda_status(launch_apply(&proxy, y, x, s), "autotune launch");
+    if (st == TP_OK) st = cuda_status(cudaEventRecord(e1, s), "autotune event");
+    if (st == TP_OK) st = cuda_status(cudaEventSynchronize(e1), "autotune sync");
+    float ms = 0.f;
+    if (st == TP_OK) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1), "autotune timing");
+    if (st == TP_OK && (v == 0 || ms < best)) {
+      best = ms;
+      best_v = v;
+    }
+  }
+  if (st == TP_OK) op->tile_variant = best_v;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(x);
+  cudaFree(y);
+  return st;
+}
+
 // Tensor family: tcgen05 (TMA, TMEM) for k = 3 with FP16/BF16 vectors, mma.sync otherwise.
 static cudaError_t prepare_tensor(tp_op_s* op) {
   if (op->prec == TP_FP64) return dmma_supported(op) ? prepare_apply_dmma(op) : cudaErrorInvalidValue;
@@ -145,7 +206,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: unknown precision %d", (int)p);
     return TP_ERR_INVALID_ARG;
   }
-  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16};
+  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16, 0};
   if (opts) o = *opts;
   if (o.penalty != TP_PENALTY_CONFIG && o.penalty != TP_PENALTY_PAPER) {
     set_error("tp_dg_laplace_create: unknown penalty mode %d", o.penalty);
@@ -203,6 +264,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   fill_const(op->c32, op);
   st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
                    "apply kernel set-up");
+  if (st == TP_OK && o.autotune) st = autotune_apply(op);
   if (st != TP_OK) {
     tp_op_destroy(op);
     return st;
@@ -222,6 +284,9 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->elem_bytes = elem_bytes(op->prec);
   info->flops_per_dof = apply_flops_per_dof(op->n);
   info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
+  info->tile_cells = info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)
+                     : info->tensor_path == 3 ? dmma_tile_cells(op->n, op->tile_variant)
+                     : info->tensor_path == 2 ? 128 : 0;
   return TP_OK;
 }
 

@@ -85,6 +85,7 @@ struct tp_op_s {
   int device = 0;
   void* tc_mats = nullptr;    // tensor kernel operand matrices (device)
   int tc_blocks_per_sm = 1, sm_count = 1;
+  int tile_variant = 1;         // CUDA-core / DMMA tile shape: 0 half, 1 default, 2 double cells per block
   bool use_umma = false;        // tensor kernel runs on tcgen05 (k = 3, FP16/BF16 vectors)
   void* umma_mats = nullptr;    // its seven block matrices (and low parts) on the device
   int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)

@@ -213,3 +213,36 @@ def test_fp64_dmma_other_degrees_rejected(k):
     from paper_2407_09621_gb300 import DGLaplace, TPError
     with pytest.raises(TPError):
         DGLaplace(2, 2, 2, k, "fp64", kernel=TENSOR)
+
+
+# ---------------------------------------------------------------- tile-shape autotuner
+CC = 1
+
+
+@pytest.mark.parametrize("k,prec,kernel", [(3, "fp64", CC), (7, "fp64", CC), (2, "fp32", CC), (3, "fp16", CC),
+                                           (5, "bf16", CC), (3, "fp64", TENSOR), (7, "fp64", TENSOR)])
+def test_autotuned_apply_identical_to_default(k, prec, kernel):
+    """The autotuner only changes cells per thread block; every cell's arithmetic is unchanged,
+    so the tuned operator's output equals the default one bit for bit, and matches the oracle."""
+    from paper_2407_09621_gb300 import DGLaplace
+    dims = (13, 9, 11)
+    m = Mesh(*dims)
+    x64 = uniform_vector(m.ncells * (k + 1) ** 3, seed=60 + k)
+    outs, tiles = [], []
+    for tune in (0, 1):
+        op = DGLaplace(*dims, k, prec, kernel=kernel, autotune=tune)
+        try:
+            tiles.append(op.info["tile_cells"])
+            x = to_device(x64, prec)
+            y = torch.empty_like(x)
+            op.apply(y, x)
+            torch.cuda.synchronize()
+            outs.append(y.cpu())
+        finally:
+            op.close()
+    base = (128 // (k + 1) ** 2) or 1
+    if kernel == TENSOR:
+        base = 4 if k == 7 else 8
+    assert tiles[0] == base and tiles[1] in (max(base // 2, 1), base, 2 * base)
+    assert torch.equal(outs[0], outs[1])
+    assert rel_l2(outs[1].double().numpy(), BlockOperator(m, k).apply(x64)) < TOL[prec]
