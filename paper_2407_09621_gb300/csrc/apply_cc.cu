@@ -64,7 +64,7 @@ __device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A,
 template <typename TS, typename TC, int N, int V>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
 apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ OpConst<TC> P,
-                int nx, int ny, int nz, long long ncells) {
+                int nx, int ny, int nz, long long c_begin, long long c_end) {
   constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr int N2 = N * N, N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -76,8 +76,8 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
   TC* sY = base + (2 * CPB + cs) * N3;      // w_y
   TC* sZ = base + (3 * CPB + cs) * N3;      // M_z w
 
-  const long long cell = (long long)blockIdx.x * CPB + cs;
-  const bool valid = cell < ncells;
+  const long long cell = c_begin + (long long)blockIdx.x * CPB + cs;  // cells [c_begin, c_end) of the mesh
+  const bool valid = cell < c_end;
   const int cx = valid ? (int)(cell % nx) : 0;
   const int cy = valid ? (int)((cell / nx) % ny) : 0;
   const int cz = valid ? (int)(cell / ((long long)nx * ny)) : 0;
@@ -158,24 +158,27 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
 }
 
 template <typename TS, typename TC, int N, int V>
-static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                               cudaStream_t s) {
   constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr size_t smem = cc_smem_bytes<TC, N, V>();
-  const long long blocks = (op->ncells + CPB - 1) / CPB;
+  const long long blocks = (c1 - c0 + CPB - 1) / CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (blocks <= 0) return cudaSuccess;
   const OpConst<TC>& P = *static_cast<const OpConst<TC>*>(op->hconst(sizeof(TC)));
   apply_cc_kernel<TS, TC, N, V><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
-      static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, op->ncells);
+      static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, c0, c1);
   return cudaGetLastError();
 }
 
 template <typename TS, typename TC, int N>
-static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                               cudaStream_t s) {
   switch (op->tile_variant) {
-    case 0: return launch_cc_v<TS, TC, N, 0>(op, y, x, s);
-    case 2: return launch_cc_v<TS, TC, N, 2>(op, y, x, s);
+    case 0: return launch_cc_v<TS, TC, N, 0>(op, y, x, c0, c1, s);
+    case 2: return launch_cc_v<TS, TC, N, 2>(op, y, x, c0, c1, s);
   }
-  return launch_cc_v<TS, TC, N, 1>(op, y, x, s);
+  return launch_cc_v<TS, TC, N, 1>(op, y, x, c0, c1, s);
 }
 
 template <typename TS, typename TC, int N>
@@ -217,15 +220,15 @@ cudaError_t prepare_apply_cc(const tp_op_s* op) {
 }
 
 template <typename TS, typename TC>
-static cudaError_t launch_cc_t(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+static cudaError_t launch_cc_t(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s) {
   switch (op->n) {
-    case 2: return launch_cc_n<TS, TC, 2>(op, y, x, s);
-    case 3: return launch_cc_n<TS, TC, 3>(op, y, x, s);
-    case 4: return launch_cc_n<TS, TC, 4>(op, y, x, s);
-    case 5: return launch_cc_n<TS, TC, 5>(op, y, x, s);
-    case 6: return launch_cc_n<TS, TC, 6>(op, y, x, s);
-    case 7: return launch_cc_n<TS, TC, 7>(op, y, x, s);
-    case 8: return launch_cc_n<TS, TC, 8>(op, y, x, s);
+    case 2: return launch_cc_n<TS, TC, 2>(op, y, x, c0, c1, s);
+    case 3: return launch_cc_n<TS, TC, 3>(op, y, x, c0, c1, s);
+    case 4: return launch_cc_n<TS, TC, 4>(op, y, x, c0, c1, s);
+    case 5: return launch_cc_n<TS, TC, 5>(op, y, x, c0, c1, s);
+    case 6: return launch_cc_n<TS, TC, 6>(op, y, x, c0, c1, s);
+    case 7: return launch_cc_n<TS, TC, 7>(op, y, x, c0, c1, s);
+    case 8: return launch_cc_n<TS, TC, 8>(op, y, x, c0, c1, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -236,14 +239,20 @@ int cc_tile_cells(int n, int v) {
   return v == 0 ? (base / 2 > 0 ? base / 2 : 1) : (v == 1 ? base : 2 * base);
 }
 
-cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+// Output rows of cells [c0, c1) only (the input is read wherever those cells' faces reach).
+cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                  cudaStream_t s) {
   switch (op->prec) {
-    case TP_FP64: return launch_cc_t<double, double>(op, y, x, s);
-    case TP_FP32: return launch_cc_t<float, float>(op, y, x, s);
-    case TP_FP16: return launch_cc_t<__half, float>(op, y, x, s);
-    case TP_BF16: return launch_cc_t<__nv_bfloat16, float>(op, y, x, s);
+    case TP_FP64: return launch_cc_t<double, double>(op, y, x, c0, c1, s);
+    case TP_FP32: return launch_cc_t<float, float>(op, y, x, c0, c1, s);
+    case TP_FP16: return launch_cc_t<__half, float>(op, y, x, c0, c1, s);
+    case TP_BF16: return launch_cc_t<__nv_bfloat16, float>(op, y, x, c0, c1, s);
   }
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  return launch_apply_cc_range(op, y, x, 0, op->ncells, s);
 }
 
 }  // namespace tp

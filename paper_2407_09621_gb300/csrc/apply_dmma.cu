@@ -87,15 +87,15 @@ __device__ __forceinline__ void faces_dmma(double* sW, const double* sU, const d
 template <int N, int V>
 __global__ void __launch_bounds__(32 * cells_per_block<N, V>())
 apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __grid_constant__ OpConst<double> P,
-                  int nx, int ny, int nz, long long ncells) {
+                  int nx, int ny, int nz, long long c_begin, long long c_end) {
   constexpr int CPB = cells_per_block<N, V>(), N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* sU = reinterpret_cast<double*>(smem_raw) + warp * 3 * N3;
   double* sW = sU + N3;
   double* sT = sW + N3;
-  const long long cell = (long long)blockIdx.x * CPB + warp;
-  if (cell >= ncells) return;  // whole warp; the kernel has no block-wide barrier
+  const long long cell = c_begin + (long long)blockIdx.x * CPB + warp;  // cells [c_begin, c_end)
+  if (cell >= c_end) return;  // whole warp; the kernel has no block-wide barrier
   const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((long long)nx * ny));
   const double* xc = x + cell * N3;
 
@@ -137,23 +137,23 @@ apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __
 }
 
 template <int N, int V>
-static cudaError_t launch_v(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+static cudaError_t launch_v(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s) {
   constexpr int CPB = cells_per_block<N, V>();
-  const long long blocks = (op->ncells + CPB - 1) / CPB;
+  const long long blocks = (c1 - c0 + CPB - 1) / CPB;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (blocks <= 0) return cudaSuccess;
   apply_dmma_kernel<N, V><<<(unsigned)blocks, 32 * CPB, smem_bytes<N, V>(), s>>>(
-      static_cast<const double*>(x), static_cast<double*>(y), op->c64, op->mesh.nx, op->mesh.ny, op->mesh.nz,
-      op->ncells);
+      static_cast<const double*>(x), static_cast<double*>(y), op->c64, op->mesh.nx, op->mesh.ny, op->mesh.nz, c0, c1);
   return cudaGetLastError();
 }
 
 template <int N>
-static cudaError_t launch_n(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+static cudaError_t launch_n(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s) {
   switch (op->tile_variant) {
-    case 0: return launch_v<N, 0>(op, y, x, s);
-    case 2: return launch_v<N, 2>(op, y, x, s);
+    case 0: return launch_v<N, 0>(op, y, x, c0, c1, s);
+    case 2: return launch_v<N, 2>(op, y, x, c0, c1, s);
   }
-  return launch_v<N, 1>(op, y, x, s);
+  return launch_v<N, 1>(op, y, x, c0, c1, s);
 }
 
 template <int N>
@@ -181,10 +181,16 @@ cudaError_t prepare_apply_dmma(const tp_op_s* op) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_apply_dmma(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
-  if (op->n == 4) return dmma::launch_n<4>(op, y, x, s);
-  if (op->n == 8) return dmma::launch_n<8>(op, y, x, s);
+// Output rows of cells [c0, c1) only.
+cudaError_t launch_apply_dmma_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                    cudaStream_t s) {
+  if (op->n == 4) return dmma::launch_n<4>(op, y, x, c0, c1, s);
+  if (op->n == 8) return dmma::launch_n<8>(op, y, x, c0, c1, s);
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_dmma(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  return launch_apply_dmma_range(op, y, x, 0, op->ncells, s);
 }
 
 }  // namespace tp

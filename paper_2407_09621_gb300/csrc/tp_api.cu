@@ -27,6 +27,10 @@ tp_status cuda_status(int err, const char* what) {
 }
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                  cudaStream_t s);
+cudaError_t launch_apply_dmma_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                    cudaStream_t s);
 cudaError_t prepare_apply_cc(const tp_op_s* op);
 cudaError_t launch_apply_tc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_tc(tp_op_s* op);
@@ -175,6 +179,104 @@ double apply_flops_per_dof(int n) { return 12.0 * n + 38.0; }
 
 using namespace tp;
 
+namespace {
+
+// Copy/compute pipeline of tp_apply_host: the cells are cut into kChunks ranges of whole z-slabs;
+// chunk i is copied in on `in`, applied on `comp` once chunks i-1..i+1 (its face neighbours) are
+// resident, and copied out on `out`, so the three overlap (H2D and D2H use separate copy engines).
+constexpr int kChunks = 8;
+struct HostPipe {
+  cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr, loaded[kChunks] = {}, applied[kChunks] = {};
+};
+
+void destroy_pipe(HostPipe* p) {
+  if (!p) return;
+  for (cudaStream_t s : {p->in, p->comp, p->out})
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : {p->start, p->done})
+    if (e) cudaEventDestroy(e);
+  for (int i = 0; i < kChunks; ++i) {
+    if (p->loaded[i]) cudaEventDestroy(p->loaded[i]);
+    if (p->applied[i]) cudaEventDestroy(p->applied[i]);
+  }
+  delete p;
+}
+
+tp_status make_pipe(HostPipe** out) {
+  HostPipe* p = new (std::nothrow) HostPipe();
+  if (!p) { set_error("tp_apply_host: out of host memory"); return TP_ERR_OOM; }
+  tp_status st = TP_OK;
+  for (cudaStream_t* s : {&p->in, &p->comp, &p->out})
+    if (st == TP_OK) st = cuda_status(cudaStreamCreateWithFlags(s, cudaStreamNonBlocking), "tp_apply_host streams");
+  for (cudaEvent_t* e : {&p->start, &p->done})
+    if (st == TP_OK) st = cuda_status(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "tp_apply_host events");
+  for (int i = 0; i < kChunks && st == TP_OK; ++i) {
+    st = cuda_status(cudaEventCreateWithFlags(&p->loaded[i], cudaEventDisableTiming), "tp_apply_host events");
+    if (st == TP_OK)
+      st = cuda_status(cudaEventCreateWithFlags(&p->applied[i], cudaEventDisableTiming), "tp_apply_host events");
+  }
+  if (st != TP_OK) {
+    destroy_pipe(p);
+    return st;
+  }
+  *out = p;
+  return TP_OK;
+}
+
+// Pipelined host apply for the kernels that can restrict their output to a range of cells
+// (CUDA-core and DMMA). Ordered after prior work on `s`, and `s` waits for its completion.
+tp_status apply_host_pipelined(tp_op_s* op, void* y_host, const void* x_host, cudaStream_t s) {
+  if (!op->hpipe) {
+    HostPipe* p = nullptr;
+    tp_status st = make_pipe(&p);
+    if (st != TP_OK) return st;
+    op->hpipe = p;
+  }
+  HostPipe& P = *static_cast<HostPipe*>(op->hpipe);
+  const long long slab = (long long)op->mesh.nx * op->mesh.ny;
+  const int nz = op->mesh.nz;
+  const size_t cell_bytes = (size_t)(op->ndofs / op->ncells) * elem_bytes(op->prec);
+  auto z_at = [&](int i) { return (long long)nz * i / kChunks; };  // chunk i = slabs [z_at(i), z_at(i+1))
+  auto launch = [&](long long c0, long long c1, cudaStream_t st) {
+    return op->opts.kernel == TP_KERNEL_TENSOR ? launch_apply_dmma_range(op, op->hy, op->hx, c0, c1, st)
+                                               : launch_apply_cc_range(op, op->hy, op->hx, c0, c1, st);
+  };
+  tp_status st = cuda_status(cudaEventRecord(P.start, s), "tp_apply_host");
+  for (cudaStream_t q : {P.in, P.comp, P.out})
+    if (st == TP_OK) st = cuda_status(cudaStreamWaitEvent(q, P.start, 0), "tp_apply_host");
+  unsigned char* dx = static_cast<unsigned char*>(op->hx);
+  unsigned char* dy = static_cast<unsigned char*>(op->hy);
+  const unsigned char* hx = static_cast<const unsigned char*>(x_host);
+  unsigned char* hy = static_cast<unsigned char*>(y_host);
+  auto copy_in = [&](int i) {
+    const size_t o = (size_t)(z_at(i) * slab) * cell_bytes, n = (size_t)((z_at(i + 1) - z_at(i)) * slab) * cell_bytes;
+    tp_status r = cuda_status(cudaMemcpyAsync(dx + o, hx + o, n, cudaMemcpyHostToDevice, P.in), "tp_apply_host H2D");
+    if (r == TP_OK) r = cuda_status(cudaEventRecord(P.loaded[i], P.in), "tp_apply_host");
+    return r;
+  };
+  if (st == TP_OK) st = copy_in(0);
+  for (int i = 0; i < kChunks && st == TP_OK; ++i) {
+    if (i + 1 < kChunks) st = copy_in(i + 1);
+    const int need = i + 1 < kChunks ? i + 1 : i;  // the chunk above must be resident (face neighbours)
+    if (st == TP_OK) st = cuda_status(cudaStreamWaitEvent(P.comp, P.loaded[need], 0), "tp_apply_host");
+    if (st == TP_OK) st = cuda_status(launch(z_at(i) * slab, z_at(i + 1) * slab, P.comp), "tp_apply_host launch");
+    if (st == TP_OK) st = cuda_status(cudaEventRecord(P.applied[i], P.comp), "tp_apply_host");
+    if (st == TP_OK) st = cuda_status(cudaStreamWaitEvent(P.out, P.applied[i], 0), "tp_apply_host");
+    if (st == TP_OK) {
+      const size_t o = (size_t)(z_at(i) * slab) * cell_bytes;
+      const size_t n = (size_t)((z_at(i + 1) - z_at(i)) * slab) * cell_bytes;
+      st = cuda_status(cudaMemcpyAsync(hy + o, dy + o, n, cudaMemcpyDeviceToHost, P.out), "tp_apply_host D2H");
+    }
+  }
+  if (st == TP_OK) st = cuda_status(cudaEventRecord(P.done, P.out), "tp_apply_host");
+  if (st == TP_OK) st = cuda_status(cudaStreamWaitEvent(s, P.done, 0), "tp_apply_host");
+  if (st == TP_OK) st = cuda_status(cudaStreamSynchronize(s), "tp_apply_host sync");
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* tp_last_error(void) { return g_err; }
@@ -303,8 +405,10 @@ tp_status tp_op_check(tp_op op) {
   return TP_ERR_TIMEOUT;
 }
 
+
 tp_status tp_op_destroy(tp_op op) {
   if (!op) return TP_OK;
+  if (op->hpipe) destroy_pipe(static_cast<HostPipe*>(op->hpipe));
   if (op->hx) cudaFree(op->hx);
   if (op->hy) cudaFree(op->hy);
   if (op->tc_mats) cudaFree(op->tc_mats);
@@ -346,6 +450,8 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
     op->hbytes = bytes;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  const bool ranged = op->opts.kernel != TP_KERNEL_TENSOR || op->prec == TP_FP64;
+  if (ranged && op->mesh.nz >= kChunks) return apply_host_pipelined(op, y_host, x_host, s);
   tp_status st = cuda_status(cudaMemcpyAsync(op->hx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host H2D");
   if (st == TP_OK) st = cuda_status(launch_apply(op, op->hy, op->hx, s), "tp_apply_host launch");
   if (st == TP_OK) st = cuda_status(cudaMemcpyAsync(y_host, op->hy, bytes, cudaMemcpyDeviceToHost, s), "tp_apply_host D2H");

@@ -91,9 +91,11 @@ struct tp_op_s {
   int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)
   tp::UmmaParams umma_params;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
-  // host-buffer path (tp_apply_host): library-owned staging
+  // host-buffer path (tp_apply_host): library-owned staging, and the streams and events of its
+  // copy/compute pipeline (created on first use)
   void* hx = nullptr; void* hy = nullptr;
   size_t hbytes = 0;
+  void* hpipe = nullptr;
   tp::Ref1D ref;
   tp::Dir1D dir[3];
 };
