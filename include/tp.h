@@ -172,9 +172,14 @@ tp_status tp_op_check(tp_op op);
  *  - restriction I_down = P^T, prolongation I_up = P, the exact embedding of
  *    the coarse DG space into the fine one;
  *  - coarse solve A_0^{-1}: exact, in FP64, by fast diagonalization.
- * Vectors of the V-cycle have the multigrid precision (TP_FP64 or TP_FP32;
- * the latter is the low-precision preconditioner of Sec. 7.1). Level 0 is the
- * coarsest, level `levels-1` the finest (the operator given at creation). */
+ * Vectors of the V-cycle have the multigrid precision: TP_FP64, TP_FP32, or
+ * TP_FP16/TP_BF16 storage with FP32 arithmetic (the low-precision
+ * preconditioners of Sec. 7.1; with TP_KERNEL_TENSOR and k = 3 the FP16/BF16
+ * level operators run on tcgen05). Level 0 is the coarsest, level `levels-1`
+ * the finest (the operator given at creation). FP16 spans only 2^-24..65504:
+ * inside tp_fgmres_solve its V-cycle input is scaled by the largest power of
+ * two (at most 1) that keeps the V-cycle's gain on the smoothest mode, about
+ * n^3 / (3 pi^2 hx hy hz), from overflowing; BF16 has FP32's range. */
 #define TP_MAX_LEVELS 16
 
 typedef struct tp_mg_s* tp_mg;
@@ -185,10 +190,10 @@ typedef struct {
   double safety;     /* factor applied to the estimated lmax (default 1.1) */
   double lmax;       /* > 0: use this bound on every level instead of estimating it */
   int coarse_cells;  /* stop coarsening once no direction has more cells (default 4) */
-  int precision;     /* TP_FP64 or TP_FP32 (default) */
+  int precision;     /* TP_FP64, TP_FP32 (default), TP_FP16 or TP_BF16 */
   int power_iters;   /* power iterations for the lmax estimate (default 20) */
   int kernel;        /* apply kernel of the level operators: TP_KERNEL_CUDA_CORE (default) or
-                        TP_KERNEL_TENSOR (FP32 vectors, k = 2, 3; other levels/degrees fall back) */
+                        TP_KERNEL_TENSOR (FP32/FP16/BF16 vectors, k = 2, 3; otherwise CUDA-core) */
   int ec;            /* tensor kernel with Algorithm 1 error correction */
   int tc_type;       /* tensor operand type: TP_FP16 (default) or TP_BF16 */
 } tp_mg_opts;

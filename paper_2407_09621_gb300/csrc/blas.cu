@@ -3,6 +3,8 @@
 // FP64 and reduce deterministically: one partial per block written to a
 // scratch array (fixed grid), then one block sums the partials in a fixed
 // order, so repeated runs give bit-identical results.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "tp_internal.h"
@@ -14,6 +16,16 @@ constexpr int kRedThreads = 256;
 
 template <typename T>
 __device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <>
+__device__ __forceinline__ double to_d<__half>(__half v) { return (double)__half2float(v); }
+template <>
+__device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <typename T>
+__device__ __forceinline__ T from_d(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ __half from_d<__half>(double v) { return __float2half_rn((float)v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) { return __float2bfloat16_rn((float)v); }
 
 // partial[q * gridDim.x + blockIdx.x] = sum over this block's grid-stride slice of w * v_q
 template <typename T, int Q>
@@ -95,16 +107,44 @@ cudaError_t multi_dot(long long n, const T* w, const T* const* v, int nq, double
   return cudaGetLastError();
 }
 
+// Accumulation type of the axpy: FP64 for FP64 vectors, FP32 for FP32/FP16/BF16 vectors (the
+// result is rounded to the storage type; FP64 arithmetic there would only load the slow FP64 pipe).
+template <typename T> struct AxpyAcc { using A = float; };
+template <> struct AxpyAcc<double> { using A = double; };
+
+template <typename A, typename T>
+__device__ __forceinline__ A to_a(T v) { return (A)to_d(v); }
+template <>
+__device__ __forceinline__ float to_a<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_a<float, __half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_a<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T, typename A>
+__device__ __forceinline__ T from_a(A v) { return from_d<T>((double)v); }
+template <>
+__device__ __forceinline__ float from_a<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half from_a<__half, float>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_a<__nv_bfloat16, float>(float v) { return __float2bfloat16_rn(v); }
+
 // w = beta * w + sum_q c[q] * v_q   (c on the host, passed by value). w may be one of the v_q:
 // every entry is read and written by the same thread.
 template <typename T, int Q>
 __global__ void multi_axpy_kernel(long long n, T* w, double beta, MultiPtr<T> v, MultiCoef c, int nq) {
+  using A = typename AxpyAcc<T>::A;
+  A cq[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) cq[q] = (A)c.c[q];
+  const A b = (A)beta;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double acc = beta == 0.0 ? 0.0 : beta * to_d(w[i]);
+    A acc = beta == 0.0 ? A(0) : b * to_a<A>(w[i]);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
-      if (q < nq) acc = fma(c.c[q], to_d(v.p[q][i]), acc);
-    w[i] = (T)acc;
+      if (q < nq) acc = fma(cq[q], to_a<A>(v.p[q][i]), acc);
+    w[i] = from_a<T>(acc);
   }
 }
 
@@ -144,7 +184,7 @@ cudaError_t multi_axpy(long long n, T* w, double beta, const T* const* v, const 
 template <typename TO, typename TI>
 __global__ void convert_kernel(long long n, TO* __restrict__ out, const TI* __restrict__ in, double scale) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = (TO)(scale * (double)in[i]);
+    out[i] = from_d<TO>(scale * to_d(in[i]));
 }
 
 template <typename TO, typename TI>
@@ -158,6 +198,16 @@ template cudaError_t multi_dot<float>(long long, const float*, const float* cons
 template cudaError_t multi_axpy<double>(long long, double*, double, const double* const*, const double*, int, cudaStream_t);
 template cudaError_t multi_axpy<float>(long long, float*, double, const float* const*, const double*, int, cudaStream_t);
 template cudaError_t convert<float, double>(long long, float*, const double*, double, cudaStream_t);
+template cudaError_t multi_dot<__half>(long long, const __half*, const __half* const*, int, double*, double*, cudaStream_t);
+template cudaError_t multi_dot<__nv_bfloat16>(long long, const __nv_bfloat16*, const __nv_bfloat16* const*, int, double*,
+                                              double*, cudaStream_t);
+template cudaError_t multi_axpy<__half>(long long, __half*, double, const __half* const*, const double*, int, cudaStream_t);
+template cudaError_t multi_axpy<__nv_bfloat16>(long long, __nv_bfloat16*, double, const __nv_bfloat16* const*,
+                                               const double*, int, cudaStream_t);
+template cudaError_t convert<__half, double>(long long, __half*, const double*, double, cudaStream_t);
+template cudaError_t convert<double, __half>(long long, double*, const __half*, double, cudaStream_t);
+template cudaError_t convert<__nv_bfloat16, double>(long long, __nv_bfloat16*, const double*, double, cudaStream_t);
+template cudaError_t convert<double, __nv_bfloat16>(long long, double*, const __nv_bfloat16*, double, cudaStream_t);
 template cudaError_t convert<double, float>(long long, double*, const float*, double, cudaStream_t);
 template cudaError_t convert<double, double>(long long, double*, const double*, double, cudaStream_t);
 template cudaError_t convert<float, float>(long long, float*, const float*, double, cudaStream_t);

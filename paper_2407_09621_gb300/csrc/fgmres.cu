@@ -7,6 +7,8 @@
 // pass (two fused multi-dot/multi-axpy passes over V), v_{j+1} = w/||w||.
 // The small Hessenberg least-squares problem is solved on the host with
 // Givens rotations; its residual |g_{j+1}| is the convergence test.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -132,6 +134,19 @@ tp_status tp_solver_destroy(tp_solver s) {
 
 namespace {
 
+// Scale of the FP16 V-cycle input relative to O(1) entries. The V-cycle approximates A^-1, whose
+// gain on the smoothest mode is 1 / (lambda_1 m), lambda_1 ~ 3 pi^2 the smallest eigenvalue of
+// (A, M (x) M (x) M) and m ~ hx hy hz / n^3 the mean row sum of the 3D mass matrix. The input is
+// scaled by the largest power of two that keeps 8x that gain times O(1) entries below FP16's
+// 65504, and by at most 1; smaller inputs would push the residuals into FP16's subnormal range.
+double fp16_input_scale(const tp_op_s* A) {
+  const double n3 = (double)A->n * A->n * A->n;
+  const double pi = 3.14159265358979323846;
+  const double gain = n3 / (3.0 * pi * pi * A->dir[0].h * A->dir[1].h * A->dir[2].h);
+  const double s = 65504.0 / (8.0 * gain);
+  return s >= 1.0 ? 1.0 : std::ldexp(1.0, (int)std::floor(std::log2(s)));
+}
+
 struct Ctx {
   tp_solver_s* s;
   cudaStream_t st;
@@ -207,14 +222,32 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
     for (int j = 0; j < m && e == cudaSuccess; ++j) {
       // z_j = M^{-1} v_j
       if (s->mg) {
-        if (mg_precision(s->mg) == TP_FP64) {
-          e = convert<double, double>(n, (double*)s->pb, s->V[j], pscale, c.st);
-          if (e == cudaSuccess) e = run_vcycle(s, c.st);
-          if (e == cudaSuccess) e = convert<double, double>(n, s->Z[j], (const double*)s->px, 1.0 / pscale, c.st);
-        } else {
-          e = convert<float, double>(n, (float*)s->pb, s->V[j], pscale, c.st);
-          if (e == cudaSuccess) e = run_vcycle(s, c.st);
-          if (e == cudaSuccess) e = convert<double, float>(n, s->Z[j], (const float*)s->px, 1.0 / pscale, c.st);
+        const tp_precision mp = mg_precision(s->mg);
+        // FP16 keeps FP32's precision over a range of only 2^-24..65504: the V-cycle's gain on
+        // smooth components (up to 1/lambda_min(A)) must not overflow its output
+        const double sc = mp == TP_FP16 ? pscale * fp16_input_scale(s->A) : pscale;
+        switch (mp) {
+          case TP_FP64:
+            e = convert<double, double>(n, (double*)s->pb, s->V[j], sc, c.st);
+            if (e == cudaSuccess) e = run_vcycle(s, c.st);
+            if (e == cudaSuccess) e = convert<double, double>(n, s->Z[j], (const double*)s->px, 1.0 / sc, c.st);
+            break;
+          case TP_FP32:
+            e = convert<float, double>(n, (float*)s->pb, s->V[j], sc, c.st);
+            if (e == cudaSuccess) e = run_vcycle(s, c.st);
+            if (e == cudaSuccess) e = convert<double, float>(n, s->Z[j], (const float*)s->px, 1.0 / sc, c.st);
+            break;
+          case TP_FP16:
+            e = convert<__half, double>(n, (__half*)s->pb, s->V[j], sc, c.st);
+            if (e == cudaSuccess) e = run_vcycle(s, c.st);
+            if (e == cudaSuccess) e = convert<double, __half>(n, s->Z[j], (const __half*)s->px, 1.0 / sc, c.st);
+            break;
+          default:
+            e = convert<__nv_bfloat16, double>(n, (__nv_bfloat16*)s->pb, s->V[j], sc, c.st);
+            if (e == cudaSuccess) e = run_vcycle(s, c.st);
+            if (e == cudaSuccess)
+              e = convert<double, __nv_bfloat16>(n, s->Z[j], (const __nv_bfloat16*)s->px, 1.0 / sc, c.st);
+            break;
         }
       } else {
         e = cudaMemcpyAsync(s->Z[j], s->V[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st);

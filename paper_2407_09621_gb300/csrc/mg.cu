@@ -9,6 +9,8 @@
 // nodes, a Kronecker product of 1D n x n matrices per child), restriction
 // its transpose; both sum-factorized. Coarse solve: exact, in FP64, by fast
 // diagonalization with the 1D generalized eigenpairs L V = M V Lambda.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -26,17 +28,49 @@ tp_status cuda_status(int err, const char* what);
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 size_t elem_bytes(tp_precision p);
 
+// Division of n < 2^31 by an invariant d >= 1 with one multiply-high (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, floor(n / d) = (umulhi(n, m) + n) >> l.
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((1ull << f.l) < d) ++f.l;
+  f.m = (uint32_t)((((1ull << 32) * ((1ull << f.l) - d)) / d) + 1);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+  return (__umulhi(n, f.m) + n) >> f.l;
+}
+
 template <typename T>
 struct JacobiParams {
   T Md[3][kMaxN], Ld[3][kMaxN];  // diagonals of the 1D mass and interior stiffness blocks
   T lo[3], hi[3];                // boundary corrections of L's diagonal at node 0 / node n-1
   int nx, ny, nz;
+  FastDiv dx, dy;                // division by nx and by ny (cells < 2^31)
 };
 
 template <typename T>
 struct TransferParams {
   T P[2][kMaxN * kMaxN];  // P[c][i*kMaxN + j] = phi_j((c + x_i)/2)
 };
+
+// Arithmetic type of a storage type: FP16/BF16 vectors are computed on in FP32.
+template <typename TS> struct Arith { using T = TS; };
+template <> struct Arith<__half> { using T = float; };
+template <> struct Arith<__nv_bfloat16> { using T = float; };
+template <typename TS> using arith_t = typename Arith<TS>::T;
+
+template <typename TS>
+__device__ __forceinline__ arith_t<TS> ld(const TS* p) { return (arith_t<TS>)(*p); }
+template <typename TS>
+__device__ __forceinline__ void st(TS* p, arith_t<TS> v) { *p = (TS)v; }
 
 // 1/d. In FP64 a division costs many instructions of the slow FP64 pipe; instead the FP32
 // reciprocal seeds two Newton-Raphson steps r <- r + r(1 - d r) (each doubles the correct bits:
@@ -53,10 +87,11 @@ __device__ __forceinline__ double recip(double d) {
 template <typename T, int N>
 __device__ __forceinline__ T jacobi_inv(const JacobiParams<T>& J, long long idx) {
   constexpr int N3 = N * N * N;
-  const long long cell = idx / N3;
-  const int loc = (int)(idx % N3);
+  const uint32_t cell = (uint32_t)(idx / N3);
+  const int loc = (int)(idx - (long long)cell * N3);
   const int i = loc % N, j = (loc / N) % N, l = loc / (N * N);
-  const int cx = (int)(cell % J.nx), cy = (int)((cell / J.nx) % J.ny), cz = (int)(cell / ((long long)J.nx * J.ny));
+  const uint32_t q = fast_div(cell, J.dx), cz_ = fast_div(q, J.dy);
+  const int cx = (int)(cell - q * (uint32_t)J.nx), cy = (int)(q - cz_ * (uint32_t)J.ny), cz = (int)cz_;
   T lx = J.Ld[0][i], ly = J.Ld[1][j], lz = J.Ld[2][l];
   if (cx == 0 && i == 0) lx += J.lo[0];
   if (cx == J.nx - 1 && i == N - 1) lx += J.hi[0];
@@ -69,36 +104,36 @@ __device__ __forceinline__ T jacobi_inv(const JacobiParams<T>& J, long long idx)
 }
 
 // Chebyshev update: if t: r -= t;  d = c1*d + c2*D^{-1} r (c1 == 0: d is not read);  x = (x_zero ? 0 : x) + d
-template <typename T, int N>
-__global__ void cheb_update_kernel(long long n, const __grid_constant__ JacobiParams<T> J, T* __restrict__ x,
-                                   T* __restrict__ r, T* __restrict__ d, const T* __restrict__ t, T c1, T c2,
+template <typename TS, int N, typename T = arith_t<TS>>
+__global__ void cheb_update_kernel(long long n, const __grid_constant__ JacobiParams<T> J, TS* __restrict__ x,
+                                   TS* __restrict__ r, TS* __restrict__ d, const TS* __restrict__ t, T c1, T c2,
                                    int x_zero) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T ri = r[i];
+    T ri = ld(r + i);
     if (t) {
-      ri -= t[i];
-      r[i] = ri;
+      ri -= ld(t + i);
+      st(r + i, ri);
     }
     T di = c2 * jacobi_inv<T, N>(J, i) * ri;
-    if (c1 != T(0)) di = fma(c1, d[i], di);
-    d[i] = di;
-    x[i] = x_zero ? di : x[i] + di;
+    if (c1 != T(0)) di = fma(c1, ld(d + i), di);
+    st(d + i, di);
+    st(x + i, x_zero ? di : ld(x + i) + di);
   }
 }
 
 // y = s * D^{-1} t (inv = 1) or y = s * D t (inv = 0)
-template <typename T, int N>
-__global__ void dinv_kernel(long long n, const __grid_constant__ JacobiParams<T> J, T* __restrict__ y,
-                            const T* __restrict__ t, T s, int inv) {
+template <typename TS, int N, typename T = arith_t<TS>>
+__global__ void dinv_kernel(long long n, const __grid_constant__ JacobiParams<T> J, TS* __restrict__ y,
+                            const TS* __restrict__ t, T s, int inv) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const T di = jacobi_inv<T, N>(J, i);
-    y[i] = inv ? s * di * t[i] : s * t[i] / di;
+    st(y + i, inv ? s * di * ld(t + i) : s * ld(t + i) / di);
   }
 }
 
 // xf += P xc : one block per coarse cell, thread (l, j, i); children in turn.
-template <typename T, int N>
-__global__ void __launch_bounds__(N * N * N) prolong_add_kernel(T* __restrict__ xf, const T* __restrict__ xc,
+template <typename TS, int N, typename T = arith_t<TS>>
+__global__ void __launch_bounds__(N * N * N) prolong_add_kernel(TS* __restrict__ xf, const TS* __restrict__ xc,
                                                                 const __grid_constant__ TransferParams<T> P, int ncx,
                                                                 int ncy, int ncz) {
   constexpr int N2 = N * N, N3 = N2 * N;
@@ -106,7 +141,7 @@ __global__ void __launch_bounds__(N * N * N) prolong_add_kernel(T* __restrict__ 
   const long long C = blockIdx.x;
   const int tid = threadIdx.x, i = tid % N, j = (tid / N) % N, l = tid / N2;
   const int cx = (int)(C % ncx), cy = (int)((C / ncx) % ncy), cz = (int)(C / ((long long)ncx * ncy));
-  u[tid] = xc[C * N3 + tid];
+  u[tid] = ld(xc + C * N3 + tid);
   __syncthreads();
   for (int b = 0; b < 8; ++b) {
     const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
@@ -124,14 +159,14 @@ __global__ void __launch_bounds__(N * N * N) prolong_add_kernel(T* __restrict__ 
 #pragma unroll
     for (int m = 0; m < N; ++m) s = fma(P.P[bz][l * kMaxN + m], t2[m * N2 + j * N + i], s);
     const long long F = ((long long)(2 * cz + bz) * (2 * ncy) + (2 * cy + by)) * (2LL * ncx) + (2 * cx + bx);
-    xf[F * N3 + tid] += s;
+    st(xf + F * N3 + tid, ld(xf + F * N3 + tid) + s);
     __syncthreads();
   }
 }
 
 // xc = P^T rf : one block per coarse cell, sum over the eight children.
-template <typename T, int N>
-__global__ void __launch_bounds__(N * N * N) restrict_kernel(T* __restrict__ xc, const T* __restrict__ rf,
+template <typename TS, int N, typename T = arith_t<TS>>
+__global__ void __launch_bounds__(N * N * N) restrict_kernel(TS* __restrict__ xc, const TS* __restrict__ rf,
                                                              const __grid_constant__ TransferParams<T> P, int ncx,
                                                              int ncy, int ncz) {
   constexpr int N2 = N * N, N3 = N2 * N;
@@ -143,7 +178,7 @@ __global__ void __launch_bounds__(N * N * N) restrict_kernel(T* __restrict__ xc,
   for (int b = 0; b < 8; ++b) {
     const int bx = b & 1, by = (b >> 1) & 1, bz = b >> 2;
     const long long F = ((long long)(2 * cz + bz) * (2 * ncy) + (2 * cy + by)) * (2LL * ncx) + (2 * cx + bx);
-    u[tid] = rf[F * N3 + tid];
+    u[tid] = ld(rf + F * N3 + tid);
     __syncthreads();
     T s = 0;
 #pragma unroll
@@ -161,7 +196,7 @@ __global__ void __launch_bounds__(N * N * N) restrict_kernel(T* __restrict__ xc,
     acc += s;
     __syncthreads();
   }
-  xc[C * N3 + tid] = acc;
+  st(xc + C * N3 + tid, acc);
 }
 
 // ---- coarse solve by fast diagonalization (FP64), on a lexicographic N1z x N1y x N1x tensor
@@ -177,7 +212,7 @@ __global__ void fd_gather(const T* __restrict__ b, double* __restrict__ lex, FDD
     const int gx = (int)(e % D.N1[0]), gy = (int)((e / D.N1[0]) % D.N1[1]), gz = (int)(e / ((long long)D.N1[0] * D.N1[1]));
     const long long cell = ((long long)(gz / D.n) * D.ny + gy / D.n) * D.nx + gx / D.n;
     const int loc = ((gz % D.n) * D.n + gy % D.n) * D.n + gx % D.n;
-    lex[e] = scale * (double)b[cell * D.n * D.n * D.n + loc];
+    lex[e] = scale * (double)ld(b + cell * D.n * D.n * D.n + loc);
   }
 }
 
@@ -188,7 +223,7 @@ __global__ void fd_scatter(const double* __restrict__ lex, T* __restrict__ x, FD
     const int gx = (int)(e % D.N1[0]), gy = (int)((e / D.N1[0]) % D.N1[1]), gz = (int)(e / ((long long)D.N1[0] * D.N1[1]));
     const long long cell = ((long long)(gz / D.n) * D.ny + gy / D.n) * D.nx + gx / D.n;
     const int loc = ((gz % D.n) * D.n + gy % D.n) * D.n + gx % D.n;
-    x[cell * D.n * D.n * D.n + loc] = (T)(scale * lex[e]);
+    st(x + cell * D.n * D.n * D.n + loc, (arith_t<T>)(scale * lex[e]));
   }
 }
 
@@ -228,7 +263,7 @@ __global__ void hash_fill(long long n, T* __restrict__ x, unsigned seed) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     z ^= z >> 31;
-    x[i] = (T)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+    st(x + i, (arith_t<T>)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0));
   }
 }
 
@@ -280,14 +315,16 @@ const TransferParams<float>& tparams<float>(const tp_mg_s* mg) { return mg->p32;
 template <typename T, int N>
 static cudaError_t cheb_update_n(const tp_mg_level& L, void* x, void* r, void* d, const void* t, double c1, double c2,
                                  int x_zero, cudaStream_t s) {
-  cheb_update_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<T>(L), (T*)x, (T*)r, (T*)d,
-                                                             (const T*)t, (T)c1, (T)c2, x_zero);
+  using A = arith_t<T>;
+  cheb_update_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<A>(L), (T*)x, (T*)r, (T*)d,
+                                                             (const T*)t, (A)c1, (A)c2, x_zero);
   return cudaGetLastError();
 }
 
 template <typename T, int N>
 static cudaError_t dinv_n(const tp_mg_level& L, void* y, const void* t, double sc, int inv, cudaStream_t s) {
-  dinv_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<T>(L), (T*)y, (const T*)t, (T)sc, inv);
+  dinv_kernel<T, N><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, jparams<arith_t<T>>(L), (T*)y, (const T*)t,
+                                                      (arith_t<T>)sc, inv);
   return cudaGetLastError();
 }
 
@@ -295,7 +332,7 @@ template <typename T, int N>
 static cudaError_t prolong_n(const tp_mg_s* mg, int l, void* xf, const void* xc, cudaStream_t s) {
   const tp_mg_level& C = mg->lv[l - 1];
   const long long nc = (long long)C.nc[0] * C.nc[1] * C.nc[2];
-  prolong_add_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xf, (const T*)xc, tparams<T>(mg), C.nc[0], C.nc[1],
+  prolong_add_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xf, (const T*)xc, tparams<arith_t<T>>(mg), C.nc[0], C.nc[1],
                                                               C.nc[2]);
   return cudaGetLastError();
 }
@@ -304,7 +341,7 @@ template <typename T, int N>
 static cudaError_t restrict_n(const tp_mg_s* mg, int l, void* xc, const void* rf, cudaStream_t s) {
   const tp_mg_level& C = mg->lv[l - 1];
   const long long nc = (long long)C.nc[0] * C.nc[1] * C.nc[2];
-  restrict_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xc, (const T*)rf, tparams<T>(mg), C.nc[0], C.nc[1],
+  restrict_kernel<T, N><<<(unsigned)nc, N * N * N, 0, s>>>((T*)xc, (const T*)rf, tparams<arith_t<T>>(mg), C.nc[0], C.nc[1],
                                                            C.nc[2]);
   return cudaGetLastError();
 }
@@ -321,54 +358,40 @@ static cudaError_t restrict_n(const tp_mg_s* mg, int l, void* xc, const void* rf
   }                            \
   return cudaErrorInvalidValue;
 
+// storage type of the V-cycle vectors
+#define TP_DISPATCH_PREC(prec, CALL)                      \
+  switch (prec) {                                         \
+    case TP_FP64: { using T = double; CALL; }             \
+    case TP_FP32: { using T = float; CALL; }              \
+    case TP_FP16: { using T = __half; CALL; }             \
+    case TP_BF16: { using T = __nv_bfloat16; CALL; }      \
+  }                                                       \
+  return cudaErrorInvalidValue;
+
 static cudaError_t cheb_update(const tp_mg_s* mg, const tp_mg_level& L, void* x, void* r, void* d, const void* t,
                                double c1, double c2, int x_zero, cudaStream_t s) {
-  if (mg->prec == TP_FP64) {
-#define C64(N) cheb_update_n<double, N>(L, x, r, d, t, c1, c2, x_zero, s)
-    TP_DISPATCH_N(mg->n, C64)
-#undef C64
-  } else {
-#define C32(N) cheb_update_n<float, N>(L, x, r, d, t, c1, c2, x_zero, s)
-    TP_DISPATCH_N(mg->n, C32)
-#undef C32
-  }
+#define CU(N) cheb_update_n<T, N>(L, x, r, d, t, c1, c2, x_zero, s)
+  TP_DISPATCH_PREC(mg->prec, TP_DISPATCH_N(mg->n, CU))
+#undef CU
 }
 
 static cudaError_t dinv(const tp_mg_s* mg, const tp_mg_level& L, void* y, const void* t, double sc, int inv,
                         cudaStream_t s) {
-  if (mg->prec == TP_FP64) {
-#define D64(N) dinv_n<double, N>(L, y, t, sc, inv, s)
-    TP_DISPATCH_N(mg->n, D64)
-#undef D64
-  } else {
-#define D32(N) dinv_n<float, N>(L, y, t, sc, inv, s)
-    TP_DISPATCH_N(mg->n, D32)
-#undef D32
-  }
+#define DI(N) dinv_n<T, N>(L, y, t, sc, inv, s)
+  TP_DISPATCH_PREC(mg->prec, TP_DISPATCH_N(mg->n, DI))
+#undef DI
 }
 
 cudaError_t mg_prolong_add(const tp_mg_s* mg, int l, void* xf, const void* xc, cudaStream_t s) {
-  if (mg->prec == TP_FP64) {
-#define P64(N) prolong_n<double, N>(mg, l, xf, xc, s)
-    TP_DISPATCH_N(mg->n, P64)
-#undef P64
-  } else {
-#define P32(N) prolong_n<float, N>(mg, l, xf, xc, s)
-    TP_DISPATCH_N(mg->n, P32)
-#undef P32
-  }
+#define PR(N) prolong_n<T, N>(mg, l, xf, xc, s)
+  TP_DISPATCH_PREC(mg->prec, TP_DISPATCH_N(mg->n, PR))
+#undef PR
 }
 
 cudaError_t mg_restrict(const tp_mg_s* mg, int l, void* xc, const void* rf, cudaStream_t s) {
-  if (mg->prec == TP_FP64) {
-#define R64(N) restrict_n<double, N>(mg, l, xc, rf, s)
-    TP_DISPATCH_N(mg->n, R64)
-#undef R64
-  } else {
-#define R32(N) restrict_n<float, N>(mg, l, xc, rf, s)
-    TP_DISPATCH_N(mg->n, R32)
-#undef R32
-  }
+#define RE(N) restrict_n<T, N>(mg, l, xc, rf, s)
+  TP_DISPATCH_PREC(mg->prec, TP_DISPATCH_N(mg->n, RE))
+#undef RE
 }
 
 static long long fd_total(const FDDims& D) { return (long long)D.N1[0] * D.N1[1] * D.N1[2]; }
@@ -377,10 +400,12 @@ cudaError_t mg_coarse_solve(const tp_mg_s* mg, void* x, const void* b, cudaStrea
   const FDDims& D = mg->fd;
   const long long tot = fd_total(D);
   const int g = grid_for(tot);
-  if (mg->prec == TP_FP64)
-    fd_gather<double><<<g, 256, 0, s>>>((const double*)b, mg->fdT0, D, 1.0);
-  else
-    fd_gather<float><<<g, 256, 0, s>>>((const float*)b, mg->fdT0, D, 1.0);
+  switch (mg->prec) {
+    case TP_FP64: fd_gather<double><<<g, 256, 0, s>>>((const double*)b, mg->fdT0, D, 1.0); break;
+    case TP_FP32: fd_gather<float><<<g, 256, 0, s>>>((const float*)b, mg->fdT0, D, 1.0); break;
+    case TP_FP16: fd_gather<__half><<<g, 256, 0, s>>>((const __half*)b, mg->fdT0, D, 1.0); break;
+    case TP_BF16: fd_gather<__nv_bfloat16><<<g, 256, 0, s>>>((const __nv_bfloat16*)b, mg->fdT0, D, 1.0); break;
+  }
   double *a = mg->fdT0, *c = mg->fdT1;
   for (int ax = 0; ax < 3; ++ax) {
     fd_contract<<<g, 256, 0, s>>>(a, c, mg->fdV[ax], D, ax, 0);
@@ -391,11 +416,21 @@ cudaError_t mg_coarse_solve(const tp_mg_s* mg, void* x, const void* b, cudaStrea
     fd_contract<<<g, 256, 0, s>>>(a, c, mg->fdV[ax], D, ax, 1);
     double* tmp = a; a = c; c = tmp;
   }
-  if (mg->prec == TP_FP64)
-    fd_scatter<double><<<g, 256, 0, s>>>(a, (double*)x, D, 1.0);
-  else
-    fd_scatter<float><<<g, 256, 0, s>>>(a, (float*)x, D, 1.0);
+  switch (mg->prec) {
+    case TP_FP64: fd_scatter<double><<<g, 256, 0, s>>>(a, (double*)x, D, 1.0); break;
+    case TP_FP32: fd_scatter<float><<<g, 256, 0, s>>>(a, (float*)x, D, 1.0); break;
+    case TP_FP16: fd_scatter<__half><<<g, 256, 0, s>>>(a, (__half*)x, D, 1.0); break;
+    case TP_BF16: fd_scatter<__nv_bfloat16><<<g, 256, 0, s>>>(a, (__nv_bfloat16*)x, D, 1.0); break;
+  }
   return cudaGetLastError();
+}
+
+// r = b - t
+template <typename T>
+static cudaError_t sub_t(long long n, void* r, const void* b, const void* t, cudaStream_t s) {
+  const double c[2] = {1.0, -1.0};
+  const T* v[2] = {(const T*)b, (const T*)t};
+  return multi_axpy<T>(n, (T*)r, 0.0, v, c, 2, s);
 }
 
 // r = b - A x  (t is scratch)
@@ -403,13 +438,7 @@ static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, co
                             cudaStream_t s) {
   cudaError_t e = launch_apply(L.op, t, x, s);
   if (e != cudaSuccess) return e;
-  const double c[2] = {1.0, -1.0};
-  if (mg->prec == TP_FP64) {
-    const double* v[2] = {(const double*)b, (const double*)t};
-    return multi_axpy<double>(L.ndofs, (double*)r, 0.0, v, c, 2, s);
-  }
-  const float* v[2] = {(const float*)b, (const float*)t};
-  return multi_axpy<float>(L.ndofs, (float*)r, 0.0, v, c, 2, s);
+  TP_DISPATCH_PREC(mg->prec, return sub_t<T>(L.ndofs, r, b, t, s))
 }
 
 // `degree` Chebyshev-Jacobi steps on level l from x (x_zero: x is taken as 0 and not read)
@@ -449,29 +478,18 @@ cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_ze
   return e;
 }
 
-// lmax(D^{-1}A) on level l: power iteration x <- D^{-1}A x / |.| from a fixed
-// pseudo-random start; the estimate is the generalized Rayleigh quotient
-// (x, A x) / (x, D x) of the last iterate, which never exceeds lmax.
-static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, double* out) {
+template <typename T>
+static tp_status estimate_lmax_t(tp_mg_s* mg, int l, int iters, cudaStream_t s, double* out) {
   tp_mg_level& L = mg->lv[l];
-  const bool f64 = mg->prec == TP_FP64;
-  if (f64)
-    hash_fill<double><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, (double*)L.d, 12345u + l);
-  else
-    hash_fill<float><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, (float*)L.d, 12345u + l);
+  hash_fill<T><<<grid_for(L.ndofs), 256, 0, s>>>(L.ndofs, (T*)L.d, 12345u + l);
   double rho = 0.0, h[2];
   // L.d = x, L.t = A x, L.r = D x then D^{-1} A x
   for (int it = 0; it < iters; ++it) {
     cudaError_t e = launch_apply(L.op, L.t, L.d, s);
     if (e == cudaSuccess) e = dinv(mg, L, L.r, L.d, 1.0, 0, s);
     if (e == cudaSuccess) {
-      if (f64) {
-        const double* v[2] = {(const double*)L.t, (const double*)L.r};
-        e = multi_dot<double>(L.ndofs, (const double*)L.d, v, 2, mg->partial, mg->dots, s);
-      } else {
-        const float* v[2] = {(const float*)L.t, (const float*)L.r};
-        e = multi_dot<float>(L.ndofs, (const float*)L.d, v, 2, mg->partial, mg->dots, s);
-      }
+      const T* v[2] = {(const T*)L.t, (const T*)L.r};
+      e = multi_dot<T>(L.ndofs, (const T*)L.d, v, 2, mg->partial, mg->dots, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, mg->dots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -485,13 +503,8 @@ static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, do
     e = dinv(mg, L, L.r, L.t, 1.0, 1, s);
     double nn = 0.0;
     if (e == cudaSuccess) {
-      if (f64) {
-        const double* v[1] = {(const double*)L.r};
-        e = multi_dot<double>(L.ndofs, (const double*)L.r, v, 1, mg->partial, mg->dots, s);
-      } else {
-        const float* v[1] = {(const float*)L.r};
-        e = multi_dot<float>(L.ndofs, (const float*)L.r, v, 1, mg->partial, mg->dots, s);
-      }
+      const T* v[1] = {(const T*)L.r};
+      e = multi_dot<T>(L.ndofs, (const T*)L.r, v, 1, mg->partial, mg->dots, s);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nn, mg->dots, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -501,17 +514,26 @@ static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, do
       return TP_ERR_NONFINITE;
     }
     const double c[1] = {1.0 / std::sqrt(nn)};
-    if (f64) {
-      const double* v[1] = {(const double*)L.r};
-      e = multi_axpy<double>(L.ndofs, (double*)L.d, 0.0, v, c, 1, s);
-    } else {
-      const float* v[1] = {(const float*)L.r};
-      e = multi_axpy<float>(L.ndofs, (float*)L.d, 0.0, v, c, 1, s);
-    }
+    const T* v[1] = {(const T*)L.r};
+    e = multi_axpy<T>(L.ndofs, (T*)L.d, 0.0, v, c, 1, s);
     if (e != cudaSuccess) return cuda_status(e, "tp_mg_create: eigenvalue estimate");
   }
   *out = rho;
   return TP_OK;
+}
+
+// lmax(D^{-1}A) on level l: power iteration x <- D^{-1}A x / |.| from a fixed
+// pseudo-random start; the estimate is the generalized Rayleigh quotient
+// (x, A x) / (x, D x) of the last iterate, which never exceeds lmax.
+static tp_status estimate_lmax(tp_mg_s* mg, int l, int iters, cudaStream_t s, double* out) {
+  switch (mg->prec) {
+    case TP_FP64: return estimate_lmax_t<double>(mg, l, iters, s, out);
+    case TP_FP32: return estimate_lmax_t<float>(mg, l, iters, s, out);
+    case TP_FP16: return estimate_lmax_t<__half>(mg, l, iters, s, out);
+    case TP_BF16: return estimate_lmax_t<__nv_bfloat16>(mg, l, iters, s, out);
+  }
+  set_error("tp_mg_create: unknown precision");
+  return TP_ERR_INVALID_ARG;
 }
 
 int mg_finest_level(const tp_mg_s* mg) { return (int)mg->lv.size() - 1; }
@@ -555,12 +577,17 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   if (!out) { set_error("tp_mg_create: out is NULL"); return TP_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!finest) { set_error("tp_mg_create: operator is NULL"); return TP_ERR_INVALID_ARG; }
+  if (finest->ncells >= (1LL << 31)) {
+    set_error("tp_mg_create: meshes of 2^31 cells or more are not supported");
+    return TP_ERR_UNSUPPORTED;
+  }
   tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20, TP_KERNEL_CUDA_CORE, 0, TP_FP16};
   if (opts) o = *opts;
   if (o.degree < 1 || o.degree > 16 || !(o.ratio > 1.0) || !(o.safety > 0) || o.coarse_cells < 1 ||
-      (o.precision != TP_FP64 && o.precision != TP_FP32) || o.power_iters < 1 || o.lmax < 0) {
+      (o.precision != TP_FP64 && o.precision != TP_FP32 && o.precision != TP_FP16 && o.precision != TP_BF16) ||
+      o.power_iters < 1 || o.lmax < 0) {
     set_error("tp_mg_create: invalid options (degree 1..16, ratio > 1, safety > 0, coarse_cells >= 1, "
-              "precision FP64 or FP32, power_iters >= 1, lmax >= 0)");
+              "precision FP64, FP32, FP16 or BF16, power_iters >= 1, lmax >= 0)");
     return TP_ERR_INVALID_ARG;
   }
   tp_mg_s* mg = new (std::nothrow) tp_mg_s();
@@ -621,6 +648,8 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
       }
       L.j64.nx = sz[0]; L.j64.ny = sz[1]; L.j64.nz = sz[2];
       L.j32.nx = sz[0]; L.j32.ny = sz[1]; L.j32.nz = sz[2];
+      L.j64.dx = L.j32.dx = make_fastdiv((uint32_t)sz[0]);
+      L.j64.dy = L.j32.dy = make_fastdiv((uint32_t)sz[1]);
       for (int d = 0; d < 3; ++d) {
         for (int i = 0; i < kMaxN; ++i) { L.j32.Md[d][i] = (float)L.j64.Md[d][i]; L.j32.Ld[d][i] = (float)L.j64.Ld[d][i]; }
         L.j32.lo[d] = (float)L.j64.lo[d];

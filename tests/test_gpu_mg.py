@@ -19,9 +19,9 @@ from tests.gpu_util import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-DT = {"fp64": torch.float64, "fp32": torch.float32}
+DT = {"fp64": torch.float64, "fp32": torch.float32, "fp16": torch.float16, "bf16": torch.bfloat16}
 TOLS = {"fp64": 1e-12, "fp32": 1e-5}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 
 
 class GpuMG:
@@ -137,11 +137,12 @@ def test_lmax_estimate_bounds_the_spectrum(k):
         g.close()
 
 
-def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4):
+def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4, kernel=1):
     from paper_2407_09621_gb300 import _lib
     mesh = _lib.tp_mesh_create(nc, nc, nc)
     op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
-    mg = _lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec]) if mg_prec else None
+    mg = (_lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec], kernel=kernel)
+          if mg_prec else None)
     solver = _lib.tp_fgmres_create(op, mg, 30)
     try:
         b = torch.from_numpy(rhs_sine(k, nc, nc, nc)).cuda()
@@ -230,3 +231,40 @@ def test_rhs_and_l2_error_match_oracle(k, nc):
     finally:
         _lib.tp_op_destroy(op)
         _lib.tp_mesh_destroy(mesh)
+
+
+# ---------------------------------------------------------------- FP16 / BF16 storage V-cycles
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-2), ("bf16", 5e-2)])
+@pytest.mark.parametrize("k,nc,cnc", [(3, 8, 1), (2, 8, 2), (7, 4, 1)])
+def test_half_storage_vcycle_matches_oracle(prec, tol, k, nc, cnc):
+    """The V-cycle with FP16/BF16 vectors (FP32 arithmetic) against the FP64 oracle V-cycle:
+    same algorithm, storage rounding only (2^-11 / 2^-8 per stored value)."""
+    lmax = 2.9
+    g = GpuMG(nc, k, prec, lmax=lmax, coarse_cells=cnc)
+    try:
+        assert g.info["precision"] == PREC[prec]
+        n = g.info["ndofs"][-1]
+        b, x0 = uniform_vector(n, seed=3), uniform_vector(n, seed=4)
+        x = g.vec(x0)
+        g.lib.tp_vcycle(g.mg, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        mg = VCycle(k, nc, coarse_nc=cnc)
+        mg.lmax = [None] + [lmax] * (len(mg.levels) - 1)
+        ref = mg.vcycle(len(mg.levels) - 1, b, x0)
+        assert rel_l2(x.double().cpu().numpy(), ref) < tol
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("mg_prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("k,nc,kernel", [(3, 32, 1), (3, 32, 2), (2, 16, 2), (7, 16, 1)])
+def test_half_vcycle_solve_meets_l2_rule(mg_prec, k, nc, kernel):
+    """FP64 FGMRES preconditioned by an FP16/BF16-storage V-cycle (CUDA-core applies, or the
+    tensor-core applies: tcgen05 at k = 3, mma.sync at k = 2) reaches the FP64 discretization
+    error of Sec. 7.2."""
+    x, info = _solve(nc, k, mg_prec, kernel=kernel, maxit=300)
+    assert info["converged"] == 1
+    u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+    e_mixed = l2_error(x, k, nc, nc, nc, sine_exact)
+    e_exact = l2_error(u, k, nc, nc, nc, sine_exact)
+    assert _l2_rule(e_mixed, e_exact), (e_mixed, e_exact)
