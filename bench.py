@@ -275,7 +275,8 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
         err = _lib.tp_l2_error_sines(op, x.data_ptr())
         out[name] = {"seconds": dt, "iterations": info["iterations"], "converged": info["converged"],
                      "true_rel_residual": info["true_rel_residual"], "l2_error": err, "status": st,
-                     "level_kernel": "tensor" if kern == TC else "cuda_core"}
+                     "level_kernel": "tensor" if kern == TC else "cuda_core",
+                     "reorthogonalizations": info.get("reorthogonalizations")}
         _lib.tp_solver_destroy(solver)
         _lib.tp_mg_destroy(mg)
         del x
@@ -361,12 +362,17 @@ def run_ours(args):
     value = world * ndofs * args.steps / (total_ms * 1e-3) / 1e9
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
+    # per-call wall times; the reported figure uses their median (isolated host-side stalls of
+    # tens of ms, unrelated to the call, appear on the shared hosts), the mean is reported beside it
     e2e_steps = max(3, min(args.steps, 10))
     op.apply_host(y_host, x_host)
-    t0 = time.perf_counter()
+    e2e_times = []
     for _ in range(e2e_steps):
+        t0 = time.perf_counter()
         op.apply_host(y_host, x_host)
-    e2e_dt = (time.perf_counter() - t0) / e2e_steps
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_dt = statistics.median(e2e_times)
+    e2e_mean = statistics.mean(e2e_times)
     e2e_bytes = ndofs * op.info["elem_bytes"]
     e2e_t = torch.tensor([e2e_dt], device="cuda", dtype=torch.float64)
     if world > 1:
@@ -401,6 +407,7 @@ def run_ours(args):
                      "hbm_gbs_algorithmic": 16.0 * ndofs / (avg_launch_ms * 1e-3) / 1e9},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": e2e_bytes,
+                "statistic": f"median of {e2e_steps} calls", "mean_value": world * ndofs / e2e_mean / 1e9,
                 "d2h_bytes_per_step": e2e_bytes},
         "gpu_launches": args.steps,
         "clocks": clk,

@@ -239,8 +239,10 @@ tp_status tp_mg_coarse_solve(tp_mg mg, void* x, const void* b, void* stream);
  * pass), the operator applications w = A z_j and the true residual at each
  * restart are FP64; the preconditioner is one V-cycle of `mg` in its own
  * precision with zero initial guess (the input is converted, scaled by
- * sqrt(ndofs), and the output converted back). Stops when the Arnoldi
- * residual norm drops below rtol * ||b - A x0||. */
+ * sqrt(ndofs), and the output converted back). Orthogonalization: classical
+ * Gram-Schmidt, repeated once when the projection removes more than half of
+ * |w|^2 (|w_new| < |w_old| / sqrt 2, the "twice is enough" criterion). Stops
+ * when the Arnoldi residual norm drops below rtol * ||b - A x0||. */
 typedef struct tp_solver_s* tp_solver;
 
 typedef struct {
@@ -252,6 +254,7 @@ typedef struct {
   const double* history;   /* host array of relative residual estimates, one per iteration + 1;
                               owned by the solver, valid until the next solve or destroy */
   int history_len;
+  int reorthogonalizations;/* Arnoldi steps that needed the second Gram-Schmidt pass */
 } tp_solve_info;
 
 /* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's

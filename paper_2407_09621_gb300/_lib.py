@@ -150,7 +150,8 @@ class tp_mg_info_t(ctypes.Structure):
 class tp_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
-                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int)]
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
+                ("reorthogonalizations", ctypes.c_int)]
 
 
 _sig2 = {
@@ -233,7 +234,8 @@ def tp_fgmres_solve(solver, x_ptr, b_ptr, rtol=1e-10, maxit=200, stream=0, raise
     st = lib.tp_fgmres_solve(solver, _vp(x_ptr), _vp(b_ptr), rtol, maxit, ctypes.byref(info), _vp(stream))
     d = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
          "rel_residual": info.rel_residual, "true_rel_residual": info.true_rel_residual,
-         "history": [info.history[i] for i in range(info.history_len)] if info.history else []}
+         "history": [info.history[i] for i in range(info.history_len)] if info.history else [],
+         "reorthogonalizations": info.reorthogonalizations}
     if st != TP_OK and raise_on_error:
         raise TPError(st, lib.tp_last_error().decode())
     return st, d

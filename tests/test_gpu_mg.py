@@ -268,3 +268,20 @@ def test_half_vcycle_solve_meets_l2_rule(mg_prec, k, nc, kernel):
     e_mixed = l2_error(x, k, nc, nc, nc, sine_exact)
     e_exact = l2_error(u, k, nc, nc, nc, sine_exact)
     assert _l2_rule(e_mixed, e_exact), (e_mixed, e_exact)
+
+
+@pytest.mark.parametrize("k,nc", [(3, 16), (7, 8)])
+def test_fgmres_basis_stays_orthonormal(k, nc):
+    """Selective re-orthogonalization keeps the FGMRES basis orthonormal: after a solve the
+    relative residual recomputed in FP64 matches the Arnoldi estimate (a lost orthogonality
+    would show as a gap between the two), and the iteration count matches the oracle's
+    modified Gram-Schmidt FGMRES within two."""
+    x, info = _solve(nc, k, "fp32", lmax=2.9, coarse_cells=2)
+    assert info["converged"] == 1
+    assert info["true_rel_residual"] < 10 * max(info["rel_residual"], 1e-12)
+    assert 0 <= info["reorthogonalizations"] <= info["iterations"]
+    mg = VCycle(k, nc, coarse_nc=2)
+    mg.lmax = [None] + [2.9] * (len(mg.levels) - 1)
+    A = BlockOperator(Mesh(nc, nc, nc), k)
+    _, its, _ = fgmres(A.apply, mg, rhs_sine(k, nc, nc, nc), rtol=1e-10)
+    assert abs(info["iterations"] - its) <= 2
