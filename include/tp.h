@@ -240,9 +240,10 @@ tp_status tp_mg_coarse_solve(tp_mg mg, void* x, const void* b, void* stream);
  * restart are FP64; the preconditioner is one V-cycle of `mg` in its own
  * precision with zero initial guess (the input is converted, scaled by
  * sqrt(ndofs), and the output converted back). Orthogonalization: classical
- * Gram-Schmidt, repeated once when the projection removes more than half of
- * |w|^2 (|w_new| < |w_old| / sqrt 2, the "twice is enough" criterion). Stops
- * when the Arnoldi residual norm drops below rtol * ||b - A x0||. */
+ * Gram-Schmidt with one re-orthogonalization pass in every step (with a good
+ * preconditioner A M^-1 is close to the identity, so the first projection
+ * cancels most of w and the second pass is always needed). Stops when the
+ * Arnoldi residual norm drops below rtol * ||b - A x0||. */
 typedef struct tp_solver_s* tp_solver;
 
 typedef struct {
@@ -254,7 +255,7 @@ typedef struct {
   const double* history;   /* host array of relative residual estimates, one per iteration + 1;
                               owned by the solver, valid until the next solve or destroy */
   int history_len;
-  int reorthogonalizations;/* Arnoldi steps that needed the second Gram-Schmidt pass */
+  int reorthogonalizations;/* Arnoldi steps with the second Gram-Schmidt pass (every step) */
 } tp_solve_info;
 
 /* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's

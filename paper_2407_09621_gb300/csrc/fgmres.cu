@@ -255,41 +255,25 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
         e = cudaMemcpyAsync(s->Z[j], s->V[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, c.st);
       }
       if (e == cudaSuccess) e = launch_apply(s->A, s->w, s->Z[j], c.st);
-      // classical Gram-Schmidt with selective re-orthogonalization ("twice is enough"): the
-      // coefficients stay on the device; pass 1: h = V^T w and |w|^2; pass 2: w -= V h, |w|^2.
-      // Only when the projection cancelled most of w (|w_new| < |w_old| / sqrt 2) is the pass
-      // repeated on w (h2 = V^T w; w -= V h2, |w|^2) before v_{j+1} = w / |w|. One host read per
-      // step (two when the second pass runs).
+      // classical Gram-Schmidt with one re-orthogonalization pass; the coefficients stay on the
+      // device (h at dots[0..j], h2 at dots[m+1..], |w|^2 after pass 3), one host read per step:
+      //   pass 1: h = V^T w;  pass 2: w -= V h, h2 = V^T w;  pass 3: w -= V h2, |w|^2;  v_{j+1} = w/|w|
       std::vector<const double*> vj(s->V.begin(), s->V.begin() + j + 1);
-      std::vector<const double*> vjw(vj);
-      vjw.push_back(s->w);
-      double* d_h = s->dots;                 // h[0..j], |w_old|^2 at [j+1]
-      double* d_h2 = s->dots + (m + 2);      // h2[0..j]
-      double* d_n = s->dots + 2 * (m + 2);   // |w|^2 after a projection at [j+1]
-      if (e == cudaSuccess) e = multi_dot<double>(n, s->w, vjw.data(), j + 2, s->partial, d_h, c.st);
-      if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h, j + 1, 0, s->partial, d_n, c.st);
-      std::vector<double> hostd(3 * (m + 2), 0.0);
+      double* d_h = s->dots;
+      double* d_h2 = s->dots + (m + 1);
+      double* d_n = s->dots + 2 * (m + 1);
+      if (e == cudaSuccess) e = multi_dot<double>(n, s->w, vj.data(), j + 1, s->partial, d_h, c.st);
+      if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h, j + 1, 1, s->partial, d_h2, c.st);
+      if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h2, j + 1, 0, s->partial, d_n, c.st);
+      if (e == cudaSuccess) e = scale_inv_sqrt<double>(n, s->V[j + 1], s->w, d_n + j + 1, c.st);
+      std::vector<double> hostd(3 * (m + 2));
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(hostd.data(), s->dots, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, c.st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
       if (e != cudaSuccess) break;
-      const double w_old2 = hostd[j + 1];
-      double w_new2 = hostd[2 * (m + 2) + j + 1];
-      for (int i = 0; i <= j; ++i) h[i] = hostd[i];
-      if (w_new2 < 0.5 * w_old2) {
-        e = multi_dot<double>(n, s->w, vj.data(), j + 1, s->partial, d_h2, c.st);
-        if (e == cudaSuccess) e = multi_axpy_dot<double>(n, s->w, vj.data(), d_h2, j + 1, 0, s->partial, d_n, c.st);
-        if (e == cudaSuccess)
-          e = cudaMemcpyAsync(hostd.data(), s->dots, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, c.st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
-        if (e != cudaSuccess) break;
-        for (int i = 0; i <= j; ++i) h[i] += hostd[(m + 2) + i];
-        w_new2 = hostd[2 * (m + 2) + j + 1];
-        ++s->reorth;
-      }
-      if (e == cudaSuccess) e = scale_inv_sqrt<double>(n, s->V[j + 1], s->w, d_n + j + 1, c.st);
-      if (e != cudaSuccess) break;
-      const double hn = std::sqrt(w_new2);
+      ++s->reorth;
+      for (int i = 0; i <= j; ++i) h[i] = hostd[i] + hostd[m + 1 + i];
+      const double hn = std::sqrt(hostd[2 * (m + 1) + j + 1]);
       for (int i = 0; i <= j; ++i) Hij(i, j) = h[i];
       Hij(j + 1, j) = hn;
       bool finite = std::isfinite(hn);
