@@ -50,6 +50,32 @@ __host__ __device__ constexpr size_t cc_smem_bytes() {
   return sizeof(TC) * cc_cells_per_block<N, V>() * 4 * N * N * N;
 }
 
+// out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst):
+// e_m = in[m] + in[n-1-m], o_m = in[m] - in[n-1-m]; ev_i = AE e, od_i = AO o;
+// out[i] = ev_i + od_i, out[n-1-i] = ev_i - od_i. n^2/2 + 2n operations instead of n^2.
+template <typename TC, int N>
+__device__ __forceinline__ void contract_eo(TC (&out)[N], const TC (&AE)[kMaxN / 2][kMaxN / 2],
+                                            const TC (&AO)[kMaxN / 2][kMaxN / 2], const TC (&in)[N]) {
+  constexpr int H = N / 2;
+  TC e[H], o[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    e[m] = in[m] + in[N - 1 - m];
+    o[m] = in[m] - in[N - 1 - m];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    TC ev = AE[i][0] * e[0], od = AO[i][0] * o[0];
+#pragma unroll
+    for (int m = 1; m < H; ++m) {
+      ev = fma(AE[i][m], e[m], ev);
+      od = fma(AO[i][m], o[m], od);
+    }
+    out[i] = ev + od;
+    out[N - 1 - i] = ev - od;
+  }
+}
+
 template <typename TC, int N>
 __device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A, const TC (&in)[N]) {
 #pragma unroll
@@ -59,6 +85,22 @@ __device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A,
     for (int m = 1; m < N; ++m) s = fma(A[i * kMaxN + m], in[m], s);
     out[i] = s;
   }
+}
+
+// out = (M or G)_d in: the even-odd form for even n >= 6 when the matrices are centrosymmetric
+// (always on the symmetric Gauss-Lobatto element; checked on the host), the plain form otherwise.
+template <typename TC, int N>
+__device__ __forceinline__ void contract_d(TC (&out)[N], const OpConst<TC>& P, bool mass, int d, const TC (&in)[N]) {
+  if constexpr (N % 2 == 0 && N >= 6) {
+    if (P.centro) {
+      if (mass)
+        contract_eo<TC, N>(out, P.ME[d], P.MO[d], in);
+      else
+        contract_eo<TC, N>(out, P.GE[d], P.GO[d], in);
+      return;
+    }
+  }
+  contract<TC, N>(out, mass ? P.M[d] : P.G[d], in);
 }
 
 template <typename TS, typename TC, int N, int V>
@@ -94,7 +136,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     TC u[N], w[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) u[m] = sU[p * N2 + q * N + m];
-    contract<TC, N>(w, P.G[0], u);
+    contract_d<TC, N>(w, P, false, 0, u);
     if (valid) {
       const TS* lo = cx > 0 ? xc - N3 + p * N2 + q * N : nullptr;
       const TS* hi = cx < nx - 1 ? xc + N3 + p * N2 + q * N : nullptr;
@@ -104,7 +146,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     for (int i = 0; i < N; ++i) sX[p * N2 + q * N + i] = w[i];
 #pragma unroll
     for (int m = 0; m < N; ++m) u[m] = sU[p * N2 + m * N + q];
-    contract<TC, N>(w, P.G[1], u);
+    contract_d<TC, N>(w, P, false, 1, u);
     if (valid) {
       const TS* lo = cy > 0 ? xc - sy + p * N2 + q : nullptr;
       const TS* hi = cy < ny - 1 ? xc + sy + p * N2 + q : nullptr;
@@ -120,7 +162,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     TC u[N], w[N], v[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) u[m] = sU[m * N2 + t];
-    contract<TC, N>(w, P.G[2], u);
+    contract_d<TC, N>(w, P, false, 2, u);
     if (valid) {
       const TS* lo = cz > 0 ? xc - sz + t : nullptr;
       const TS* hi = cz < nz - 1 ? xc + sz + t : nullptr;
@@ -128,7 +170,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     }
 #pragma unroll
     for (int l = 0; l < N; ++l) w[l] += sX[l * N2 + t] + sY[l * N2 + t];
-    contract<TC, N>(v, P.M[2], w);
+    contract_d<TC, N>(v, P, true, 2, w);
 #pragma unroll
     for (int l = 0; l < N; ++l) sZ[l * N2 + t] = v[l];
   }
@@ -139,7 +181,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     TC w[N], v[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) w[m] = sZ[p * N2 + m * N + q];
-    contract<TC, N>(v, P.M[1], w);
+    contract_d<TC, N>(v, P, true, 1, w);
 #pragma unroll
     for (int j = 0; j < N; ++j) sX[p * N2 + j * N + q] = v[j];
   }
@@ -150,7 +192,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
     TC w[N], v[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) w[m] = sX[p * N2 + q * N + m];
-    contract<TC, N>(v, P.M[0], w);
+    contract_d<TC, N>(v, P, true, 0, w);
     TS* yc = y + cell * N3 + p * N2 + q * N;
 #pragma unroll
     for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, v[i]);

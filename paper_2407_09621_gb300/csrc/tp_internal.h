@@ -52,6 +52,12 @@ struct OpConst {
   T G[3][kMaxN * kMaxN];
   T d0[kMaxN], d1[kMaxN];
   T E[3][8][kMaxN];
+  // Even-odd halves of the centrosymmetric M and G (A[n-1-i][n-1-m] = A[i][m], the reference
+  // element and the Gauss-Lobatto nodes being symmetric about 1/2), for i, m < n/2:
+  // AE[i][m] = (A[i][m] + A[i][n-1-m]) / 2 and AO[i][m] = (A[i][m] - A[i][n-1-m]) / 2.
+  T ME[3][kMaxN / 2][kMaxN / 2], MO[3][kMaxN / 2][kMaxN / 2];
+  T GE[3][kMaxN / 2][kMaxN / 2], GO[3][kMaxN / 2][kMaxN / 2];
+  int centro;  // 1 if every M and G above is centrosymmetric (to 1e-12 relative)
 };
 
 // Kernel parameters of the Blackwell tensor-core apply (apply_umma.cu).
