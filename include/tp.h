@@ -315,6 +315,22 @@ typedef struct {
 tp_status tp_batch_solve(const tp_batch_problem* probs, int count, const tp_batch_opts* opts,
                          tp_batch_result* results, double* total_seconds);
 
+/* Batched solves over the caller's own problems: entry i solves A_i x[i] = b[i] with
+ * solvers[i] (its FP64 operator A_i and, optionally, its V-cycle preconditioner, built
+ * by tp_fgmres_create on meshes and degrees of any size), x[i] the initial guess and
+ * result, b[i] the right-hand side (DEVICE FP64 vectors of A_i's size, owned by the
+ * caller). The solves run concurrently as in tp_batch_solve (opts: rtol, maxit and
+ * streams are used; NULL = defaults). The solvers run at the same time, so no solver
+ * and no multigrid object may appear twice. infos and statuses (count entries each,
+ * may be NULL) receive each solve's tp_solve_info (its history stays owned by that
+ * solver) and tp_status; *total_seconds (may be NULL) the wall time of the concurrent
+ * phase. Blocks until done. Errors: TP_ERR_INVALID_ARG (NULL entries, duplicates,
+ * options), TP_ERR_CUDA, or the first solve's hard failure; solves that only miss the
+ * tolerance report TP_ERR_NOT_CONVERGED in statuses. */
+tp_status tp_batch_solve_solvers(const tp_solver* solvers, double* const* x, const double* const* b, int count,
+                                 const tp_batch_opts* opts, tp_solve_info* infos, tp_status* statuses,
+                                 double* total_seconds);
+
 /* ------------------------------------------------------------------ Poisson problem data
  * Manufactured problems of Sec. 7.2: u = sum_m a[m] sin(p pi x/lx) sin(q pi y/ly) sin(r pi z/lz)
  * with (p, q, r) = pqr[3m..3m+2] >= 1, 1 <= nmodes <= 16; on the unit cube the

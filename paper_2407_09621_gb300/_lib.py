@@ -263,6 +263,28 @@ def tp_op_check(op):
     _check(lib.tp_op_check(op))
 
 
+lib.tp_batch_solve_solvers.restype = ctypes.c_int
+lib.tp_batch_solve_solvers.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+
+
+def tp_batch_solve_solvers(solvers, x_ptrs, b_ptrs, rtol=1e-10, maxit=300, streams=8):
+    """Concurrent solves of the caller's (solver, x, b) entries; returns (infos, statuses, seconds)."""
+    n = len(solvers)
+    if not (n == len(x_ptrs) == len(b_ptrs)):
+        raise ValueError("solvers, x_ptrs and b_ptrs must have the same length")
+    sv = (_vp * n)(*[s if isinstance(s, _vp) else _vp(s) for s in solvers])
+    xv = (_vp * n)(*[_vp(p) for p in x_ptrs])
+    bv = (_vp * n)(*[_vp(p) for p in b_ptrs])
+    opts = tp_batch_opts(TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, rtol, maxit, streams, 0)
+    infos = (tp_solve_info * n)()
+    sts = (ctypes.c_int * n)()
+    total = ctypes.c_double()
+    _check(lib.tp_batch_solve_solvers(sv, xv, bv, n, ctypes.byref(opts), infos, sts, ctypes.byref(total)))
+    out = [{"iterations": i.iterations, "converged": i.converged, "rel_residual": i.rel_residual,
+            "true_rel_residual": i.true_rel_residual} for i in infos]
+    return out, list(sts), total.value
+
+
 # ---------------------------------------------------------------- Poisson problem data
 lib.tp_rhs_sines.restype = ctypes.c_int
 lib.tp_rhs_sines.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), _vp]

@@ -24,6 +24,8 @@
 namespace tp {
 tp_status cuda_status(int err, const char* what);
 void fgmres_prepare(tp_solver_s* s);
+long long solver_ndofs(const tp_solver_s* s);
+const void* solver_mg(const tp_solver_s* s);
 }  // namespace tp
 
 using namespace tp;
@@ -49,6 +51,71 @@ void release(Item& it) {
   if (it.b) cudaFree(it.b);
   if (it.own_x && it.x) cudaFree(it.x);
   it = Item();
+}
+
+}  // namespace
+
+namespace {
+
+// One FGMRES solve per entry, run by `streams` host worker threads with one non-blocking CUDA stream
+// each, taking entries from a shared queue ordered by size (largest first). zero_x: start from
+// x = 0 (else the given x is the initial guess). Returns the first hard failure (not-converged
+// solves only report it in their status).
+tp_status run_concurrent(int count, tp_solver_s* const* solvers, double* const* x, const double* const* b,
+                         const long long* ndofs, double rtol, int maxit, int streams, bool zero_x,
+                         tp_solve_info* infos, tp_status* statuses, double* seconds, double* total_seconds) {
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return ndofs[a] > ndofs[c]; });
+  std::atomic<int> next{0};
+  std::mutex err_mu;
+  tp_status worker_status = TP_OK;
+  char worker_err[512] = "";
+  int device = 0;
+  cudaGetDevice(&device);
+  const int nthreads = std::min(streams, count);
+  const auto t0 = std::chrono::steady_clock::now();
+  auto worker = [&]() {
+    cudaSetDevice(device);
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      std::lock_guard<std::mutex> lock(err_mu);
+      worker_status = TP_ERR_CUDA;
+      snprintf(worker_err, sizeof(worker_err), "batched solve: stream creation failed");
+      return;
+    }
+    for (;;) {
+      const int q = next.fetch_add(1);
+      if (q >= count) break;
+      const int i = order[q];
+      const auto ts = std::chrono::steady_clock::now();
+      tp_solve_info info;
+      memset(&info, 0, sizeof(info));
+      tp_status r = zero_x ? cuda_status(cudaMemsetAsync(x[i], 0, sizeof(double) * ndofs[i], s), "batched solve")
+                           : TP_OK;
+      if (r == TP_OK) r = tp_fgmres_solve(solvers[i], x[i], b[i], rtol, maxit, &info, s);
+      const auto te = std::chrono::steady_clock::now();
+      if (infos) infos[i] = info;
+      if (statuses) statuses[i] = r;
+      if (seconds) seconds[i] = std::chrono::duration<double>(te - ts).count();
+      if (r != TP_OK && r != TP_ERR_NOT_CONVERGED) {
+        std::lock_guard<std::mutex> lock(err_mu);
+        if (worker_status == TP_OK) {
+          worker_status = r;
+          snprintf(worker_err, sizeof(worker_err), "%s", tp_last_error());
+        }
+      }
+    }
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (std::thread& t : pool) t.join();
+  const auto t1 = std::chrono::steady_clock::now();
+  if (total_seconds) *total_seconds = std::chrono::duration<double>(t1 - t0).count();
+  if (worker_status != TP_OK) set_error("%s", worker_err);
+  return worker_status;
 }
 
 }  // namespace
@@ -98,57 +165,30 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     return st;
   }
   // ---- concurrent solves (timed)
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return items[a].ndofs > items[b].ndofs; });
-  std::atomic<int> next{0};
-  std::mutex err_mu;
-  tp_status worker_status = TP_OK;
+  std::vector<tp_solver_s*> sol(count);
+  std::vector<double*> xs(count);
+  std::vector<const double*> bs(count);
+  std::vector<long long> nd(count);
+  std::vector<tp_solve_info> infos(count);
+  std::vector<tp_status> sts(count, TP_OK);
+  std::vector<double> secs(count, 0.0);
+  for (int i = 0; i < count; ++i) {
+    sol[i] = items[i].solver;
+    xs[i] = items[i].x;
+    bs[i] = items[i].b;
+    nd[i] = items[i].ndofs;
+  }
+  tp_status worker_status = run_concurrent(count, sol.data(), xs.data(), bs.data(), nd.data(), o.rtol, o.maxit,
+                                           o.streams, true, infos.data(), sts.data(), secs.data(), total_seconds);
   char worker_err[512] = "";
-  int device = 0;
-  cudaGetDevice(&device);
-  const int nthreads = std::min(o.streams, count);
-  const auto t0 = std::chrono::steady_clock::now();
-  auto worker = [&]() {
-    cudaSetDevice(device);
-    cudaStream_t s;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-      std::lock_guard<std::mutex> lock(err_mu);
-      worker_status = TP_ERR_CUDA;
-      snprintf(worker_err, sizeof(worker_err), "tp_batch_solve: stream creation failed");
-      return;
-    }
-    for (;;) {
-      const int q = next.fetch_add(1);
-      if (q >= count) break;
-      const int i = order[q];
-      Item& it = items[i];
-      const auto ts = std::chrono::steady_clock::now();
-      tp_solve_info info;
-      tp_status r = cuda_status(cudaMemsetAsync(it.x, 0, sizeof(double) * it.ndofs, s), "tp_batch_solve");
-      if (r == TP_OK) r = tp_fgmres_solve(it.solver, it.x, it.b, o.rtol, o.maxit, &info, s);
-      const auto te = std::chrono::steady_clock::now();
-      results[i].iterations = info.iterations;
-      results[i].converged = info.converged;
-      results[i].true_rel_residual = info.true_rel_residual;
-      results[i].seconds = std::chrono::duration<double>(te - ts).count();
-      results[i].status = r;
-      if (r != TP_OK && r != TP_ERR_NOT_CONVERGED) {
-        std::lock_guard<std::mutex> lock(err_mu);
-        if (worker_status == TP_OK) {
-          worker_status = r;
-          snprintf(worker_err, sizeof(worker_err), "%s", tp_last_error());
-        }
-      }
-    }
-    cudaStreamSynchronize(s);
-    cudaStreamDestroy(s);
-  };
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
-  for (std::thread& t : pool) t.join();
-  const auto t1 = std::chrono::steady_clock::now();
-  if (total_seconds) *total_seconds = std::chrono::duration<double>(t1 - t0).count();
+  if (worker_status != TP_OK) snprintf(worker_err, sizeof(worker_err), "%s", tp_last_error());
+  for (int i = 0; i < count; ++i) {
+    results[i].iterations = infos[i].iterations;
+    results[i].converged = infos[i].converged;
+    results[i].true_rel_residual = infos[i].true_rel_residual;
+    results[i].seconds = secs[i];
+    results[i].status = sts[i];
+  }
   // ---- errors against the manufactured solutions (not timed)
   for (int i = 0; i < count && worker_status == TP_OK; ++i) {
     const tp_batch_problem& p = probs[i];
@@ -161,4 +201,43 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     return worker_status;
   }
   return TP_OK;
+}
+
+extern "C" tp_status tp_batch_solve_solvers(const tp_solver* solvers, double* const* x, const double* const* b,
+                                            int count, const tp_batch_opts* opts, tp_solve_info* infos,
+                                            tp_status* statuses, double* total_seconds) {
+  if (!solvers || !x || !b || count < 1) {
+    set_error("tp_batch_solve_solvers: need solvers, x and b arrays and count >= 1");
+    return TP_ERR_INVALID_ARG;
+  }
+  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0};
+  if (opts) o = *opts;
+  if (o.streams < 1 || o.streams > 64 || !(o.rtol > 0) || o.maxit < 1) {
+    set_error("tp_batch_solve_solvers: invalid options (streams 1..64, rtol > 0, maxit >= 1)");
+    return TP_ERR_INVALID_ARG;
+  }
+  std::vector<long long> nd(count);
+  for (int i = 0; i < count; ++i) {
+    if (!solvers[i] || !x[i] || !b[i]) {
+      set_error("tp_batch_solve_solvers: NULL solver or vector at entry %d", i);
+      return TP_ERR_INVALID_ARG;
+    }
+    nd[i] = solver_ndofs(solvers[i]);
+  }
+  // solvers run concurrently: each must own its state (no solver or multigrid object twice)
+  std::vector<const void*> owners;
+  for (int i = 0; i < count; ++i) {
+    owners.push_back(solvers[i]);
+    if (solver_mg(solvers[i])) owners.push_back(solver_mg(solvers[i]));
+  }
+  std::sort(owners.begin(), owners.end());
+  if (std::adjacent_find(owners.begin(), owners.end()) != owners.end()) {
+    set_error("tp_batch_solve_solvers: a solver or multigrid object appears twice in the batch");
+    return TP_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < count; ++i) fgmres_prepare(solvers[i]);
+  tp_status st = cuda_status(cudaDeviceSynchronize(), "tp_batch_solve_solvers set-up");
+  if (st != TP_OK) return st;
+  return run_concurrent(count, const_cast<tp_solver_s* const*>(solvers), x, b, nd.data(), o.rtol, o.maxit, o.streams,
+                        false, infos, statuses, nullptr, total_seconds);
 }

@@ -342,6 +342,9 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
 }
 
 namespace tp {
+long long solver_ndofs(const tp_solver_s* s) { return s->n; }
+const void* solver_mg(const tp_solver_s* s) { return s->mg; }
+
 // Captures the preconditioner's V-cycle graph ahead of the first solve (used by batched
 // set-up so that capture happens outside the timed, multi-threaded solve phase).
 void fgmres_prepare(tp_solver_s* s) {

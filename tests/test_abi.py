@@ -65,3 +65,15 @@ def test_failed_operator_creation_releases_mesh_once():
         with pytest.raises(TPError):
             DGLaplace(2, 2, 2, 4, "fp64", kernel=2)  # FP64 tensor kernel: k = 3, 7 only
         gc.collect()
+
+
+def test_library_resolves_all_of_its_own_symbols():
+    """libtp.so must not leave any of its own functions undefined (a shared library links even
+    when an internal declaration has no definition; the call would fail only at run time)."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--undefined-only", _lib.LIB_PATH], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("nm unavailable")
+    undefined = [l.split()[-1] for l in out.stdout.splitlines() if l.strip()]
+    own = [u for u in undefined if u.startswith("tp_") or "2tp" in u]
+    assert own == []

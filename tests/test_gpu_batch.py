@@ -48,3 +48,37 @@ def test_concurrent_equals_sequential():
     for a, b in zip(r_seq, r_con):
         assert a["iterations"] == b["iterations"]
         assert abs(a["l2_error"] - b["l2_error"]) <= 1e-12 + 1e-9 * a["l2_error"]
+
+
+def test_batch_over_caller_solvers_matches_exact_discrete_solutions():
+    """tp_batch_solve_solvers: the caller's own (solver, x, b) entries of uneven sizes and degrees,
+    solved concurrently, each against its exact discrete solution; a solver listed twice is
+    rejected before any work."""
+    from paper_2407_09621_gb300 import _lib
+    from oracle.solve import rhs_sine
+    specs = [(8, 2), (6, 3), (4, 5), (5, 1)]
+    objs, xs, bs = [], [], []
+    try:
+        for nc, k in specs:
+            mesh = _lib.tp_mesh_create(nc, nc, nc)
+            op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+            mg = _lib.tp_mg_create(op, precision=_lib.TP_FP32, coarse_cells=2)
+            solver = _lib.tp_fgmres_create(op, mg, 30)
+            objs.append((mesh, op, mg, solver))
+            bs.append(torch.from_numpy(rhs_sine(k, nc, nc, nc)).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        infos, sts, total = _lib.tp_batch_solve_solvers([o[3] for o in objs], [x.data_ptr() for x in xs],
+                                                        [b.data_ptr() for b in bs], streams=3)
+        assert total > 0 and sts == [0] * len(specs)
+        for (nc, k), x, info in zip(specs, xs, infos):
+            assert info["converged"] == 1
+            u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+            assert rel_l2(x.cpu().numpy(), u) < 1e-7
+        with pytest.raises(_lib.TPError):
+            _lib.tp_batch_solve_solvers([objs[0][3], objs[0][3]], [xs[0].data_ptr()] * 2, [bs[0].data_ptr()] * 2)
+    finally:
+        for mesh, op, mg, solver in objs:
+            _lib.tp_solver_destroy(solver)
+            _lib.tp_mg_destroy(mg)
+            _lib.tp_op_destroy(op)
+            _lib.tp_mesh_destroy(mesh)
