@@ -56,7 +56,10 @@ typedef enum { TP_KERNEL_AUTO = 0, TP_KERNEL_CUDA_CORE = 1, TP_KERNEL_TENSOR = 2
 typedef struct {
   int penalty;  /* tp_penalty */
   int kernel;   /* tp_kernel */
-  int ec;       /* 1: error-corrected half-precision products (Algorithm 1), tensor kernel only */
+  int ec;       /* error-corrected half-precision products, tensor kernel only: 0 off, 1 both
+                   operands split (Algorithm 1), 2 the operator matrices only, 3 the vector-side
+                   operand only (the FP32 vector and the intermediate W; with FP16/BF16 vectors
+                   the vector is exact, so 3 is 0 for FP16 and 1 for BF16, which always splits) */
   int tc_type;  /* operand type of the tensor kernel: TP_FP16 (default) or TP_BF16; for FP16/BF16
                    vectors it must equal the vector type */
   int autotune; /* 1: at creation, time the tile shapes of the apply kernel (CUDA-core and DMMA:

@@ -97,10 +97,11 @@ __device__ __forceinline__ void mma16816<__nv_bfloat16>(float (&c)[4], const uin
 }
 
 // acc (16 cells x 64) = A_rows (16 x 64, shared, row stride kTcRow) * B^T, B stored [out][in].
-// With EC: main = Ah Bh, corr = Al Bh + Ah Bl (Al may be absent: has_al = false).
+// With EC: main = Ah Bh, corr = Al Bh (has_al: the A operand is refined) + Ah Bl (has_bl: the
+// matrix is refined); Algorithm 1 refines both.
 template <typename TO, bool EC>
 __device__ __forceinline__ void tile_gemm(float (&acc)[8][4], float (&cor)[8][4], const TO* Ah, const TO* Al,
-                                          bool has_al, const TO* Bh, const TO* Bl, int lane) {
+                                          bool has_al, const TO* Bh, const TO* Bl, bool has_bl, int lane) {
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
@@ -122,10 +123,12 @@ __device__ __forceinline__ void tile_gemm(float (&acc)[8][4], float (&cor)[8][4]
       mma16816<TO>(acc[2 * np], ah, b[0], b[1]);
       mma16816<TO>(acc[2 * np + 1], ah, b[2], b[3]);
       if (EC) {
-        uint32_t bl[4];
-        ldsm_x4(smem_u32(Bl + (np * 16 + brow) * kTcRow + ks * 16 + bcol), bl[0], bl[1], bl[2], bl[3]);
-        mma16816<TO>(cor[2 * np], ah, bl[0], bl[1]);
-        mma16816<TO>(cor[2 * np + 1], ah, bl[2], bl[3]);
+        if (has_bl) {
+          uint32_t bl[4];
+          ldsm_x4(smem_u32(Bl + (np * 16 + brow) * kTcRow + ks * 16 + bcol), bl[0], bl[1], bl[2], bl[3]);
+          mma16816<TO>(cor[2 * np], ah, bl[0], bl[1]);
+          mma16816<TO>(cor[2 * np + 1], ah, bl[2], bl[3]);
+        }
         if (has_al) {
           mma16816<TO>(cor[2 * np], al, b[0], b[1]);
           mma16816<TO>(cor[2 * np + 1], al, b[2], b[3]);
@@ -181,6 +184,7 @@ struct TcDims {
   long long ncells;
   float scale, inv_scale;  // 2^s and 2^-s of Algorithm 1
   float k3_inv, m3_inv;    // the operand matrices are stored times powers of two k3, m3
+  int refine_vec, refine_mat;  // error-correction mode (both 1: Algorithm 1)
 };
 
 // Copies cells [first, first + count) of x into dst (zeros outside [0, ncells)),
@@ -268,8 +272,8 @@ __global__ void __launch_bounds__(128) apply_tc_kernel(const TS* __restrict__ x,
 
   float acc[8][4], cor[8][4];
   // ---- W = U K3^T
-  tile_gemm<TO, EC>(acc, cor, sAh + 16 * w * kTcRow, sAl + 16 * w * kTcRow, EC && sizeof(TS) == 4, sK,
-                    sK + MAT, lane);
+  tile_gemm<TO, EC>(acc, cor, sAh + 16 * w * kTcRow, sAl + 16 * w * kTcRow, EC && sizeof(TS) == 4 && D.refine_vec,
+                    sK, sK + MAT, D.refine_mat != 0, lane);
   store_acc<EC>(sW, acc, cor, w, lane, D.inv_scale, sRow);
   __syncthreads();
 
@@ -348,7 +352,8 @@ __global__ void __launch_bounds__(128) apply_tc_kernel(const TS* __restrict__ x,
   __syncthreads();
 
   // ---- V = W M3^T
-  tile_gemm<TO, EC>(acc, cor, sAh + 16 * w * kTcRow, sAl + 16 * w * kTcRow, EC, sM, sM + MAT, lane);
+  tile_gemm<TO, EC>(acc, cor, sAh + 16 * w * kTcRow, sAl + 16 * w * kTcRow, EC && D.refine_vec, sM, sM + MAT,
+                    D.refine_mat != 0, lane);
   store_acc<EC>(sW, acc, cor, w, lane, D.inv_scale, sRow);
   __syncthreads();
 
@@ -464,6 +469,9 @@ static cudaError_t launch_tc_t(const tp_op_s* op, void* y, const void* x, cudaSt
   tc_scales(op, sk, sm);
   D.k3_inv = (float)(1.0 / sk);
   D.m3_inv = (float)(1.0 / sm);
+  // error-correction mode: 1 both operands (Algorithm 1), 2 the matrix only, 3 the vector only
+  D.refine_vec = op->opts.ec == 1 || op->opts.ec == 3;
+  D.refine_mat = op->opts.ec == 1 || op->opts.ec == 2;
   // persistent blocks: every block copies the operand matrices once and walks over tiles
   const long long tiles = (op->ncells + kTcCells - 1) / kTcCells;
   const long long cap = (long long)op->tc_blocks_per_sm * op->sm_count;

@@ -352,6 +352,10 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: tc_type must be TP_FP16 or TP_BF16");
     return TP_ERR_INVALID_ARG;
   }
+  if (o.ec < 0 || o.ec > 3) {
+    set_error("tp_dg_laplace_create: ec must be 0 (off), 1 (both operands), 2 (matrix) or 3 (vector)");
+    return TP_ERR_INVALID_ARG;
+  }
   if (o.kernel == TP_KERNEL_TENSOR && p == TP_FP64) {
     if (k != 3 && k != 7) {
       set_error("tp_dg_laplace_create: the FP64 tensor (DMMA) kernel supports k = 3 and k = 7");
@@ -369,7 +373,9 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     if ((p == TP_FP16 || p == TP_BF16) && o.tc_type != (int)p) o.tc_type = p;
     // BF16 keeps 8 significand bits: without the split of Algorithm 1 the five roundings of the
     // tensor path (input, K3, W, M3, output) exceed the 5e-3 per-apply tolerance
-    if (p == TP_BF16) o.ec = 1;
+    if (p == TP_BF16 && o.ec != 1 && o.ec != 2) o.ec = 1;
+    // FP16/BF16 vectors are exact operands: refining "the vector" alone refines nothing
+    if (p == TP_FP16 && o.ec == 3) o.ec = 0;
   } else if (o.ec) {
     set_error("tp_dg_laplace_create: error correction needs the tensor kernel");
     return TP_ERR_UNSUPPORTED;

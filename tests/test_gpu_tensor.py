@@ -151,3 +151,18 @@ def test_tensor_path_selection(k, prec, path):
         assert op.info["tensor_path"] == path
     finally:
         op.close()
+
+
+@pytest.mark.parametrize("tc_type", [TP_FP16, TP_BF16])
+def test_error_correction_modes_order_the_errors(tc_type):
+    """Refining one operand of the half-precision products (ec = 2: the operator matrices, ec = 3:
+    the vector side) removes one of the two rounding contributions; refining both (Algorithm 1,
+    ec = 1) removes both."""
+    dims, k = (6, 5, 7), 3
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * 64, seed=31)
+    ref = BlockOperator(m, k).apply(x)
+    err = {ec: rel_l2(_apply_tc(dims, k, "fp32", x, ec=ec, tc_type=tc_type), ref) for ec in (0, 1, 2, 3)}
+    assert err[1] < 1e-2 * err[0]
+    assert err[2] < err[0] and err[3] < err[0]
+    assert err[1] < min(err[2], err[3])
