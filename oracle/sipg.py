@@ -28,9 +28,10 @@ Layout: cell-major, g = ((cz*ny + cy)*nx + cx)*n^3 + (l*n + j)*n + i with
 n = k+1 and i the x node (fastest).
 
 Pinned by tests/test_oracle_sipg.py: brute-force 3D quadrature of Eq. (2)
-on one- and two-cell meshes (oracle/brute.py), symmetry, positive
-definiteness, the hand-derived k = 1 one-cell 1D matrix, the spectral
-closed form of Eq. (9), and agreement of the global and block forms.
+on one- and two-cell meshes (oracle/brute.py; k <= 5, 7 and 8), symmetry,
+positive definiteness, the hand-derived k = 1 one-cell 1D matrix, the
+spectral closed form of Eq. (9), and agreement of the global, block and
+Kronecker-sum forms (``kron_apply``, the one used for degrees up to 15).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -321,3 +322,21 @@ def lex_to_cell_major(k, nx, ny, nz):
                                       np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     gx, gy, gz = cx * n + i, cy * n + j, cz * n + l
     return ((gz * (ny * n) + gy) * (nx * n) + gx).reshape(-1)
+
+
+def kron_apply(x, k, dims, lengths=(1.0, 1.0, 1.0), pen="config"):
+    """y = A x by the Kronecker-sum form of Eq. (9) with each direction's global 1D factors:
+    A = L_z (x) M_y (x) M_x + M_z (x) L_y (x) M_x + M_z (x) M_y (x) L_x in the lexicographic
+    global-node order, x and y in the cell-major layout. The 1D factors are dense (nc*n
+    square), so this serves meshes of a few cells per direction at any degree."""
+    nx, ny, nz = dims
+    n = k + 1
+    (Mx, Lx), (My, Ly), (Mz, Lz) = [global_1d(k, nc, length=ln, pen=pen) for nc, ln in zip(dims, lengths)]
+    perm = lex_to_cell_major(k, nx, ny, nz)
+    x_lex = np.empty(len(perm))
+    x_lex[perm] = np.asarray(x, dtype=np.float64)
+    X = x_lex.reshape(nz * n, ny * n, nx * n)
+    Y = (np.einsum("zc,yb,xa,cba->zyx", Lz, My, Mx, X, optimize=True)
+         + np.einsum("zc,yb,xa,cba->zyx", Mz, Ly, Mx, X, optimize=True)
+         + np.einsum("zc,yb,xa,cba->zyx", Mz, My, Lx, X, optimize=True))
+    return Y.reshape(-1)[perm]

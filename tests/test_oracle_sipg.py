@@ -10,7 +10,7 @@ import scipy.linalg as sla
 import scipy.sparse.linalg as spla
 
 from oracle.brute import assemble_dense
-from oracle.sipg import (Mesh, assemble, BlockOperator, global_1d, lex_to_cell_major,
+from oracle.sipg import (Mesh, assemble, BlockOperator, global_1d, kron_apply, lex_to_cell_major,
                          penalty, Ref1D)
 from oracle.solve import FastDiag, rhs_sine, l2_error, sine_exact
 
@@ -37,6 +37,12 @@ def test_brute_force_anisotropic_cells(pen):
 def test_brute_force_k7_one_cell():
     m = Mesh(1, 1, 1)
     assert _rel(assemble(m, 7).toarray(), assemble_dense(m, 7)) < 1e-13
+
+
+def test_brute_force_k8_one_cell():
+    # the first degree of the arbitrary-size range (n = 9): 3D quadrature of Eq. (2), 729 x 729
+    m = Mesh(1, 1, 1)
+    assert _rel(assemble(m, 8).toarray(), assemble_dense(m, 8)) < 1e-13
 
 
 def test_hand_worked_k1_one_cell():
@@ -86,6 +92,51 @@ def test_spectral_closed_form(k):
         v = np.kron(Vz[:, c], np.kron(Vy[:, b], Vx[:, a]))[perm]
         w = (lx[a] + ly[b] + lz[c]) * np.kron(Mz @ Vz[:, c], np.kron(My @ Vy[:, b], Mx @ Vx[:, a]))[perm]
         assert _rel(A @ v, w) < 1e-12
+
+
+@pytest.mark.parametrize("k,dims,lengths,pen", [
+    (1, (3, 2, 4), (1.0, 1.0, 1.0), "config"), (2, (4, 3, 2), (0.7, 1.9, 0.45), "paper"),
+    (3, (2, 3, 1), (1.0, 1.0, 1.0), "config"), (5, (1, 2, 3), (1.3, 0.6, 1.0), "config")])
+def test_kron_apply_matches_assembled_matrix(k, dims, lengths, pen):
+    # Kronecker-sum form of Eq. (9) (global 1D factors) against the element + face assembly
+    A = assemble(Mesh(*dims, *lengths), k, pen)
+    x = np.random.default_rng(k).uniform(-1, 1, A.shape[0])
+    assert _rel(kron_apply(x, k, dims, lengths, pen), A @ x) < 1e-14
+
+
+def test_kron_apply_matches_block_operator_k8():
+    # element/face block rows (pinned to quadrature at k = 8 above) against the Kronecker sum
+    dims = (2, 1, 3)
+    bo = BlockOperator(Mesh(*dims), 8)
+    x = np.random.default_rng(8).uniform(-1, 1, 6 * 9 ** 3)
+    assert _rel(kron_apply(x, 8, dims), bo.apply(x)) < 1e-13
+
+
+@pytest.mark.parametrize("k", [11, 15])
+def test_high_degree_1d_lowest_eigenvalue(k):
+    # the face terms of the global 1D stiffness at high degree: lowest eigenvalue of
+    # -u'' = lam u with u(0) = u(1) = 0 on 3 cells is pi^2 to spectral accuracy
+    M, L = global_1d(k, 3)
+    lam = sla.eigh(L, M, eigvals_only=True)[0]
+    assert abs(lam - np.pi ** 2) < 1e-9 * np.pi ** 2
+
+
+@pytest.mark.parametrize("k", [12, 15])
+def test_kron_apply_spectral_closed_form_high_degree(k):
+    # tensor products of 1D generalized eigenvectors V (L V = M V diag(lam)) are mapped to
+    # (lam_a + lam_b + lam_c) M v: checks the index order of the Kronecker sum on an anisotropic mesh
+    dims = (3, 1, 2)
+    eig = []
+    for nc in dims:
+        M, L = global_1d(k, nc)
+        lam, V = sla.eigh(L, M)
+        eig.append((M, lam, V))
+    perm = lex_to_cell_major(k, *dims)
+    (Mx, lx, Vx), (My, ly, Vy), (Mz, lz, Vz) = eig
+    for (a, b, c) in [(0, 0, 0), (5, 3, 7), (30, 2, 19)]:
+        v = np.kron(Vz[:, c], np.kron(Vy[:, b], Vx[:, a]))[perm]
+        w = (lx[a] + ly[b] + lz[c]) * np.kron(Mz @ Vz[:, c], np.kron(My @ Vy[:, b], Mx @ Vx[:, a]))[perm]
+        assert _rel(kron_apply(v, k, dims), w) < 1e-11
 
 
 @pytest.mark.parametrize("k", [2, 3])
