@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
     p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
     p.add_argument("--no-tune", action="store_true", help="keep the default apply tile shape (no autotuner)")
+    p.add_argument("--sweep-only", action="store_true",
+                   help="print only the apply throughput for degrees 1..15 (FP64 and FP32) and exit")
     p.add_argument("--solve-only", action="store_true",
                    help="only the Sec. 7.2 Poisson solves at --k/--cells (for profiler captures)")
     return p.parse_args()
@@ -131,7 +133,7 @@ class Clocks:
 
 # the device-code sources of each kernel whose ncu counters a profile summary records
 KERNEL_SOURCES = {
-    "apply_cc": ["apply_cc.cu", "apply_common.cuh"],
+    "apply_cc": ["apply_cc.cu", "apply_cc.cuh", "apply_common.cuh"],
     "apply_umma": ["apply_umma.cu"],
     "apply_dmma": ["apply_dmma.cu", "apply_common.cuh"],
 }
@@ -258,6 +260,36 @@ def secondary(stream):
     return out
 
 
+def degree_sweep(stream, precs=("fp64", "fp32"), degrees=range(1, 16), target_dofs=1 << 26):
+    """Apply throughput of the CUDA-core kernel for n = 2..16 nodes per direction (the arbitrary-size
+    experiment of the paper's appendix): a cube mesh of about 2^26 DoFs per degree (vectors larger
+    than L2), tile shape autotuned where n <= 8, 8 timed applies after 2 warm-ups."""
+    import torch
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    from tp_synth import uniform_vector
+    peaks = {p: _lib.tp_bench_fma_peak(_lib.TP_FP64 if p == "fp64" else _lib.TP_FP32, stream.cuda_stream)
+             for p in precs}
+    out = []
+    for prec in precs:
+        for k in degrees:
+            n = k + 1
+            nc = max(2, round((target_dofs / n ** 3) ** (1.0 / 3.0)))
+            op = DGLaplace(nc, nc, nc, k, prec, autotune=1)
+            x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
+            y = torch.empty_like(x)
+            per, _ = time_applies(op, y, x, 8, 2, stream)
+            ms = statistics.mean(per)
+            tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
+            gbs = 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6
+            out.append({"k": k, "n": n, "cells": f"{nc}^3", "precision": prec, "dofs": op.ndofs, "ms": ms,
+                        "gdofs": op.ndofs / ms / 1e6, "flops_per_dof": op.info["flops_per_dof"],
+                        "tflops": tf, "fma_frac_of_measured": tf / peaks[prec],
+                        "hbm_frac_of_measured": gbs / PEAKS["hbm_gbs"], "tile_cells": op.info["tile_cells"]})
+            op.close()
+            del x, y
+    return out
+
+
 def solve_bench(k, nc, rtol=1e-10, half=True):
     """Sec. 7.2 Poisson solve: FP64 FGMRES(30) with a FP32 (mixed) or FP64 V-cycle preconditioner.
 
@@ -341,6 +373,10 @@ def run_ours(args):
     if args.solve_only:
         print(json.dumps({"solve_only": True, **solve_bench(kdeg, nc)}), flush=True)
         return
+    if args.sweep_only:
+        print(json.dumps({"sweep_only": True, "degree_sweep": degree_sweep(torch.cuda.current_stream())}),
+              flush=True)
+        return
     op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=2 if args.tensor else 0, ec=1 if args.ec else 0,
                    autotune=0 if args.no_tune else 1)
     ndofs = op.ndofs
@@ -401,6 +437,7 @@ def run_ours(args):
     solves = None if args.no_extra else [solve_bench(3, 128), solve_bench(7, 64), solve_bench(3, 64),
                                          solve_bench(7, 32)]
     batch = None if args.no_extra else batch_bench()
+    sweep = None if args.no_extra else degree_sweep(stream)
     cpu = oracle_sample() if world == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -424,6 +461,7 @@ def run_ours(args):
         "extra": extra,
         "solve": solves,
         "batch": batch,
+        "degree_sweep": sweep,
     }
     print(json.dumps(line), flush=True)
     op.close()

@@ -112,11 +112,15 @@ tp_status tp_mesh_destroy(tp_mesh m);
 
 /* SIPG Laplace operator of degree k on mesh m, for vectors of precision p,
  * on the current CUDA device (Sec. 2, Eq. (2) and Sec. 2.1, Eq. (9)).
- * 1 <= k <= 7. opts may be NULL (config penalty, AUTO kernel, no EC).
+ * 1 <= k <= 15; degrees above 7 (n = k + 1 up to 16, the arbitrary-size
+ * sweep of the paper's appendix) run on the CUDA-core kernel with FP64 or FP32
+ * vectors only, and take no multigrid hierarchy and no tp_l2_error_sines.
+ * opts may be NULL (config penalty, AUTO kernel, no EC).
  * The 1D matrices are computed on the host in FP64 and uploaded once; the
  * library owns that device memory until tp_op_destroy. The mesh may be
  * destroyed after this call. Errors: TP_ERR_INVALID_ARG (k, p, opts),
- * TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_UNSUPPORTED (kernel family not built for p). */
+ * TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_UNSUPPORTED (kernel family not built for p
+ * and k, e.g. k > 7 with a tensor kernel or FP16/BF16 vectors). */
 tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, const tp_op_opts* opts);
 tp_status tp_op_get_info(tp_op op, tp_op_info_t* info);
 tp_status tp_op_destroy(tp_op op);
@@ -214,7 +218,8 @@ typedef struct {
  * Allocates the level operators, vectors and scratch (owned until
  * tp_mg_destroy) and, unless opts->lmax > 0, estimates lmax(D^{-1}A_l) per
  * level by power iteration on the GPU (synchronizes the device).
- * Errors: TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_NONFINITE. */
+ * Errors: TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_NONFINITE,
+ * TP_ERR_UNSUPPORTED (finest degree above 7). */
 tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts);
 tp_status tp_mg_get_info(tp_mg mg, tp_mg_info_t* info);
 /* Level operator (owned by the hierarchy; valid until tp_mg_destroy). */
@@ -348,7 +353,8 @@ tp_status tp_rhs_sines(tp_op op, double* b, int nmodes, const double* a, const i
 
 /* *err = || u_h - u ||_L2 for the DEVICE FP64 coefficient vector u_h, by
  * per-cell tensor Gauss quadrature with k+4 points per direction (FP64).
- * Allocates a scratch array of ncells doubles; synchronizes `stream`. */
+ * Allocates a scratch array of ncells doubles; synchronizes `stream`.
+ * TP_ERR_UNSUPPORTED for degrees above 7. */
 tp_status tp_l2_error_sines(tp_op op, const double* u_h, int nmodes, const double* a, const int* pqr, double* err,
                             void* stream);
 

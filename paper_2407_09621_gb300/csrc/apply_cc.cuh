@@ -1,0 +1,269 @@
+// Sum-factorized SIPG Laplace apply on the FMA pipes ("CUDA-core" kernel).
+//
+// Sec. 2.1, Eq. (9): with the global 1D factors (M block diagonal, L block
+// tridiagonal with the face terms) the operator is
+//   A = L_z(x)M_y(x)M_x + M_z(x)L_y(x)M_x + M_z(x)M_y(x)L_x
+//     = (M_z(x)M_y(x)M_x) * [ (M^-1 L)_x + (M^-1 L)_y + (M^-1 L)_z ],
+// the same matrix written with one mass tensor on the left. Evaluated this
+// way a cell needs six n x n contractions instead of seven, and the face
+// terms need no tangential mass (they enter before the mass tensor):
+//   w = sum_d (M_d^-1 L_d) u  along each direction d (three contractions),
+//   v = M_z M_y M_x w          (three contractions).
+// M^-1 L is block tridiagonal like L. Its diagonal block G = M^-1 L_int is
+// the same for every cell; its neighbour blocks and the boundary-face
+// corrections are rank 2 along the normal, because Gauss-Lobatto value traces
+// are unit vectors (v0 = e_0, v1 = e_{n-1}):
+//   high neighbour:  s = w_0,     sd = d0.w  ->  s*P1 + sd*P2
+//   low neighbour:   s = w_{n-1}, sd = d1.w  ->  s*Q1 + sd*Q2
+//   high boundary:   s = u_{n-1}, sd = d1.u  ->  s*B1 + sd*B2   (own line u)
+//   low boundary:    s = u_0,     sd = d0.u  ->  s*C1 + sd*C2
+// with P1 = M^-1(-g v1 + d1/2h), P2 = -M^-1 v1/2h, Q1 = M^-1(-g v0 - d0/2h),
+// Q2 = M^-1 v0/2h, B1 = -M^-1 d1/2h, B2 = -M^-1 v1/2h, C1 = M^-1 d0/2h,
+// C2 = M^-1 v0/2h (g the penalty, h the cell width normal to the face).
+//
+// Work layout: n^2 threads per cell, CPB cells per block (the tile shape: CPB is
+// 128/n^2 halved, kept or doubled, picked per operator by the autotuner in tp_api.cu). In every phase a
+// thread owns one line of its cell along the direction being contracted, so
+// all threads of a warp apply the same 1D coefficients at the same time: the
+// 1D data is a __grid_constant__ kernel parameter and the coefficients are
+// constant-bank operands of the FMAs. Phases: (A) x- and y-lines of
+// w_x = G_x u + x faces and w_y = G_y u + y faces; (B) z-lines: w = w_x + w_y
+// + G_z u + z faces, then M_z w in registers; (C) y-lines: M_y; (D) x-lines:
+// M_x and the store. TS = storage type of the vectors, TC = arithmetic type.
+//
+// Degrees above 7 (8 < n <= 16, FP64 and FP32): one cell per block (n^2 threads), the cell
+// tensors padded to a row pitch of n + 1 so that the x-line phases, whose threads read rows n
+// values apart, hit distinct shared-memory banks, and three cell buffers instead of four (M_z w
+// overwrites u: in phase B every thread reads and writes its own z-line only).
+//
+// Instantiated in apply_cc.cu (n <= 8) and apply_cc_high.cu (8 < n <= 16).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "apply_common.cuh"
+
+namespace tp {
+
+// cells per block of tile-shape variant V (0: half, 1: the default 128/n^2, 2: double)
+template <int N, int V>
+__host__ __device__ constexpr int cc_cells_per_block() {
+  return V == 0 ? ((128 / (N * N)) / 2 > 0 ? (128 / (N * N)) / 2 : 1)
+                : (V == 1 ? ((128 / (N * N)) > 0 ? 128 / (N * N) : 1) : 2 * ((128 / (N * N)) > 0 ? 128 / (N * N) : 1));
+}
+
+// Row pitch of the shared cell tensors (element (l, j, i) at (l*N + j)*R + i) and the number
+// of cell buffers; the operator constants' row pitch.
+template <int N> __host__ __device__ constexpr int cc_pitch() { return N > kMaxN ? N + 1 : N; }
+template <int N> __host__ __device__ constexpr int cc_buffers() { return N > kMaxN ? 3 : 4; }
+template <typename TC, int N> using CcConst = OpConst<TC, (N > kMaxN ? kMaxNHigh : kMaxN)>;
+
+template <typename TC, int N, int V>
+__host__ __device__ constexpr size_t cc_smem_bytes() {
+  return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<N>() * N * N * cc_pitch<N>();
+}
+
+// out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst):
+// e_m = in[m] + in[n-1-m], o_m = in[m] - in[n-1-m]; ev_i = AE e, od_i = AO o;
+// out[i] = ev_i + od_i, out[n-1-i] = ev_i - od_i. n^2/2 + 2n operations instead of n^2.
+template <typename TC, int N, int S>
+__device__ __forceinline__ void contract_eo(TC (&out)[N], const TC (&AE)[S / 2][S / 2], const TC (&AO)[S / 2][S / 2],
+                                            const TC (&in)[N]) {
+  constexpr int H = N / 2;
+  TC e[H], o[H];
+#pragma unroll
+  for (int m = 0; m < H; ++m) {
+    e[m] = in[m] + in[N - 1 - m];
+    o[m] = in[m] - in[N - 1 - m];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    TC ev = AE[i][0] * e[0], od = AO[i][0] * o[0];
+#pragma unroll
+    for (int m = 1; m < H; ++m) {
+      ev = fma(AE[i][m], e[m], ev);
+      od = fma(AO[i][m], o[m], od);
+    }
+    out[i] = ev + od;
+    out[N - 1 - i] = ev - od;
+  }
+}
+
+template <typename TC, int N, int S>
+__device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A, const TC (&in)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    TC s = A[i * S] * in[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) s = fma(A[i * S + m], in[m], s);
+    out[i] = s;
+  }
+}
+
+// out = (M or G)_d in: the even-odd form for even n >= 6 when the matrices are centrosymmetric
+// (always on the symmetric Gauss-Lobatto element; checked on the host), the plain form otherwise.
+template <typename TC, int N>
+__device__ __forceinline__ void contract_d(TC (&out)[N], const CcConst<TC, N>& P, bool mass, int d,
+                                           const TC (&in)[N]) {
+  constexpr int S = CcConst<TC, N>::S;
+  if constexpr (N % 2 == 0 && N >= 6) {
+    if (P.centro) {
+      if (mass)
+        contract_eo<TC, N, S>(out, P.ME[d], P.MO[d], in);
+      else
+        contract_eo<TC, N, S>(out, P.GE[d], P.GO[d], in);
+      return;
+    }
+  }
+  contract<TC, N, S>(out, mass ? P.M[d] : P.G[d], in);
+}
+
+template <typename TS, typename TC, int N, int V>
+__global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
+apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ CcConst<TC, N> P,
+                int nx, int ny, int nz, long long c_begin, long long c_end) {
+  constexpr int CPB = cc_cells_per_block<N, V>();
+  constexpr int N2 = N * N, N3 = N * N * N;
+  constexpr int R = cc_pitch<N>(), B = N * N * R;  // row pitch and size of a shared cell tensor
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TC* base = reinterpret_cast<TC*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int cs = tid / N2, t = tid % N2, p = t / N, q = t % N;
+  TC* sU = base + cs * B;                   // u
+  TC* sX = base + (CPB + cs) * B;           // w_x, later M_y M_z w
+  TC* sY = base + (2 * CPB + cs) * B;       // w_y
+  TC* sZ = cc_buffers<N>() == 4 ? base + (3 * CPB + cs) * B : sU;  // M_z w
+
+  const long long cell = c_begin + (long long)blockIdx.x * CPB + cs;  // cells [c_begin, c_end) of the mesh
+  const bool valid = cell < c_end;
+  const int cx = valid ? (int)(cell % nx) : 0;
+  const int cy = valid ? (int)((cell / nx) % ny) : 0;
+  const int cz = valid ? (int)(cell / ((long long)nx * ny)) : 0;
+  const TS* xc = x + (valid ? cell : 0) * N3;
+  const long long sy = (long long)nx * N3, sz = (long long)nx * ny * N3;
+
+  // ---- gather u (coalesced)
+#pragma unroll
+  for (int l = 0; l < N; ++l) sU[(l * N + p) * R + q] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
+  __syncthreads();
+
+  // ---- (A) x-line (l=p, j=q) and y-line (l=p, i=q)
+  {
+    TC u[N], w[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) u[m] = sU[(p * N + q) * R + m];
+    contract_d<TC, N>(w, P, false, 0, u);
+    if (valid) {
+      const TS* lo = cx > 0 ? xc - N3 + p * N2 + q * N : nullptr;
+      const TS* hi = cx < nx - 1 ? xc + N3 + p * N2 + q * N : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, 1, P, 0);
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) sX[(p * N + q) * R + i] = w[i];
+#pragma unroll
+    for (int m = 0; m < N; ++m) u[m] = sU[(p * N + m) * R + q];
+    contract_d<TC, N>(w, P, false, 1, u);
+    if (valid) {
+      const TS* lo = cy > 0 ? xc - sy + p * N2 + q : nullptr;
+      const TS* hi = cy < ny - 1 ? xc + sy + p * N2 + q : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, N, P, 1);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) sY[(p * N + j) * R + q] = w[j];
+  }
+  __syncthreads();
+
+  // ---- (B) z-line (j=p, i=q): w = w_x + w_y + G_z u + z faces; then M_z w
+  {
+    TC u[N], w[N], v[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) u[m] = sU[(m * N + p) * R + q];
+    contract_d<TC, N>(w, P, false, 2, u);
+    if (valid) {
+      const TS* lo = cz > 0 ? xc - sz + t : nullptr;
+      const TS* hi = cz < nz - 1 ? xc + sz + t : nullptr;
+      add_faces<TS, TC, N>(w, u, lo, hi, N2, P, 2);
+    }
+#pragma unroll
+    for (int l = 0; l < N; ++l) w[l] += sX[(l * N + p) * R + q] + sY[(l * N + p) * R + q];
+    contract_d<TC, N>(v, P, true, 2, w);
+#pragma unroll
+    for (int l = 0; l < N; ++l) sZ[(l * N + p) * R + q] = v[l];
+  }
+  __syncthreads();
+
+  // ---- (C) y-line (l=p, i=q): M_y
+  {
+    TC w[N], v[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = sZ[(p * N + m) * R + q];
+    contract_d<TC, N>(v, P, true, 1, w);
+#pragma unroll
+    for (int j = 0; j < N; ++j) sX[(p * N + j) * R + q] = v[j];
+  }
+  __syncthreads();
+
+  // ---- (D) x-line (l=p, j=q): M_x and scatter
+  if (valid) {
+    TC w[N], v[N];
+#pragma unroll
+    for (int m = 0; m < N; ++m) w[m] = sX[(p * N + q) * R + m];
+    contract_d<TC, N>(v, P, true, 0, w);
+    TS* yc = y + cell * N3 + p * N2 + q * N;
+#pragma unroll
+    for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, v[i]);
+  }
+}
+
+template <typename TS, typename TC, int N, int V>
+static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                               cudaStream_t s) {
+  constexpr int CPB = cc_cells_per_block<N, V>();
+  constexpr size_t smem = cc_smem_bytes<TC, N, V>();
+  const long long blocks = (c1 - c0 + CPB - 1) / CPB;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (blocks <= 0) return cudaSuccess;
+  const CcConst<TC, N>& P = *static_cast<const CcConst<TC, N>*>(
+      N > kMaxN ? op->hconst_high(sizeof(TC)) : op->hconst(sizeof(TC)));
+  apply_cc_kernel<TS, TC, N, V><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
+      static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, c0, c1);
+  return cudaGetLastError();
+}
+
+// Launch of the tile variant the operator selected (n > 8: the one-cell tile only).
+template <typename TS, typename TC, int N>
+static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                               cudaStream_t s) {
+  if constexpr (N > kMaxN) {
+    return launch_cc_v<TS, TC, N, 1>(op, y, x, c0, c1, s);
+  } else {
+    switch (op->tile_variant) {
+      case 0: return launch_cc_v<TS, TC, N, 0>(op, y, x, c0, c1, s);
+      case 2: return launch_cc_v<TS, TC, N, 2>(op, y, x, c0, c1, s);
+    }
+    return launch_cc_v<TS, TC, N, 1>(op, y, x, c0, c1, s);
+  }
+}
+
+template <typename TS, typename TC, int N, int V>
+static cudaError_t prepare_cc_v() {
+  return cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cc_smem_bytes<TC, N, V>());
+}
+
+// Sets the dynamic shared-memory limit of every tile variant of degree N on the current device.
+template <typename TS, typename TC, int N>
+static cudaError_t prepare_cc_n() {
+  if constexpr (N > kMaxN) {
+    return prepare_cc_v<TS, TC, N, 1>();
+  } else {
+    cudaError_t e = prepare_cc_v<TS, TC, N, 0>();
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 1>();
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 2>();
+    return e;
+  }
+}
+
+}  // namespace tp

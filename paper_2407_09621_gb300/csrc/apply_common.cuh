@@ -30,10 +30,10 @@ __device__ __forceinline__ void store_as<__nv_bfloat16, float>(__nv_bfloat16* p,
 
 // Adds the two faces of direction d to the line accumulator acc[] of a line whose own
 // values are u[] (nodes 0..N-1 along d). src_lo / src_hi: the neighbour's line or nullptr
-// at the boundary; `step` is the stride of the line inside a cell.
-template <typename TS, typename TC, int N>
+// at the boundary; `step` is the stride of the line inside a cell. PC is an OpConst<TC, .>.
+template <typename TS, typename TC, int N, typename PC>
 __device__ __forceinline__ void add_faces(TC (&acc)[N], const TC (&u)[N], const TS* src_lo, const TS* src_hi,
-                                          int step, const OpConst<TC>& P, int d) {
+                                          int step, const PC& P, int d) {
   // high face
   if (src_hi) {
     TC w[N];

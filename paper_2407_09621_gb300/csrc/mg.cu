@@ -657,6 +657,11 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   if (!out) { set_error("tp_mg_create: out is NULL"); return TP_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!finest) { set_error("tp_mg_create: operator is NULL"); return TP_ERR_INVALID_ARG; }
+  if (finest->n > kMaxN) {
+    set_error("tp_mg_create: degree k=%d above %d (the transfer and smoother kernels take n <= %d)", finest->k,
+              kMaxN - 1, kMaxN);
+    return TP_ERR_UNSUPPORTED;
+  }
   if (finest->ncells >= (1LL << 31)) {
     set_error("tp_mg_create: meshes of 2^31 cells or more are not supported");
     return TP_ERR_UNSUPPORTED;

@@ -191,6 +191,10 @@ extern "C" tp_status tp_l2_error_sines(tp_op op, const double* u, int nmodes, co
   tp_status st = check_modes(nmodes, a, pqr, "tp_l2_error_sines");
   if (st != TP_OK) return st;
   if (op->ncells > 0x7fffffffLL) { set_error("tp_l2_error_sines: too many cells"); return TP_ERR_INVALID_ARG; }
+  if (op->n > kMaxN) {
+    set_error("tp_l2_error_sines: degree k=%d above %d is not supported", op->k, kMaxN - 1);
+    return TP_ERR_UNSUPPORTED;
+  }
   L2Params P;
   memset(&P, 0, sizeof(P));
   P.n = op->n;

@@ -57,10 +57,11 @@ size_t elem_bytes(tp_precision p);
 // operator's mesh (same nx and ny, enough z-layers for about 128 MB per vector) after one
 // warm-up launch; the fastest is kept. The per-cell arithmetic does not depend on the shape, so
 // the choice changes no result. Tuning is best effort: if the proxy vectors cannot be
-// allocated the default shape stays.
+// allocated the default shape stays. Degrees above 7 have a single shape and are not tuned.
 static tp_status autotune_apply(tp_op_s* op) {
   const bool dm = op->opts.kernel == TP_KERNEL_TENSOR && op->prec == TP_FP64;
   if (op->opts.kernel == TP_KERNEL_TENSOR && !dm) return TP_OK;  // tcgen05 / mma.sync: fixed tiles
+  if (op->n > kMaxN) return TP_OK;                                 // n > 8: one tile shape
   const long long eb = (long long)elem_bytes(op->prec);
   const long long n3 = (long long)op->n * op->n * op->n;
   const long long slab = (long long)op->mesh.nx * op->mesh.ny;
@@ -126,8 +127,8 @@ size_t elem_bytes(tp_precision p) {
   return 0;
 }
 
-template <typename T>
-static void fill_const(OpConst<T>& c, const tp_op_s* op) {
+template <typename T, int NM>
+static void fill_const(OpConst<T, NM>& c, const tp_op_s* op) {
   memset(&c, 0, sizeof(c));
   const int n = op->n;
   const std::vector<double>& d0 = op->ref.d0;
@@ -151,8 +152,8 @@ static void fill_const(OpConst<T>& c, const tp_op_s* op) {
       for (int j = 0; j < n; ++j) {
         double gij = 0.0;
         for (int m = 0; m < n; ++m) gij += Minv[i * n + m] * D.L[m * n + j];
-        c.M[d][i * kMaxN + j] = (T)D.M[i * n + j];
-        c.G[d][i * kMaxN + j] = (T)gij;
+        c.M[d][i * NM + j] = (T)D.M[i * n + j];
+        c.G[d][i * NM + j] = (T)gij;
       }
       c.E[d][0][i] = (T)(-g * mv1[i] + hh * md1[i]);  // P1: high neighbour, value trace
       c.E[d][1][i] = (T)(-hh * mv1[i]);               // P2: high neighbour, derivative trace
@@ -333,7 +334,10 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   if (!out) { set_error("tp_dg_laplace_create: out is NULL"); return TP_ERR_INVALID_ARG; }
   *out = nullptr;
   if (!m) { set_error("tp_dg_laplace_create: mesh is NULL"); return TP_ERR_INVALID_ARG; }
-  if (k < 1 || k > 7) { set_error("tp_dg_laplace_create: degree k=%d outside [1,7]", k); return TP_ERR_INVALID_ARG; }
+  if (k < 1 || k > kMaxNHigh - 1) {
+    set_error("tp_dg_laplace_create: degree k=%d outside [1,%d]", k, kMaxNHigh - 1);
+    return TP_ERR_INVALID_ARG;
+  }
   if (p != TP_FP64 && p != TP_FP32 && p != TP_FP16 && p != TP_BF16) {
     set_error("tp_dg_laplace_create: unknown precision %d", (int)p);
     return TP_ERR_INVALID_ARG;
@@ -380,6 +384,10 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: error correction needs the tensor kernel");
     return TP_ERR_UNSUPPORTED;
   }
+  if (k + 1 > kMaxN && (o.kernel == TP_KERNEL_TENSOR || (p != TP_FP64 && p != TP_FP32))) {
+    set_error("tp_dg_laplace_create: degrees above %d need the CUDA-core kernel and FP64 or FP32 vectors", kMaxN - 1);
+    return TP_ERR_UNSUPPORTED;
+  }
   const long long ncells = (long long)m->nx * m->ny * m->nz;
   const long long n3 = (long long)(k + 1) * (k + 1) * (k + 1);
   if (ncells > (1LL << 62) / n3) { set_error("tp_dg_laplace_create: DoF count overflows"); return TP_ERR_INVALID_ARG; }
@@ -398,8 +406,13 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   for (int d = 0; d < 3; ++d) op->dir[d] = make_dir1d(op->ref, hs[d], o.penalty);
   tp_status st = cuda_status(cudaGetDevice(&op->device), "cudaGetDevice");
   if (st != TP_OK) { delete op; return st; }
-  fill_const(op->c64, op);
-  fill_const(op->c32, op);
+  if (op->n > kMaxN) {
+    fill_const(op->c64h, op);
+    fill_const(op->c32h, op);
+  } else {
+    fill_const(op->c64, op);
+    fill_const(op->c32, op);
+  }
   st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
                    "apply kernel set-up");
   if (st == TP_OK && o.autotune) st = autotune_apply(op);
@@ -421,7 +434,8 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->kernel = op->opts.kernel;
   info->elem_bytes = elem_bytes(op->prec);
   // the CUDA-core kernel takes the even-odd path (the DMMA and tensor kernels do not)
-  const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n % 2 == 0 && op->n >= 6 && op->c64.centro;
+  const int centro = op->n > kMaxN ? op->c64h.centro : op->c64.centro;
+  const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n % 2 == 0 && op->n >= 6 && centro;
   info->flops_per_dof = apply_flops_per_dof(op->n, eo);
   info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
   info->tile_cells = info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)

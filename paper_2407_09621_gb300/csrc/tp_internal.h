@@ -10,7 +10,8 @@
 
 namespace tp {
 
-constexpr int kMaxN = 8;  // n = k + 1 <= 8 (k <= 7)
+constexpr int kMaxN = 8;       // n = k + 1 <= 8 (k <= 7): every kernel family and the multigrid
+constexpr int kMaxNHigh = 16;  // n <= 16 (k <= 15): the CUDA-core apply in FP64 and FP32 only
 
 // 1D reference data of the Gauss-Lobatto Lagrange basis on [0, 1] (Sec. 2).
 struct Ref1D {
@@ -41,22 +42,24 @@ std::vector<double> invert(int n, const std::vector<double>& A);
 bool gen_eig(int N, const std::vector<double>& M, const std::vector<double>& L, std::vector<double>& lam,
              std::vector<double>& V);
 
-// 1D operator data of the apply kernel, templated on the compute type.
-// Passed by value as a __grid_constant__ kernel parameter (4.7 KB for
-// double), so the coefficients are read from the constant bank. Per
-// direction d: M = h M-hat, G = M^-1 L_int, and the face expansion vectors
-// E[d][0..7] = P1, P2, Q1, Q2, B1, B2, C1, C2 (see apply_cc.cu).
-template <typename T>
+// 1D operator data of the apply kernel, templated on the compute type and on the
+// row pitch NM of its matrices (kMaxN for n <= 8, kMaxNHigh above). Passed by value
+// as a __grid_constant__ kernel parameter (5.5 KB for double at NM = 8, 22 KB at 16),
+// so the coefficients are read from the constant bank. Per direction d: M = h M-hat,
+// G = M^-1 L_int, and the face expansion vectors E[d][0..7] = P1, P2, Q1, Q2, B1, B2,
+// C1, C2 (see apply_cc.cuh).
+template <typename T, int NM = kMaxN>
 struct OpConst {
-  T M[3][kMaxN * kMaxN];
-  T G[3][kMaxN * kMaxN];
-  T d0[kMaxN], d1[kMaxN];
-  T E[3][8][kMaxN];
+  static constexpr int S = NM;  // row pitch of M and G: entry (i, j) at [i * S + j]
+  T M[3][NM * NM];
+  T G[3][NM * NM];
+  T d0[NM], d1[NM];
+  T E[3][8][NM];
   // Even-odd halves of the centrosymmetric M and G (A[n-1-i][n-1-m] = A[i][m], the reference
   // element and the Gauss-Lobatto nodes being symmetric about 1/2), for i, m < n/2:
   // AE[i][m] = (A[i][m] + A[i][n-1-m]) / 2 and AO[i][m] = (A[i][m] - A[i][n-1-m]) / 2.
-  T ME[3][kMaxN / 2][kMaxN / 2], MO[3][kMaxN / 2][kMaxN / 2];
-  T GE[3][kMaxN / 2][kMaxN / 2], GO[3][kMaxN / 2][kMaxN / 2];
+  T ME[3][NM / 2][NM / 2], MO[3][NM / 2][NM / 2];
+  T GE[3][NM / 2][NM / 2], GO[3][NM / 2][NM / 2];
   int centro;  // 1 if every M and G above is centrosymmetric (to 1e-12 relative)
 };
 
@@ -86,8 +89,10 @@ struct tp_op_s {
   tp_precision prec;
   tp_op_opts opts;
   long long ncells, ndofs;
-  tp::OpConst<double> c64;    // host copies of the kernel-parameter constants
+  tp::OpConst<double> c64;    // host copies of the kernel-parameter constants (n <= 8)
   tp::OpConst<float> c32;
+  tp::OpConst<double, tp::kMaxNHigh> c64h;  // the same for 8 < n <= 16
+  tp::OpConst<float, tp::kMaxNHigh> c32h;
   int device = 0;
   void* tc_mats = nullptr;    // tensor kernel operand matrices (device)
   int tc_blocks_per_sm = 1, sm_count = 1;
@@ -97,6 +102,7 @@ struct tp_op_s {
   int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)
   tp::UmmaParams umma_params;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
+  const void* hconst_high(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64h : (const void*)&c32h; }
   // host-buffer path (tp_apply_host): library-owned staging, and the streams and events of its
   // copy/compute pipeline (created on first use)
   void* hx = nullptr; void* hy = nullptr;

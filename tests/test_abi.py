@@ -30,10 +30,15 @@ def test_mesh_validation():
 def test_operator_argument_validation():
     m = _lib.tp_mesh_create(2, 2, 2)
     try:
-        for k in (0, 8):
+        for k in (0, 16):
             with pytest.raises(_lib.TPError) as e:
                 _lib.tp_dg_laplace_create(m, k, _lib.TP_FP64)
             assert e.value.status == _lib.TP_ERR_INVALID_ARG
+        # degrees 8..15: CUDA-core kernel with FP64 or FP32 vectors only (rejected before any CUDA call)
+        for k, p, kern in ((8, _lib.TP_FP16, 1), (15, _lib.TP_BF16, 0), (8, _lib.TP_FP64, 2), (11, _lib.TP_FP32, 2)):
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_dg_laplace_create(m, k, p, kernel=kern)
+            assert e.value.status == _lib.TP_ERR_UNSUPPORTED
         with pytest.raises(_lib.TPError) as e:
             _lib.tp_dg_laplace_create(m, 3, 9)
         assert e.value.status == _lib.TP_ERR_INVALID_ARG

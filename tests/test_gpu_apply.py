@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle.sipg import Mesh, assemble, BlockOperator, global_1d
+from oracle.sipg import Mesh, assemble, BlockOperator, global_1d, kron_apply
 from tp_synth import uniform_vector, sample_cells
 from tests.gpu_util import TOL, DTYPES, rel_l2, to_device, to_host64
 
@@ -273,5 +273,85 @@ def test_pipelined_host_apply_matches_device(k, prec, kernel, dims, pinned):
         torch.cuda.synchronize()
         assert torch.equal(yh, yd.cpu())
         assert rel_l2(yh.double().numpy(), BlockOperator(m, k).apply(x64)) < TOL[prec]
+    finally:
+        op.close()
+
+
+# ---------------------------------------------------------------- degrees 8..15 (CUDA-core, FP64 and FP32)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", range(8, 16))
+def test_high_degrees_ragged_meshes(k, prec):
+    """n = 9..16 nodes per direction (the arbitrary-size range of the paper's appendix): every
+    entry against the Kronecker-sum form of Eq. (9), on meshes with one, two and three cells per
+    direction (interior faces, boundary faces and both on one cell)."""
+    for dims in [(3, 2, 2), (1, 3, 1)]:
+        x = uniform_vector(int(np.prod(dims)) * (k + 1) ** 3, seed=80 + k)
+        y = _gpu_apply(dims, k, prec, x)
+        ref = kron_apply(x, k, dims)
+        assert rel_l2(y, ref) < TOL[prec]
+        if prec == "fp64":
+            assert np.abs(y - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_high_degree_block_operator_k8():
+    # the element/face block rows at k = 8, the oracle path that is independent of the 1D factors
+    dims = (2, 3, 2)
+    m = Mesh(*dims)
+    x = uniform_vector(m.ncells * 9 ** 3, seed=88)
+    assert rel_l2(_gpu_apply(dims, 8, "fp64", x), BlockOperator(m, 8).apply(x)) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("pen", [0, 1])
+def test_high_degree_paper_penalty_anisotropic_box(pen):
+    dims, k, lengths = (2, 3, 2), 13, (0.7, 1.9, 0.45)
+    x = uniform_vector(int(np.prod(dims)) * (k + 1) ** 3, seed=90 + pen)
+    y = _gpu_apply(dims, k, "fp64", x, penalty=pen, lengths=lengths)
+    assert rel_l2(y, kron_apply(x, k, dims, lengths, "paper" if pen else "config")) < TOL["fp64"]
+
+
+@pytest.mark.parametrize("k,nc", [(8, 32), (11, 24), (15, 20)])
+def test_high_degree_full_size_rank1(k, nc):
+    # 23.9M - 32.8M DoFs: the rank-1 closed form of Eq. (9) on every entry
+    xs, ys = _rank1_vectors(k, nc, seed=19)
+    y = _gpu_apply((nc, nc, nc), k, "fp64", xs)
+    assert rel_l2(y, ys) < TOL["fp64"]
+    y32 = _gpu_apply((nc, nc, nc), k, "fp32", xs)
+    assert rel_l2(y32, ys) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("k,prec", [(9, "fp64"), (14, "fp32")])
+def test_high_degree_pipelined_host_apply(k, prec):
+    # tp_apply_host's z-slab pipeline with n > 8 equals tp_apply bit for bit
+    from paper_2407_09621_gb300 import DGLaplace
+    dims = (2, 2, 9)
+    x64 = uniform_vector(36 * (k + 1) ** 3, seed=95)
+    op = DGLaplace(*dims, k, prec)
+    try:
+        assert op.info["tile_cells"] == 1
+        xd = to_device(x64, prec)
+        xh = xd.cpu().pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        op.apply_host(yh, xh)
+        yd = torch.empty_like(xd)
+        op.apply(yd, xd)
+        torch.cuda.synchronize()
+        assert torch.equal(yh, yd.cpu())
+        assert rel_l2(yh.double().numpy(), kron_apply(x64, k, dims)) < TOL[prec]
+    finally:
+        op.close()
+
+
+def test_high_degree_autotune_keeps_single_tile_and_rejects_multigrid():
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    op = DGLaplace(4, 4, 4, 10, "fp64", autotune=1)
+    try:
+        assert op.info["tile_cells"] == 1 and op.info["k"] == 10
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_mg_create(op.op)
+        assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+        u = torch.zeros(op.ndofs, dtype=torch.float64, device="cuda")
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_l2_error_sines(op.op, u.data_ptr())
+        assert e.value.status == _lib.TP_ERR_UNSUPPORTED
     finally:
         op.close()
