@@ -65,19 +65,22 @@ __host__ __device__ constexpr size_t cc_smem_bytes() {
   return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<N>() * N * N * cc_pitch<N>();
 }
 
-// out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst):
-// e_m = in[m] + in[n-1-m], o_m = in[m] - in[n-1-m]; ev_i = AE e, od_i = AO o;
-// out[i] = ev_i + od_i, out[n-1-i] = ev_i - od_i. n^2/2 + 2n operations instead of n^2.
+// out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst), H = n/2
+// rounded down: e_m = in[m] + in[n-1-m], o_m = in[m] - in[n-1-m] for m < H; ev_i = AE e,
+// od_i = AO o; out[i] = ev_i + od_i, out[n-1-i] = ev_i - od_i. For odd n the middle node is
+// its own mirror image: e_H = in[H] enters ev through the column AE[i][H] = A[i][H], no od term
+// involves it, and the middle row is out[H] = AE[H] e. About n^2/2 + 2n operations instead of n^2.
 template <typename TC, int N, int S>
 __device__ __forceinline__ void contract_eo(TC (&out)[N], const TC (&AE)[S / 2][S / 2], const TC (&AO)[S / 2][S / 2],
                                             const TC (&in)[N]) {
-  constexpr int H = N / 2;
-  TC e[H], o[H];
+  constexpr int H = N / 2, HE = (N + 1) / 2;  // odd and even halves' lengths
+  TC e[HE], o[H];
 #pragma unroll
   for (int m = 0; m < H; ++m) {
     e[m] = in[m] + in[N - 1 - m];
     o[m] = in[m] - in[N - 1 - m];
   }
+  if constexpr (HE > H) e[H] = in[H];
 #pragma unroll
   for (int i = 0; i < H; ++i) {
     TC ev = AE[i][0] * e[0], od = AO[i][0] * o[0];
@@ -86,8 +89,15 @@ __device__ __forceinline__ void contract_eo(TC (&out)[N], const TC (&AE)[S / 2][
       ev = fma(AE[i][m], e[m], ev);
       od = fma(AO[i][m], o[m], od);
     }
+    if constexpr (HE > H) ev = fma(AE[i][H], e[H], ev);
     out[i] = ev + od;
     out[N - 1 - i] = ev - od;
+  }
+  if constexpr (HE > H) {
+    TC mid = AE[H][0] * e[0];
+#pragma unroll
+    for (int m = 1; m < HE; ++m) mid = fma(AE[H][m], e[m], mid);
+    out[H] = mid;
   }
 }
 
@@ -102,13 +112,14 @@ __device__ __forceinline__ void contract(TC (&out)[N], const TC* __restrict__ A,
   }
 }
 
-// out = (M or G)_d in: the even-odd form for even n >= 6 when the matrices are centrosymmetric
-// (always on the symmetric Gauss-Lobatto element; checked on the host), the plain form otherwise.
+// out = (M or G)_d in: the even-odd form for n >= 5 when the matrices are centrosymmetric
+// (always on the symmetric Gauss-Lobatto element; checked on the host), the plain form otherwise
+// (for n <= 4 the even-odd form saves no instruction).
 template <typename TC, int N>
 __device__ __forceinline__ void contract_d(TC (&out)[N], const CcConst<TC, N>& P, bool mass, int d,
                                            const TC (&in)[N]) {
   constexpr int S = CcConst<TC, N>::S;
-  if constexpr (N % 2 == 0 && N >= 6) {
+  if constexpr (N >= 5) {
     if (P.centro) {
       if (mass)
         contract_eo<TC, N, S>(out, P.ME[d], P.MO[d], in);

@@ -169,8 +169,8 @@ static void fill_const(OpConst<T, NM>& c, const tp_op_s* op) {
     c.d0[i] = (T)d0[i];
     c.d1[i] = (T)d1[i];
   }
-  // even-odd halves (used for even n >= 6 when the matrices are centrosymmetric)
-  bool centro = n % 2 == 0;
+  // even-odd halves (used for n >= 5 when the matrices are centrosymmetric)
+  bool centro = n >= 5;
   for (int d = 0; d < 3 && centro; ++d) {
     const Dir1D& D = op->dir[d];
     const std::vector<double> Minv = invert(n, D.M);
@@ -188,23 +188,35 @@ static void fill_const(OpConst<T, NM>& c, const tp_op_s* op) {
         const int r = (n - 1 - i) * n + (n - 1 - j);
         centro = std::fabs(G[i * n + j] - G[r]) <= 1e-12 * gmax && std::fabs(D.M[i * n + j] - D.M[r]) <= 1e-12 * mmax;
       }
-    for (int i = 0; i < n / 2; ++i)
-      for (int m = 0; m < n / 2; ++m) {
+    const int H = n / 2;
+    for (int i = 0; i < H; ++i)
+      for (int m = 0; m < H; ++m) {
         c.ME[d][i][m] = (T)(0.5 * (D.M[i * n + m] + D.M[i * n + n - 1 - m]));
         c.MO[d][i][m] = (T)(0.5 * (D.M[i * n + m] - D.M[i * n + n - 1 - m]));
         c.GE[d][i][m] = (T)(0.5 * (G[i * n + m] + G[i * n + n - 1 - m]));
         c.GO[d][i][m] = (T)(0.5 * (G[i * n + m] - G[i * n + n - 1 - m]));
       }
+    if (n % 2 == 1) {  // the middle node: column H of the even half, and the middle row
+      for (int i = 0; i <= H; ++i) {
+        c.ME[d][i][H] = (T)D.M[i * n + H];
+        c.GE[d][i][H] = (T)G[i * n + H];
+        c.ME[d][H][i] = (T)D.M[H * n + i];
+        c.GE[d][H][i] = (T)G[H * n + i];
+      }
+    }
   }
   c.centro = centro ? 1 : 0;
 }
 
-// algorithmic flops per DoF of the sum-factorized apply in the inverse-mass form
-// (FMA = 2 flops): 6 n x n contractions (12n), 6 derivative traces (12), 6 faces x two
-// dense expansion vectors (24), summing the three directions (2). With the even-odd form of
-// the contractions (even n >= 6, centrosymmetric matrices) a line costs n^2/2 FMAs and 2n adds,
-// so the six contractions take 6n + 12 flops per DoF instead of 12n.
-double apply_flops_per_dof(int n, bool even_odd) { return (even_odd ? 6.0 * n + 12.0 : 12.0 * n) + 38.0; }
+// Algorithmic flops per DoF of the sum-factorized apply in the inverse-mass form (FMA = 2
+// flops): 6 n x n contractions (12n), 6 derivative traces (12), 6 faces x two dense expansion
+// vectors (24), summing the three directions (2): 12n + 38. With the even-odd form of the
+// contractions (n >= 5, centrosymmetric matrices) a line costs n^2/2 FMAs and 2n adds for even
+// n, (n^2 + 1)/2 FMAs and 2(n - 1) adds for odd n: 6n + 50 (even) or 6n + 50 - 6/n (odd).
+double apply_flops_per_dof(int n, bool even_odd) {
+  const double line = !even_odd ? 2.0 * n * n : (n % 2 == 0 ? 1.0 * n * n + 2.0 * n : n * n + 1.0 + 2.0 * (n - 1));
+  return 6.0 * line / n + 38.0;
+}
 
 }  // namespace tp
 
@@ -435,7 +447,7 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->elem_bytes = elem_bytes(op->prec);
   // the CUDA-core kernel takes the even-odd path (the DMMA and tensor kernels do not)
   const int centro = op->n > kMaxN ? op->c64h.centro : op->c64.centro;
-  const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n % 2 == 0 && op->n >= 6 && centro;
+  const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n >= 5 && centro;
   info->flops_per_dof = apply_flops_per_dof(op->n, eo);
   info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
   info->tile_cells = info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)

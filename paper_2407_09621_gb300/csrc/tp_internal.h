@@ -56,8 +56,9 @@ struct OpConst {
   T d0[NM], d1[NM];
   T E[3][8][NM];
   // Even-odd halves of the centrosymmetric M and G (A[n-1-i][n-1-m] = A[i][m], the reference
-  // element and the Gauss-Lobatto nodes being symmetric about 1/2), for i, m < n/2:
-  // AE[i][m] = (A[i][m] + A[i][n-1-m]) / 2 and AO[i][m] = (A[i][m] - A[i][n-1-m]) / 2.
+  // element and the Gauss-Lobatto nodes being symmetric about 1/2), for i, m < H = floor(n/2):
+  // AE[i][m] = (A[i][m] + A[i][n-1-m]) / 2 and AO[i][m] = (A[i][m] - A[i][n-1-m]) / 2; for odd n
+  // also the middle column and row AE[i][H] = A[i][H], AE[H][m] = A[H][m] (i, m <= H).
   T ME[3][NM / 2][NM / 2], MO[3][NM / 2][NM / 2];
   T GE[3][NM / 2][NM / 2], GO[3][NM / 2][NM / 2];
   int centro;  // 1 if every M and G above is centrosymmetric (to 1e-12 relative)

@@ -355,3 +355,20 @@ def test_high_degree_autotune_keeps_single_tile_and_rejects_multigrid():
         assert e.value.status == _lib.TP_ERR_UNSUPPORTED
     finally:
         op.close()
+
+
+@pytest.mark.parametrize("k", range(1, 16))
+def test_flops_per_dof_reports_the_contraction_form(k):
+    """n >= 5 takes the even-odd form of the centrosymmetric 1D matrices: a line costs n^2/2 FMAs
+    and 2n adds (even n) or (n^2 + 1)/2 FMAs and 2(n - 1) adds (odd n) instead of n^2 FMAs."""
+    from paper_2407_09621_gb300 import DGLaplace
+    n = k + 1
+    op = DGLaplace(2, 2, 2, k, "fp64")
+    try:
+        if n >= 5:
+            line = n * n + 2 * n if n % 2 == 0 else n * n + 1 + 2 * (n - 1)
+        else:
+            line = 2 * n * n
+        assert op.info["flops_per_dof"] == pytest.approx(6 * line / n + 38)
+    finally:
+        op.close()
