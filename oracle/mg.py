@@ -15,11 +15,13 @@ What this restates
   Gauss-Lobatto nodes: per direction P1_c[i, j] = phi_j((c + x_i) / 2) for
   child c in {0, 1}, and in 3D the Kronecker product of the three 1D
   factors. Restriction is its transpose.
-* Smoother (the paper uses a vertex-patch Schwarz smoother; this build uses
-  Chebyshev-Jacobi): ``degree`` steps of the Chebyshev semi-iteration for
-  D^{-1} A on the interval [lmax / ratio, lmax], D = diag(A) (Saad,
-  "Iterative Methods for Sparse Linear Systems", Alg. 12.1 with a Jacobi
-  preconditioner). The eigenvalue bound lmax is an input.
+* Smoother, one of two: Chebyshev-Jacobi, ``degree`` steps of the Chebyshev
+  semi-iteration for D^{-1} A on the interval [lmax / ratio, lmax], D = diag(A)
+  (Saad, "Iterative Methods for Sparse Linear Systems", Alg. 12.1 with a Jacobi
+  preconditioner; the eigenvalue bound lmax is an input); or the paper's
+  vertex-patch multiplicative Schwarz smoother (oracle/schwarz.py), one sweep
+  over the eight patch colours, ascending before and descending after the
+  coarse-grid correction.
 * Coarse solve: exact (fast diagonalization, oracle/solve.py).
 * FGMRES (Saad 1993, right preconditioning, restart m): modified
   Gram-Schmidt Arnoldi, Givens rotations, stop when the Arnoldi residual
@@ -38,6 +40,7 @@ import scipy.sparse as sp
 from .basis import gauss_lobatto_nodes, lagrange_values
 from .sipg import Mesh, BlockOperator, global_1d, lex_to_cell_major
 from .solve import FastDiag
+from .schwarz import VertexPatchSmoother
 
 
 def prolongation_1d(k):
@@ -115,8 +118,9 @@ class Level:
 class VCycle:
     """Algorithm 2 on the cube, finest nc^3 cells, coarsest `coarse_nc`^3 cells."""
 
-    def __init__(self, k, nc, coarse_nc=1, pen="config", degree=3, ratio=15.0, lmax=None):
+    def __init__(self, k, nc, coarse_nc=1, pen="config", degree=3, ratio=15.0, lmax=None, smoother="chebyshev"):
         self.k = k
+        self.smoother = smoother
         sizes = [nc]
         while sizes[-1] > coarse_nc:
             if sizes[-1] % 2:
@@ -128,8 +132,17 @@ class VCycle:
         self.coarse = FastDiag(k, sizes[0], sizes[0], sizes[0], pen)
         self.degree, self.ratio = degree, ratio
         self.lmax = lmax if lmax is not None else [None] * len(sizes)
+        self.vp = None
+        if smoother == "vertex_patch":
+            from .sipg import assemble
+            self.vp = [None] + [VertexPatchSmoother(assemble(Mesh(s, s, s), k, pen), k, (s, s, s))
+                                for s in sizes[1:]]
+        elif smoother != "chebyshev":
+            raise ValueError("smoother is 'chebyshev' or 'vertex_patch'")
 
-    def smooth(self, l, b, x):
+    def smooth(self, l, b, x, post=False):
+        if self.vp is not None:
+            return self.vp[l].smooth(x, b, reverse=post)
         lev = self.levels[l]
         return chebyshev(lev.A.apply, lev.dinv, b, x, self.lmax[l], self.degree, self.ratio)
 
@@ -142,7 +155,7 @@ class VCycle:
         rc = self.P[l].T @ r
         xc = self.vcycle(l - 1, rc, np.zeros_like(rc))
         x = x + self.P[l] @ xc
-        return self.smooth(l, b, x)
+        return self.smooth(l, b, x, post=True)
 
     def __call__(self, b):
         return self.vcycle(len(self.levels) - 1, b, np.zeros_like(b))
