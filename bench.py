@@ -305,13 +305,15 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
     _lib.tp_rhs_sines(op, b.data_ptr())
     out = {"k": k, "cells": f"{nc}^3", "dofs": ndofs, "rtol": rtol, "restart": 30}
     CC, TC = _lib.TP_KERNEL_CUDA_CORE, _lib.TP_KERNEL_TENSOR
-    runs = [("mixed_fp32_vcycle", _lib.TP_FP32, CC), ("fp64_vcycle", _lib.TP_FP64, CC)]
+    CH, VP = _lib.TP_SMOOTHER_CHEBYSHEV, _lib.TP_SMOOTHER_VERTEX_PATCH
+    runs = [("mixed_fp32_vcycle", _lib.TP_FP32, CC, CH), ("fp64_vcycle", _lib.TP_FP64, CC, CH),
+            ("mixed_fp32_vertex_patch", _lib.TP_FP32, CC, VP), ("fp64_vertex_patch", _lib.TP_FP64, CC, VP)]
     if half:
         # FP16/BF16-storage V-cycles: tcgen05 level applies at k = 3, CUDA-core otherwise
         kh = TC if k == 3 else CC
-        runs += [("bf16_vcycle", _lib.TP_BF16, kh), ("fp16_vcycle", _lib.TP_FP16, kh)]
-    for name, prec, kern in runs:
-        mg = _lib.tp_mg_create(op, precision=prec, kernel=kern)
+        runs += [("bf16_vcycle", _lib.TP_BF16, kh, CH), ("fp16_vcycle", _lib.TP_FP16, kh, CH)]
+    for name, prec, kern, smoother in runs:
+        mg = _lib.tp_mg_create(op, precision=prec, kernel=kern, smoother=smoother)
         solver = _lib.tp_fgmres_create(op, mg, 30)
         x = torch.zeros_like(b)
         _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), rtol, 2, raise_on_error=False)  # warm-up
@@ -324,6 +326,7 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
         out[name] = {"seconds": dt, "iterations": info["iterations"], "converged": info["converged"],
                      "true_rel_residual": info["true_rel_residual"], "l2_error": err, "status": st,
                      "level_kernel": "tensor" if kern == TC else "cuda_core",
+                     "smoother": "vertex_patch" if smoother == VP else "chebyshev_jacobi",
                      "reorthogonalizations": info.get("reorthogonalizations")}
         _lib.tp_solver_destroy(solver)
         _lib.tp_mg_destroy(mg)
@@ -332,9 +335,17 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
     rule = lambda e: (abs(e - e64) <= 0.01 * e64) if e64 > 1e-10 else (e <= max(1.01 * e64, 1e-11))
     out["speedup_mixed_vs_fp64"] = out["fp64_vcycle"]["seconds"] / out["mixed_fp32_vcycle"]["seconds"]
     out["l2_within_rule"] = rule(out["mixed_fp32_vcycle"]["l2_error"])
-    for name, _, _ in runs[2:]:
+    out["mixed_fp32_vcycle"]["l2_within_rule"] = out["l2_within_rule"] and out["mixed_fp32_vcycle"]["converged"] == 1
+    for name, _, _, _ in runs[2:]:
         out[name]["speedup_vs_fp64"] = out["fp64_vcycle"]["seconds"] / out[name]["seconds"]
         out[name]["l2_within_rule"] = rule(out[name]["l2_error"]) and out[name]["converged"] == 1
+    out["speedup_mixed_vs_fp64_vertex_patch"] = (out["fp64_vertex_patch"]["seconds"] /
+                                                 out["mixed_fp32_vertex_patch"]["seconds"])
+    fastest_fp64 = min(out["fp64_vcycle"]["seconds"], out["fp64_vertex_patch"]["seconds"])
+    mixed = [n for n, p, _, _ in runs if p != _lib.TP_FP64 and out[n]["l2_within_rule"]]
+    best = min(mixed or ["mixed_fp32_vcycle"], key=lambda n: out[n]["seconds"])
+    out["best_mixed"] = {"run": best, "seconds": out[best]["seconds"],
+                         "speedup_vs_fastest_fp64": fastest_fp64 / out[best]["seconds"]}
     _lib.tp_op_destroy(op)
     _lib.tp_mesh_destroy(mesh)
     return out

@@ -173,9 +173,17 @@ tp_status tp_op_check(tp_op op);
  * levels from uniform coarsening by 2 in every direction (while all cell
  * counts are even and one exceeds coarse_cells), the same degree and penalty
  * on every level, the operator rediscretized with that level's h.
- *  - smoother S_l: `degree` steps of Chebyshev iteration on D^{-1} A_l,
- *    D = diag(A_l), eigenvalue interval [lmax/ratio, lmax] (the paper's
- *    vertex-patch Schwarz smoother is replaced by Chebyshev-Jacobi);
+ *  - smoother S_l, one of two (tp_mg_opts.smoother):
+ *    TP_SMOOTHER_CHEBYSHEV (default): `degree` steps of Chebyshev iteration on
+ *    D^{-1} A_l, D = diag(A_l), eigenvalue interval [lmax/ratio, lmax];
+ *    TP_SMOOTHER_VERTEX_PATCH: the paper's multiplicative vertex-patch Schwarz
+ *    smoother (Sec. 7.1): the 2x2x2-cell patches around interior vertices,
+ *    coloured by vertex parity (8 colours, a colour's patches disjoint); per
+ *    colour r = b - A_l x, then x_P += A_P^{-1} r_P on each of its patches,
+ *    solved exactly by fast diagonalization of the patch's Kronecker-sum
+ *    matrix. One sweep per smoothing step, colours ascending before and
+ *    descending after the coarse correction (tp_mg_smooth: ascending). FP64
+ *    and FP32 multigrid precision only;
  *  - restriction I_down = P^T, prolongation I_up = P, the exact embedding of
  *    the coarse DG space into the fine one;
  *  - coarse solve A_0^{-1}: exact, in FP64, by fast diagonalization.
@@ -188,6 +196,9 @@ tp_status tp_op_check(tp_op op);
  * two (at most 1) that keeps the V-cycle's gain on the smoothest mode, about
  * n^3 / (3 pi^2 hx hy hz), from overflowing; BF16 has FP32's range. */
 #define TP_MAX_LEVELS 16
+
+#define TP_SMOOTHER_CHEBYSHEV 0
+#define TP_SMOOTHER_VERTEX_PATCH 1
 
 typedef struct tp_mg_s* tp_mg;
 
@@ -203,6 +214,7 @@ typedef struct {
                         TP_KERNEL_TENSOR (FP32/FP16/BF16 vectors, k = 2, 3; otherwise CUDA-core) */
   int ec;            /* tensor kernel with Algorithm 1 error correction */
   int tc_type;       /* tensor operand type: TP_FP16 (default) or TP_BF16 */
+  int smoother;      /* TP_SMOOTHER_CHEBYSHEV (default) or TP_SMOOTHER_VERTEX_PATCH */
 } tp_mg_opts;
 
 typedef struct {
@@ -218,8 +230,10 @@ typedef struct {
  * Allocates the level operators, vectors and scratch (owned until
  * tp_mg_destroy) and, unless opts->lmax > 0, estimates lmax(D^{-1}A_l) per
  * level by power iteration on the GPU (synchronizes the device).
+ * The vertex-patch smoother estimates no lmax (lmax and ratio are unused).
  * Errors: TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_NONFINITE,
- * TP_ERR_UNSUPPORTED (finest degree above 7). */
+ * TP_ERR_UNSUPPORTED (finest degree above 7; vertex-patch smoother with
+ * FP16/BF16 vectors). */
 tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts);
 tp_status tp_mg_get_info(tp_mg mg, tp_mg_info_t* info);
 /* Level operator (owned by the hierarchy; valid until tp_mg_destroy). */

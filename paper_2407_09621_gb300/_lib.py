@@ -132,13 +132,14 @@ def tp_bench_fma_peak(precision, stream=0):
 
 # ---------------------------------------------------------------- multigrid / FGMRES
 TP_MAX_LEVELS = 16
+TP_SMOOTHER_CHEBYSHEV, TP_SMOOTHER_VERTEX_PATCH = 0, 1
 
 
 class tp_mg_opts(ctypes.Structure):
     _fields_ = [("degree", ctypes.c_int), ("ratio", ctypes.c_double), ("safety", ctypes.c_double),
                 ("lmax", ctypes.c_double), ("coarse_cells", ctypes.c_int), ("precision", ctypes.c_int),
                 ("power_iters", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
-                ("tc_type", ctypes.c_int)]
+                ("tc_type", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class tp_mg_info_t(ctypes.Structure):
@@ -176,9 +177,9 @@ for _name, (_res, _args) in _sig2.items():
 
 
 def tp_mg_create(op, degree=3, ratio=15.0, safety=1.1, lmax=0.0, coarse_cells=4, precision=TP_FP32,
-                 power_iters=20, kernel=TP_KERNEL_CUDA_CORE, ec=0, tc_type=TP_FP16):
+                 power_iters=20, kernel=TP_KERNEL_CUDA_CORE, ec=0, tc_type=TP_FP16, smoother=TP_SMOOTHER_CHEBYSHEV):
     h = _vp()
-    o = tp_mg_opts(degree, ratio, safety, lmax, coarse_cells, precision, power_iters, kernel, ec, tc_type)
+    o = tp_mg_opts(degree, ratio, safety, lmax, coarse_cells, precision, power_iters, kernel, ec, tc_type, smoother)
     _check(lib.tp_mg_create(ctypes.byref(h), op, ctypes.byref(o)))
     return h
 

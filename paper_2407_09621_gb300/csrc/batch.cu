@@ -144,7 +144,7 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     if (st == TP_OK) st = tp_dg_laplace_create(&it.op, it.mesh, p.k, TP_FP64, &oo);
     if (st != TP_OK) break;
     it.ndofs = it.op->ndofs;
-    tp_mg_opts mo{3, 15.0, 1.1, 0.0, 4, o.mg_precision, 20, o.kernel, o.ec, TP_FP16};
+    tp_mg_opts mo{3, 15.0, 1.1, 0.0, 4, o.mg_precision, 20, o.kernel, o.ec, TP_FP16, TP_SMOOTHER_CHEBYSHEV};
     st = tp_mg_create(&it.mg, it.op, &mo);
     if (st == TP_OK) st = tp_fgmres_create(&it.solver, it.op, it.mg, o.restart);
     if (st == TP_OK) st = cuda_status(cudaMalloc(&it.b, sizeof(double) * it.ndofs), "tp_batch_solve");

@@ -3,8 +3,9 @@
 // Levels: uniform coarsening by 2 in every direction, same degree k, the
 // operator rediscretized on each level (Sec. 2 with that level's h).
 // Smoother: Chebyshev semi-iteration of the given degree on D^{-1} A with
-// D = diag(A) evaluated from the Kronecker form of Eq. (9) (the paper's
-// vertex-patch Schwarz smoother is not used). Transfer: prolongation is the
+// D = diag(A) evaluated from the Kronecker form of Eq. (9), or the paper's
+// multiplicative vertex-patch Schwarz smoother (patch solves in schwarz.cu;
+// the sweep over the eight colours here). Transfer: prolongation is the
 // exact embedding of the coarse DG space (coarse basis evaluated at the fine
 // nodes, a Kronecker product of 1D n x n matrices per child), restriction
 // its transpose; both sum-factorized. Coarse solve: exact, in FP64, by fast
@@ -27,6 +28,11 @@ namespace tp {
 tp_status cuda_status(int err, const char* what);
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 size_t elem_bytes(tp_precision p);
+// vertex-patch smoother (schwarz.cu)
+bool vp_colour_nonempty(const int nc[3], int c);
+cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, void* x, const void* r, const void* S,
+                      const void* L, cudaStream_t s);
+tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out);
 
 // Division of n < 2^31 by an invariant d >= 1 with one multiply-high (Granlund and Montgomery,
 // "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
@@ -348,6 +354,7 @@ struct tp_mg_level {
   long long ndofs = 0;
   void *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
   double lmax = 0.0;
+  void *vpS = nullptr, *vpL = nullptr;  // vertex-patch smoother: 1D patch eigenbases and eigenvalues
   tp::JacobiParams<double> j64;
   tp::JacobiParams<float> j32;
 };
@@ -521,8 +528,33 @@ static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, co
   TP_DISPATCH_PREC(mg->prec, return sub_t<T>(L.ndofs, r, b, t, s))
 }
 
-// `degree` Chebyshev-Jacobi steps on level l from x (x_zero: x is taken as 0 and not read)
-cudaError_t mg_smooth(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s) {
+// One vertex-patch Schwarz sweep on level l: for each colour (ascending, or descending when
+// `post`) r = b - A x, then x_P += A_P^{-1} r_P on the colour's patches. With x_zero, x is
+// cleared and the first colour takes r = b.
+static cudaError_t smooth_vertex_patch(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, int post,
+                                       cudaStream_t s) {
+  const tp_mg_level& L = mg->lv[l];
+  cudaError_t e = cudaSuccess;
+  if (x_zero) e = cudaMemsetAsync(x, 0, L.ndofs * elem_bytes(mg->prec), s);
+  bool zero = x_zero != 0;
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) {
+    const int c = post ? 7 - i : i;
+    if (!vp_colour_nonempty(L.nc, c)) continue;
+    const void* r = b;
+    if (!zero) {
+      e = residual(mg, L, L.r, b, x, L.t, s);
+      r = L.r;
+    }
+    zero = false;
+    if (e == cudaSuccess) e = vp_colour(mg->prec, mg->n, L.nc, c, x, r, L.vpS, L.vpL, s);
+  }
+  return e;
+}
+
+// Smoothing step on level l from x (x_zero: x is taken as 0 and not read): `degree`
+// Chebyshev-Jacobi steps, or one vertex-patch sweep (colours descending when `post`).
+cudaError_t mg_smooth(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s, int post = 0) {
+  if (mg->opts.smoother == TP_SMOOTHER_VERTEX_PATCH) return smooth_vertex_patch(mg, l, x, b, x_zero, post, s);
   const tp_mg_level& L = mg->lv[l];
   const double lmax = L.lmax, lmin = lmax / mg->opts.ratio;
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
@@ -554,7 +586,7 @@ cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_ze
   if (e == cudaSuccess) e = mg_restrict(mg, l, C.b, L.r, s);
   if (e == cudaSuccess) e = mg_vcycle(mg, l - 1, C.x, C.b, 1, s);
   if (e == cudaSuccess) e = mg_prolong_add(mg, l, x, C.x, s);
-  if (e == cudaSuccess) e = mg_smooth(mg, l, x, b, 0, s);
+  if (e == cudaSuccess) e = mg_smooth(mg, l, x, b, 0, s, 1);
   return e;
 }
 
@@ -633,6 +665,8 @@ static void free_level(tp_mg_level& L, bool own_xb) {
   if (L.r) cudaFree(L.r);
   if (L.d) cudaFree(L.d);
   if (L.t) cudaFree(L.t);
+  if (L.vpS) cudaFree(L.vpS);
+  if (L.vpL) cudaFree(L.vpL);
   L = tp_mg_level();
 }
 
@@ -666,8 +700,16 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
     set_error("tp_mg_create: meshes of 2^31 cells or more are not supported");
     return TP_ERR_UNSUPPORTED;
   }
-  tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20, TP_KERNEL_CUDA_CORE, 0, TP_FP16};
+  tp_mg_opts o{3, 15.0, 1.1, 0.0, 4, TP_FP32, 20, TP_KERNEL_CUDA_CORE, 0, TP_FP16, TP_SMOOTHER_CHEBYSHEV};
   if (opts) o = *opts;
+  if (o.smoother != TP_SMOOTHER_CHEBYSHEV && o.smoother != TP_SMOOTHER_VERTEX_PATCH) {
+    set_error("tp_mg_create: smoother must be TP_SMOOTHER_CHEBYSHEV or TP_SMOOTHER_VERTEX_PATCH");
+    return TP_ERR_INVALID_ARG;
+  }
+  if (o.smoother == TP_SMOOTHER_VERTEX_PATCH && o.precision != TP_FP64 && o.precision != TP_FP32) {
+    set_error("tp_mg_create: the vertex-patch smoother takes FP64 or FP32 multigrid vectors");
+    return TP_ERR_UNSUPPORTED;
+  }
   if (o.degree < 1 || o.degree > 16 || !(o.ratio > 1.0) || !(o.safety > 0) || o.coarse_cells < 1 ||
       (o.precision != TP_FP64 && o.precision != TP_FP32 && o.precision != TP_FP16 && o.precision != TP_BF16) ||
       o.power_iters < 1 || o.lmax < 0) {
@@ -779,8 +821,12 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   }
   if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->partial, sizeof(double) * (kMaxMulti + 1) * dot_blocks(mg->lv.back().ndofs)), "tp_mg_create: scratch");
   if (st == TP_OK) st = cuda_status(cudaMalloc(&mg->dots, sizeof(double) * kMaxMulti), "tp_mg_create: scratch");
+  // vertex-patch eigenbases of every smoothed level (each has >= 2 cells per direction: it is at
+  // least twice the coarsest level)
+  for (int l = 1; l < nl && st == TP_OK && o.smoother == TP_SMOOTHER_VERTEX_PATCH; ++l)
+    st = vp_tables(mg->lv[l].op, mg->lv[l].nc, mg->prec, &mg->lv[l].vpS, &mg->lv[l].vpL);
   // smoother eigenvalue bounds
-  for (int l = 1; l < nl && st == TP_OK; ++l) {
+  for (int l = 1; l < nl && st == TP_OK && o.smoother == TP_SMOOTHER_CHEBYSHEV; ++l) {
     if (o.lmax > 0) {
       mg->lv[l].lmax = o.lmax;
     } else {

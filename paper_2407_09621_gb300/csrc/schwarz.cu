@@ -1,0 +1,269 @@
+// Vertex-patch multiplicative Schwarz smoother (Sec. 7.1, after Cui et al. 2024 and Witte et
+// al. 2021): the local solves of one colour of patches.
+//
+// A vertex patch is the 2 x 2 x 2 block of cells around an interior vertex v (1 <= v_d <= nc_d
+// - 1), P = 2n nodes per direction. On a Cartesian mesh the restriction of Eq. (9) to a patch
+// is again a Kronecker sum, of the 1D factors restricted to the patch's two cells:
+//   A_P = L_z (x) M_y (x) M_x + M_z (x) L_y (x) M_x + M_z (x) M_y (x) L_x   (P x P factors),
+// so with the 1D generalized eigenpairs L S = M S diag(lam), S^T M S = I, the local solve is
+// exact fast diagonalization:
+//   A_P^{-1} r = (S_z (x) S_y (x) S_x) diag(1 / (lam_x + lam_y + lam_z)) (S_z (x) S_y (x) S_x)^T r,
+// six P x P contractions and one scaling per patch DoF. The 1D patch factors depend only on
+// whether the patch's left / right cell touches the boundary (type t = [v == 1] + 2 [v == nc - 1]),
+// so each level holds 3 x 4 eigenbases, computed on the host in FP64.
+//
+// The colour of a patch is the parity of its vertex; patches of one colour share no DoF, so one
+// thread block per patch adds its correction x_P += A_P^{-1} r_P without atomics. The sweep
+// over colours, with the residual r = b - A x formed before each colour, is in mg.cu.
+//
+// Work layout: P^2 threads per patch; in every phase a thread owns one line of the patch tensor
+// along the contracted direction (rows padded to P + 1 against bank conflicts). Phases: S_x^T,
+// S_y^T, then along z S_z^T, the scaling and S_z in registers, then S_y, and S_x with the update
+// of x.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+tp_status cuda_status(int err, const char* what);
+
+namespace {
+
+constexpr int kMaxP = 2 * kMaxN;  // patch nodes per direction (k <= 7)
+
+struct VPDims {
+  int nx, ny, nz;
+  int first[3];  // vertex of the colour's first patch per direction (1 or 2)
+};
+
+// patches of parity p along a direction with nc cells: vertices p, p + 2, ... in [1, nc - 1]
+__host__ __device__ inline int vp_count(int p, int nc) { return p ? nc / 2 : (nc - 1) / 2; }
+
+// dynamic shared memory of the patch kernel: two padded patch tensors, three P x P bases, 3P
+// eigenvalues
+template <typename T, int N>
+constexpr size_t vp_smem_bytes() {
+  return sizeof(T) * (2 * (2 * N) * (2 * N) * (2 * N + 1) + 3 * (2 * N) * (2 * N) + 3 * (2 * N));
+}
+
+template <typename T, int N>
+__global__ void __launch_bounds__(4 * N * N)
+vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
+                VPDims D) {
+  constexpr int P = 2 * N, R = P + 1, N3 = N * N * N;
+  extern __shared__ __align__(16) unsigned char vp_smem[];
+  T* bufA = reinterpret_cast<T*>(vp_smem);
+  T* bufB = bufA + P * P * R;
+  T (*sS)[P * P] = reinterpret_cast<T (*)[P * P]>(bufB + P * P * R);
+  T (*sL)[P] = reinterpret_cast<T (*)[P]>(bufB + P * P * R + 3 * P * P);
+  const int tid = threadIdx.x, p = tid / P, q = tid % P;
+  const int vx = D.first[0] + 2 * (int)blockIdx.x, vy = D.first[1] + 2 * (int)blockIdx.y;
+  const int vz = D.first[2] + 2 * (int)blockIdx.z;
+  {
+    const int t[3] = {(vx == 1 ? 1 : 0) + (vx == D.nx - 1 ? 2 : 0), (vy == 1 ? 1 : 0) + (vy == D.ny - 1 ? 2 : 0),
+                      (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      sS[d][tid] = Stab[(size_t)(d * 4 + t[d]) * kMaxP * kMaxP + p * kMaxP + q];  // tid = X * P + a
+      if (tid < P) sL[d][tid] = Ltab[(d * 4 + t[d]) * kMaxP + tid];
+    }
+  }
+  // the patch's cells: (v - 1 + lx, v - 1 + ly, v - 1 + lz), lx, ly, lz in {0, 1}
+  const long long c0 = ((long long)(vz - 1) * D.ny + (vy - 1)) * D.nx + (vx - 1);
+  auto gidx = [&](int Z, int Y, int X) {
+    const long long cell = c0 + ((long long)(Z / N) * D.ny + (Y / N)) * D.nx + (X / N);
+    return cell * N3 + ((Z % N) * N + (Y % N)) * N + (X % N);
+  };
+  for (int e = tid; e < P * P * P; e += P * P) {
+    const int Z = e / (P * P), Y = (e / P) % P, X = e % P;
+    bufA[(Z * P + Y) * R + X] = r[gidx(Z, Y, X)];
+  }
+  __syncthreads();
+  // One line of the patch tensor in registers, in[m], contracted per output node o:
+  // sum_m S[m][o] in[m] (S^T applied) or sum_m S[o][m] in[m] (S applied); each output goes
+  // straight to shared memory.
+  T in[P];
+  // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
+#pragma unroll
+  for (int m = 0; m < P; ++m) in[m] = bufA[(p * P + q) * R + m];
+#pragma unroll 2
+  for (int a = 0; a < P; ++a) {
+    T s = sS[0][a] * in[0];
+#pragma unroll
+    for (int m = 1; m < P; ++m) s = fma(sS[0][m * P + a], in[m], s);
+    bufB[(p * P + q) * R + a] = s;
+  }
+  __syncthreads();
+  // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
+#pragma unroll
+  for (int m = 0; m < P; ++m) in[m] = bufB[(p * P + m) * R + q];
+#pragma unroll 2
+  for (int b = 0; b < P; ++b) {
+    T s = sS[1][b] * in[0];
+#pragma unroll
+    for (int m = 1; m < P; ++m) s = fma(sS[1][m * P + b], in[m], s);
+    bufA[(p * P + b) * R + q] = s;
+  }
+  __syncthreads();
+  // z-lines (b = p, a = q): S_z^T and the eigenvalue scaling into bufB, then S_z back into bufA.
+  // A thread reads and writes only its own z-line here, so no barrier is needed in between.
+#pragma unroll
+  for (int m = 0; m < P; ++m) in[m] = bufA[(m * P + p) * R + q];
+  const T lxy = sL[0][q] + sL[1][p];
+#pragma unroll 2
+  for (int c = 0; c < P; ++c) {
+    T s = sS[2][c] * in[0];
+#pragma unroll
+    for (int m = 1; m < P; ++m) s = fma(sS[2][m * P + c], in[m], s);
+    bufB[(c * P + p) * R + q] = s / (lxy + sL[2][c]);
+  }
+#pragma unroll
+  for (int c = 0; c < P; ++c) in[c] = bufB[(c * P + p) * R + q];
+#pragma unroll 2
+  for (int Z = 0; Z < P; ++Z) {
+    T s = sS[2][Z * P] * in[0];
+#pragma unroll
+    for (int c = 1; c < P; ++c) s = fma(sS[2][Z * P + c], in[c], s);
+    bufA[(Z * P + p) * R + q] = s;
+  }
+  __syncthreads();
+  // S_y along y-lines (Z = p, a = q): bufA -> bufB
+#pragma unroll
+  for (int b = 0; b < P; ++b) in[b] = bufA[(p * P + b) * R + q];
+#pragma unroll 2
+  for (int Y = 0; Y < P; ++Y) {
+    T s = sS[1][Y * P] * in[0];
+#pragma unroll
+    for (int b = 1; b < P; ++b) s = fma(sS[1][Y * P + b], in[b], s);
+    bufB[(p * P + Y) * R + q] = s;
+  }
+  __syncthreads();
+  // S_x along x-lines (Z = p, Y = q) and x_P += the correction
+#pragma unroll
+  for (int a = 0; a < P; ++a) in[a] = bufB[(p * P + q) * R + a];
+#pragma unroll 2
+  for (int X = 0; X < P; ++X) {
+    T s = sS[0][X * P] * in[0];
+#pragma unroll
+    for (int a = 1; a < P; ++a) s = fma(sS[0][X * P + a], in[a], s);
+    T* px = x + gidx(p, q, X);
+    *px += s;
+  }
+}
+
+template <typename T, int N>
+cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
+                          cudaStream_t s) {
+  const int par[3] = {colour & 1, (colour >> 1) & 1, (colour >> 2) & 1};
+  const dim3 grid(vp_count(par[0], nc[0]), vp_count(par[1], nc[1]), vp_count(par[2], nc[2]));
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
+  vp_patch_kernel<T, N><<<grid, 4 * N * N, vp_smem_bytes<T, N>(), s>>>(
+      static_cast<T*>(x), static_cast<const T*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+cudaError_t prepare_colour() {
+  return cudaFuncSetAttribute(vp_patch_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)vp_smem_bytes<T, N>());
+}
+
+template <typename T>
+cudaError_t prepare_t(int n) {
+  switch (n) {
+    case 2: return prepare_colour<T, 2>();
+    case 3: return prepare_colour<T, 3>();
+    case 4: return prepare_colour<T, 4>();
+    case 5: return prepare_colour<T, 5>();
+    case 6: return prepare_colour<T, 6>();
+    case 7: return prepare_colour<T, 7>();
+    case 8: return prepare_colour<T, 8>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_colour_t(int n, int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
+                            cudaStream_t s) {
+  switch (n) {
+    case 2: return launch_colour<T, 2>(colour, nc, x, r, S, L, s);
+    case 3: return launch_colour<T, 3>(colour, nc, x, r, S, L, s);
+    case 4: return launch_colour<T, 4>(colour, nc, x, r, S, L, s);
+    case 5: return launch_colour<T, 5>(colour, nc, x, r, S, L, s);
+    case 6: return launch_colour<T, 6>(colour, nc, x, r, S, L, s);
+    case 7: return launch_colour<T, 7>(colour, nc, x, r, S, L, s);
+    case 8: return launch_colour<T, 8>(colour, nc, x, r, S, L, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+// true if colour c (vertex parities c & 1, c >> 1 & 1, c >> 2 & 1) has a patch on the mesh
+bool vp_colour_nonempty(const int nc[3], int c) {
+  return vp_count(c & 1, nc[0]) > 0 && vp_count((c >> 1) & 1, nc[1]) > 0 && vp_count((c >> 2) & 1, nc[2]) > 0;
+}
+
+// x_P += A_P^{-1} r_P for every patch of colour c (FP64 or FP32 vectors; every nc >= 2).
+cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, void* x, const void* r, const void* S,
+                      const void* L, cudaStream_t s) {
+  if (prec == TP_FP64) return launch_colour_t<double>(n, colour, nc, x, r, S, L, s);
+  if (prec == TP_FP32) return launch_colour_t<float>(n, colour, nc, x, r, S, L, s);
+  return cudaErrorInvalidValue;
+}
+
+// Eigenbases of the 1D patch factors of one level, uploaded in the vectors' precision:
+// S[(d*4 + t)][X * kMaxP + a] = component X of eigenvector a, L[(d*4 + t)][a] = its eigenvalue,
+// for direction d and boundary type t. A mesh of min(nc, 4) cells with the level's h has every
+// type of the level at its vertices 1 .. min(nc, 4) - 1.
+tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out) {
+  const int n = op->n, P = 2 * n;
+  std::vector<double> S((size_t)12 * kMaxP * kMaxP, 0.0), lam((size_t)12 * kMaxP, 0.0);
+  for (int d = 0; d < 3; ++d) {
+    if (nc[d] < 2) { set_error("vertex-patch smoother: fewer than two cells in a direction"); return TP_ERR_UNSUPPORTED; }
+    const int m = nc[d] >= 4 ? 4 : nc[d];
+    std::vector<double> M, L;
+    global_1d(op->ref, op->dir[d], m, M, L);
+    const int N1 = m * n;
+    for (int v = 1; v <= m - 1; ++v) {
+      const int t = (v == 1 ? 1 : 0) + (v == m - 1 ? 2 : 0);
+      std::vector<double> Mp((size_t)P * P), Lp((size_t)P * P), lv, V;
+      for (int i = 0; i < P; ++i)
+        for (int j = 0; j < P; ++j) {
+          Mp[(size_t)i * P + j] = M[(size_t)((v - 1) * n + i) * N1 + (v - 1) * n + j];
+          Lp[(size_t)i * P + j] = L[(size_t)((v - 1) * n + i) * N1 + (v - 1) * n + j];
+        }
+      if (!gen_eig(P, Mp, Lp, lv, V)) {
+        set_error("vertex-patch smoother: patch mass matrix not positive definite");
+        return TP_ERR_INVALID_ARG;
+      }
+      for (int X = 0; X < P; ++X)
+        for (int a = 0; a < P; ++a) S[(size_t)(d * 4 + t) * kMaxP * kMaxP + X * kMaxP + a] = V[(size_t)X * P + a];
+      for (int a = 0; a < P; ++a) lam[(size_t)(d * 4 + t) * kMaxP + a] = lv[a];
+    }
+  }
+  const size_t eb = prec == TP_FP64 ? 8 : 4;
+  std::vector<unsigned char> hS(S.size() * eb), hL(lam.size() * eb);
+  for (size_t i = 0; i < S.size(); ++i) {
+    if (eb == 8) reinterpret_cast<double*>(hS.data())[i] = S[i];
+    else reinterpret_cast<float*>(hS.data())[i] = (float)S[i];
+  }
+  for (size_t i = 0; i < lam.size(); ++i) {
+    if (eb == 8) reinterpret_cast<double*>(hL.data())[i] = lam[i];
+    else reinterpret_cast<float*>(hL.data())[i] = (float)lam[i];
+  }
+  *S_out = *L_out = nullptr;
+  tp_status st = cuda_status(prec == TP_FP64 ? prepare_t<double>(n) : prepare_t<float>(n), "vertex-patch kernel set-up");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(S_out, hS.size()), "vertex-patch tables");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(L_out, hL.size()), "vertex-patch tables");
+  if (st == TP_OK) st = cuda_status(cudaMemcpy(*S_out, hS.data(), hS.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  if (st == TP_OK) st = cuda_status(cudaMemcpy(*L_out, hL.data(), hL.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
+  return st;
+}
+
+}  // namespace tp

@@ -25,13 +25,13 @@ PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 
 
 class GpuMG:
-    def __init__(self, nc, k, prec, lmax=0.0, coarse_cells=1, degree=3):
+    def __init__(self, nc, k, prec, lmax=0.0, coarse_cells=1, degree=3, smoother=0, dims=None):
         from paper_2407_09621_gb300 import _lib
         self.lib = _lib
-        self.mesh = _lib.tp_mesh_create(nc, nc, nc)
+        self.mesh = _lib.tp_mesh_create(*(dims or (nc, nc, nc)))
         self.op = _lib.tp_dg_laplace_create(self.mesh, k, _lib.TP_FP64)
         self.mg = _lib.tp_mg_create(self.op, degree=degree, lmax=lmax, coarse_cells=coarse_cells,
-                                    precision=PREC[prec])
+                                    precision=PREC[prec], smoother=smoother)
         self.info = _lib.tp_mg_get_info(self.mg)
         self.dtype = DT[prec]
 
@@ -137,11 +137,12 @@ def test_lmax_estimate_bounds_the_spectrum(k):
         g.close()
 
 
-def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4, kernel=1):
+def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4, kernel=1, smoother=0):
     from paper_2407_09621_gb300 import _lib
     mesh = _lib.tp_mesh_create(nc, nc, nc)
     op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
-    mg = (_lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec], kernel=kernel)
+    mg = (_lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec], kernel=kernel,
+                            smoother=smoother)
           if mg_prec else None)
     solver = _lib.tp_fgmres_create(op, mg, 30)
     try:
@@ -285,3 +286,103 @@ def test_fgmres_basis_stays_orthonormal(k, nc):
     A = BlockOperator(Mesh(nc, nc, nc), k)
     _, its, _ = fgmres(A.apply, mg, rhs_sine(k, nc, nc, nc), rtol=1e-10)
     assert abs(info["iterations"] - its) <= 2
+
+
+# ---------------------------------------------------------------- vertex-patch Schwarz smoother
+VP = 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,dims", [(1, (4, 4, 4)), (2, (4, 6, 2)), (3, (4, 2, 4)), (2, (6, 4, 4))])
+def test_vertex_patch_smoother_matches_oracle(prec, k, dims):
+    """One sweep (colours ascending) on the finest level against the oracle's dense patch solves."""
+    from oracle.schwarz import VertexPatchSmoother
+    from oracle.sipg import assemble
+    g = GpuMG(None, k, prec, coarse_cells=1, smoother=VP, dims=dims)
+    try:
+        fl = g.info["levels"] - 1
+        n = g.info["ndofs"][fl]
+        b, x0 = uniform_vector(n, seed=21), uniform_vector(n, seed=22)
+        x = g.vec(x0)
+        g.lib.tp_mg_smooth(g.mg, fl, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        ref = VertexPatchSmoother(assemble(Mesh(*dims), k), k, dims).smooth(x0, b)
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-12 if prec == "fp64" else 5e-5)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k", [1, 4, 5, 7])
+def test_vertex_patch_single_patch_level_solves_exactly(prec, k):
+    """2^3 cells: the only patch is the whole mesh, so one sweep from any x is A^{-1} b."""
+    g = GpuMG(2, k, prec, coarse_cells=1, smoother=VP)
+    try:
+        fl = g.info["levels"] - 1
+        n = g.info["ndofs"][fl]
+        b, x0 = uniform_vector(n, seed=23), uniform_vector(n, seed=24)
+        x = g.vec(x0)
+        g.lib.tp_mg_smooth(g.mg, fl, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        ref = FastDiag(k, 2, 2, 2).solve(b)
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-11 if prec == "fp64" else 1e-4)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,nc,cnc", [(1, 8, 1), (2, 8, 2), (3, 4, 1)])
+def test_vertex_patch_vcycle_matches_oracle(prec, k, nc, cnc):
+    g = GpuMG(nc, k, prec, coarse_cells=cnc, smoother=VP)
+    try:
+        n = g.info["ndofs"][-1]
+        b, x0 = uniform_vector(n, seed=25), uniform_vector(n, seed=26)
+        x = g.vec(x0)
+        g.lib.tp_vcycle(g.mg, x.data_ptr(), g.vec(b).data_ptr())
+        torch.cuda.synchronize()
+        mg = VCycle(k, nc, coarse_nc=cnc, smoother="vertex_patch")
+        assert len(mg.levels) == g.info["levels"]
+        ref = mg.vcycle(len(mg.levels) - 1, b, x0)
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-11 if prec == "fp64" else 5e-5)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("mg_prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("k,nc", [(3, 16), (2, 16), (7, 8)])
+def test_vertex_patch_solve_matches_exact_discrete_solution(mg_prec, k, nc):
+    """FGMRES with the vertex-patch V-cycle: the exact discrete solution in at most six iterations
+    (the Chebyshev-Jacobi V-cycle takes 12-15 on these problems)."""
+    x, info = _solve(nc, k, mg_prec, coarse_cells=2, smoother=VP)
+    assert info["converged"] == 1 and info["iterations"] <= 6
+    assert info["true_rel_residual"] < 2e-10
+    assert rel_l2(x, FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))) < 1e-8
+
+
+@pytest.mark.parametrize("k,nc", [(3, 64), (7, 32)])
+def test_vertex_patch_mixed_solve_discretization_error(k, nc):
+    # FP32 vertex-patch V-cycle inside FP64 FGMRES at the Sec. 7.2 sizes: the L2 rule against the
+    # exact discrete solution
+    x, info = _solve(nc, k, "fp32", smoother=VP)
+    assert info["converged"] == 1
+    u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+    e_mixed = l2_error(x, k, nc, nc, nc, sine_exact)
+    e_exact = l2_error(u, k, nc, nc, nc, sine_exact)
+    assert _l2_rule(e_mixed, e_exact), (e_mixed, e_exact)
+
+
+def test_vertex_patch_rejects_half_precision():
+    from paper_2407_09621_gb300 import _lib
+    mesh = _lib.tp_mesh_create(4, 4, 4)
+    op = _lib.tp_dg_laplace_create(mesh, 3, _lib.TP_FP64)
+    try:
+        for p in (_lib.TP_FP16, _lib.TP_BF16):
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_mg_create(op, precision=p, smoother=VP)
+            assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_mg_create(op, smoother=5)
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
+    finally:
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
