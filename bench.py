@@ -360,13 +360,17 @@ def batch_bench(count=32, streams=8):
     probs = batch_problems(count=count)
     res_c, t_c = _lib.tp_batch_solve(probs, streams=streams)
     res_s, t_s = _lib.tp_batch_solve(probs, streams=1)
+    res_v, t_v = _lib.tp_batch_solve(probs, streams=streams, smoother=_lib.TP_SMOOTHER_VERTEX_PATCH)
     dofs = sum(p["dofs"] for p in probs)
     return {"problems": count, "total_dofs": dofs, "degrees": sorted({p["k"] for p in probs}),
             "cells": sorted({p["cells"] for p in probs}),
             "concurrent_seconds": t_c, "sequential_seconds": t_s, "speedup": t_s / t_c, "streams": streams,
             "all_converged": all(r["converged"] == 1 for r in res_c),
             "iterations_max": max(r["iterations"] for r in res_c),
-            "l2_errors": [r["l2_error"] for r in res_c]}
+            "l2_errors": [r["l2_error"] for r in res_c],
+            "vertex_patch": {"concurrent_seconds": t_v, "speedup_vs_chebyshev": t_c / t_v,
+                             "all_converged": all(r["converged"] == 1 for r in res_v),
+                             "iterations_max": max(r["iterations"] for r in res_v)}}
 
 
 def run_ours(args):

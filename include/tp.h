@@ -320,6 +320,7 @@ typedef struct {
   int maxit;           /* per problem (default 300) */
   int streams;         /* concurrent worker streams (default 8; 1 = one after another) */
   int autotune;        /* 1: autotune every problem's apply tile shapes (tp_op_opts.autotune) */
+  int smoother;        /* as tp_mg_opts.smoother (default TP_SMOOTHER_CHEBYSHEV) */
 } tp_batch_opts;
 
 typedef struct {

@@ -276,7 +276,7 @@ def tp_batch_solve_solvers(solvers, x_ptrs, b_ptrs, rtol=1e-10, maxit=300, strea
     sv = (_vp * n)(*[s if isinstance(s, _vp) else _vp(s) for s in solvers])
     xv = (_vp * n)(*[_vp(p) for p in x_ptrs])
     bv = (_vp * n)(*[_vp(p) for p in b_ptrs])
-    opts = tp_batch_opts(TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, rtol, maxit, streams, 0)
+    opts = tp_batch_opts(TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, rtol, maxit, streams, 0, TP_SMOOTHER_CHEBYSHEV)
     infos = (tp_solve_info * n)()
     sts = (ctypes.c_int * n)()
     total = ctypes.c_double()
@@ -323,7 +323,7 @@ class tp_batch_problem(ctypes.Structure):
 class tp_batch_opts(ctypes.Structure):
     _fields_ = [("mg_precision", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("streams", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("streams", ctypes.c_int), ("autotune", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 
 class tp_batch_result(ctypes.Structure):
@@ -338,7 +338,7 @@ lib.tp_batch_solve.argtypes = [ctypes.POINTER(tp_batch_problem), ctypes.c_int, c
 
 
 def tp_batch_solve(problems, mg_precision=TP_FP32, kernel=TP_KERNEL_CUDA_CORE, ec=0, restart=30, rtol=1e-10,
-                   maxit=300, streams=8, autotune=0):
+                   maxit=300, streams=8, autotune=0, smoother=TP_SMOOTHER_CHEBYSHEV):
     """problems: list of dicts {cells: (nx, ny, nz) or int, k, modes: [(a, p, q, r), ...], x_ptr (optional)}.
     Returns (list of result dicts, total solve seconds)."""
     n = len(problems)
@@ -350,7 +350,7 @@ def tp_batch_solve(problems, mg_precision=TP_FP32, kernel=TP_KERNEL_CUDA_CORE, e
         a, pqr = _modes_arrays(p["modes"])
         keep += [a, pqr]
         arr[i] = tp_batch_problem(nx, ny, nz, p["k"], len(p["modes"]), a, pqr, _vp(p.get("x_ptr") or 0))
-    opts = tp_batch_opts(mg_precision, kernel, ec, restart, rtol, maxit, streams, autotune)
+    opts = tp_batch_opts(mg_precision, kernel, ec, restart, rtol, maxit, streams, autotune, smoother)
     res = (tp_batch_result * n)()
     total = ctypes.c_double()
     _check(lib.tp_batch_solve(arr, n, ctypes.byref(opts), res, ctypes.byref(total)))

@@ -8,7 +8,7 @@ namespace tp {
 // n > 8, FP64 and FP32 vectors (apply_cc_high.cu)
 cudaError_t prepare_apply_cc_high(const tp_op_s* op);
 cudaError_t launch_apply_cc_high(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const void* b);
 
 template <typename TS, typename TC>
 static cudaError_t prepare_cc_t(int n) {
@@ -37,15 +37,16 @@ cudaError_t prepare_apply_cc(const tp_op_s* op) {
 }
 
 template <typename TS, typename TC>
-static cudaError_t launch_cc_t(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s) {
+static cudaError_t launch_cc_t(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s,
+                               const void* b) {
   switch (op->n) {
-    case 2: return launch_cc_n<TS, TC, 2>(op, y, x, c0, c1, s);
-    case 3: return launch_cc_n<TS, TC, 3>(op, y, x, c0, c1, s);
-    case 4: return launch_cc_n<TS, TC, 4>(op, y, x, c0, c1, s);
-    case 5: return launch_cc_n<TS, TC, 5>(op, y, x, c0, c1, s);
-    case 6: return launch_cc_n<TS, TC, 6>(op, y, x, c0, c1, s);
-    case 7: return launch_cc_n<TS, TC, 7>(op, y, x, c0, c1, s);
-    case 8: return launch_cc_n<TS, TC, 8>(op, y, x, c0, c1, s);
+    case 2: return launch_cc_n<TS, TC, 2>(op, y, x, c0, c1, s, b);
+    case 3: return launch_cc_n<TS, TC, 3>(op, y, x, c0, c1, s, b);
+    case 4: return launch_cc_n<TS, TC, 4>(op, y, x, c0, c1, s, b);
+    case 5: return launch_cc_n<TS, TC, 5>(op, y, x, c0, c1, s, b);
+    case 6: return launch_cc_n<TS, TC, 6>(op, y, x, c0, c1, s, b);
+    case 7: return launch_cc_n<TS, TC, 7>(op, y, x, c0, c1, s, b);
+    case 8: return launch_cc_n<TS, TC, 8>(op, y, x, c0, c1, s, b);
   }
   return cudaErrorInvalidValue;
 }
@@ -58,21 +59,22 @@ int cc_tile_cells(int n, int v) {
   return v == 0 ? (base / 2 > 0 ? base / 2 : 1) : (v == 1 ? base : 2 * base);
 }
 
-// Output rows of cells [c0, c1) only (the input is read wherever those cells' faces reach).
+// Output rows of cells [c0, c1) only (the input is read wherever those cells' faces reach);
+// y = A x, or y = b - A x when b is not null (b and y must not overlap x).
 cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                                  cudaStream_t s) {
-  if (op->n > kMaxN) return launch_apply_cc_high(op, y, x, c0, c1, s);
+                                  cudaStream_t s, const void* b) {
+  if (op->n > kMaxN) return launch_apply_cc_high(op, y, x, c0, c1, s, b);
   switch (op->prec) {
-    case TP_FP64: return launch_cc_t<double, double>(op, y, x, c0, c1, s);
-    case TP_FP32: return launch_cc_t<float, float>(op, y, x, c0, c1, s);
-    case TP_FP16: return launch_cc_t<__half, float>(op, y, x, c0, c1, s);
-    case TP_BF16: return launch_cc_t<__nv_bfloat16, float>(op, y, x, c0, c1, s);
+    case TP_FP64: return launch_cc_t<double, double>(op, y, x, c0, c1, s, b);
+    case TP_FP32: return launch_cc_t<float, float>(op, y, x, c0, c1, s, b);
+    case TP_FP16: return launch_cc_t<__half, float>(op, y, x, c0, c1, s, b);
+    case TP_BF16: return launch_cc_t<__nv_bfloat16, float>(op, y, x, c0, c1, s, b);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
-  return launch_apply_cc_range(op, y, x, 0, op->ncells, s);
+  return launch_apply_cc_range(op, y, x, 0, op->ncells, s, nullptr);
 }
 
 }  // namespace tp

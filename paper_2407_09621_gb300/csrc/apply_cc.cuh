@@ -29,12 +29,15 @@
 // constant-bank operands of the FMAs. Phases: (A) x- and y-lines of
 // w_x = G_x u + x faces and w_y = G_y u + y faces; (B) z-lines: w = w_x + w_y
 // + G_z u + z faces, then M_z w in registers; (C) y-lines: M_y; (D) x-lines:
-// M_x and the store. TS = storage type of the vectors, TC = arithmetic type.
+// M_x and the store; given a vector b the store is the residual b - A x instead (the smoother's
+// residuals without a separate pass). TS = storage type of the vectors, TC = arithmetic type.
 //
-// Degrees above 7 (8 < n <= 16, FP64 and FP32): one cell per block (n^2 threads), the cell
-// tensors padded to a row pitch of n + 1 so that the x-line phases, whose threads read rows n
-// values apart, hit distinct shared-memory banks, and three cell buffers instead of four (M_z w
-// overwrites u: in phase B every thread reads and writes its own z-line only).
+// Degrees above 7 (8 < n <= 16, FP64 and FP32): one cell per block (n^2 threads) and three cell
+// buffers instead of four (M_z w overwrites u: in phase B every thread reads and writes its own
+// z-line only). The cell tensors are padded to a row pitch of n + 1 there and for FP32
+// arithmetic at every n, so that the x-line phases, whose threads read rows n values apart, hit
+// distinct shared-memory banks (the FP32 kernels are bound by shared-memory and L1 throughput;
+// the FP64 ones by the FP64 pipe, and keep the unpadded layout).
 //
 // Instantiated in apply_cc.cu (n <= 8) and apply_cc_high.cu (8 < n <= 16).
 #pragma once
@@ -56,13 +59,15 @@ __host__ __device__ constexpr int cc_cells_per_block() {
 
 // Row pitch of the shared cell tensors (element (l, j, i) at (l*N + j)*R + i) and the number
 // of cell buffers; the operator constants' row pitch.
-template <int N> __host__ __device__ constexpr int cc_pitch() { return N > kMaxN ? N + 1 : N; }
+template <typename TC, int N> __host__ __device__ constexpr int cc_pitch() {
+  return (N > kMaxN || sizeof(TC) == 4) ? N + 1 : N;
+}
 template <int N> __host__ __device__ constexpr int cc_buffers() { return N > kMaxN ? 3 : 4; }
 template <typename TC, int N> using CcConst = OpConst<TC, (N > kMaxN ? kMaxNHigh : kMaxN)>;
 
 template <typename TC, int N, int V>
 __host__ __device__ constexpr size_t cc_smem_bytes() {
-  return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<N>() * N * N * cc_pitch<N>();
+  return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<N>() * N * N * cc_pitch<TC, N>();
 }
 
 // out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst), H = n/2
@@ -131,13 +136,13 @@ __device__ __forceinline__ void contract_d(TC (&out)[N], const CcConst<TC, N>& P
   contract<TC, N, S>(out, mass ? P.M[d] : P.G[d], in);
 }
 
-template <typename TS, typename TC, int N, int V>
+template <typename TS, typename TC, int N, int V, bool RES>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
-apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_constant__ CcConst<TC, N> P,
-                int nx, int ny, int nz, long long c_begin, long long c_end) {
+apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restrict__ b,
+                const __grid_constant__ CcConst<TC, N> P, int nx, int ny, int nz, long long c_begin, long long c_end) {
   constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr int N2 = N * N, N3 = N * N * N;
-  constexpr int R = cc_pitch<N>(), B = N * N * R;  // row pitch and size of a shared cell tensor
+  constexpr int R = cc_pitch<TC, N>(), B = N * N * R;  // row pitch and size of a shared cell tensor
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
@@ -216,21 +221,27 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const __grid_const
   }
   __syncthreads();
 
-  // ---- (D) x-line (l=p, j=q): M_x and scatter
+  // ---- (D) x-line (l=p, j=q): M_x and scatter (y = A x, or y = b - A x when b is given)
   if (valid) {
     TC w[N], v[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) w[m] = sX[(p * N + q) * R + m];
     contract_d<TC, N>(v, P, true, 0, w);
     TS* yc = y + cell * N3 + p * N2 + q * N;
+    if constexpr (RES) {
+      const TS* bc = b + cell * N3 + p * N2 + q * N;
 #pragma unroll
-    for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, v[i]);
+      for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, load_as<TS, TC>(bc + i) - v[i]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, v[i]);
+    }
   }
 }
 
-template <typename TS, typename TC, int N, int V>
-static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                               cudaStream_t s) {
+template <typename TS, typename TC, int N, int V, bool RES>
+static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s,
+                               const void* b) {
   constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr size_t smem = cc_smem_bytes<TC, N, V>();
   const long long blocks = (c1 - c0 + CPB - 1) / CPB;
@@ -238,43 +249,48 @@ static cudaError_t launch_cc_v(const tp_op_s* op, void* y, const void* x, long l
   if (blocks <= 0) return cudaSuccess;
   const CcConst<TC, N>& P = *static_cast<const CcConst<TC, N>*>(
       N > kMaxN ? op->hconst_high(sizeof(TC)) : op->hconst(sizeof(TC)));
-  apply_cc_kernel<TS, TC, N, V><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
-      static_cast<const TS*>(x), static_cast<TS*>(y), P, op->mesh.nx, op->mesh.ny, op->mesh.nz, c0, c1);
+  apply_cc_kernel<TS, TC, N, V, RES><<<(unsigned)blocks, N * N * CPB, smem, s>>>(
+      static_cast<const TS*>(x), static_cast<TS*>(y), static_cast<const TS*>(b), P, op->mesh.nx, op->mesh.ny,
+      op->mesh.nz, c0, c1);
   return cudaGetLastError();
 }
 
-// Launch of the tile variant the operator selected (n > 8: the one-cell tile only).
+// Launch of the tile variant the operator selected (n > 8: the one-cell tile only); the
+// residual form b - A x (b not null) always takes the default tile.
 template <typename TS, typename TC, int N>
-static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                               cudaStream_t s) {
+static cudaError_t launch_cc_n(const tp_op_s* op, void* y, const void* x, long long c0, long long c1, cudaStream_t s,
+                               const void* b) {
+  if (b) return launch_cc_v<TS, TC, N, 1, true>(op, y, x, c0, c1, s, b);
   if constexpr (N > kMaxN) {
-    return launch_cc_v<TS, TC, N, 1>(op, y, x, c0, c1, s);
+    return launch_cc_v<TS, TC, N, 1, false>(op, y, x, c0, c1, s, b);
   } else {
     switch (op->tile_variant) {
-      case 0: return launch_cc_v<TS, TC, N, 0>(op, y, x, c0, c1, s);
-      case 2: return launch_cc_v<TS, TC, N, 2>(op, y, x, c0, c1, s);
+      case 0: return launch_cc_v<TS, TC, N, 0, false>(op, y, x, c0, c1, s, b);
+      case 2: return launch_cc_v<TS, TC, N, 2, false>(op, y, x, c0, c1, s, b);
     }
-    return launch_cc_v<TS, TC, N, 1>(op, y, x, c0, c1, s);
+    return launch_cc_v<TS, TC, N, 1, false>(op, y, x, c0, c1, s, b);
   }
 }
 
-template <typename TS, typename TC, int N, int V>
+template <typename TS, typename TC, int N, int V, bool RES>
 static cudaError_t prepare_cc_v() {
-  return cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(apply_cc_kernel<TS, TC, N, V, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)cc_smem_bytes<TC, N, V>());
 }
 
-// Sets the dynamic shared-memory limit of every tile variant of degree N on the current device.
+// Sets the dynamic shared-memory limit of every tile variant of degree N, and of the residual
+// form, on the current device.
 template <typename TS, typename TC, int N>
 static cudaError_t prepare_cc_n() {
+  cudaError_t e = prepare_cc_v<TS, TC, N, 1, true>();
   if constexpr (N > kMaxN) {
-    return prepare_cc_v<TS, TC, N, 1>();
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 1, false>();
   } else {
-    cudaError_t e = prepare_cc_v<TS, TC, N, 0>();
-    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 1>();
-    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 2>();
-    return e;
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 0, false>();
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 1, false>();
+    if (e == cudaSuccess) e = prepare_cc_v<TS, TC, N, 2, false>();
   }
+  return e;
 }
 
 }  // namespace tp

@@ -22,16 +22,16 @@ static cudaError_t prepare_high_t(int n) {
 
 template <typename T>
 static cudaError_t launch_high_t(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const void* b) {
   switch (op->n) {
-    case 9: return launch_cc_n<T, T, 9>(op, y, x, c0, c1, s);
-    case 10: return launch_cc_n<T, T, 10>(op, y, x, c0, c1, s);
-    case 11: return launch_cc_n<T, T, 11>(op, y, x, c0, c1, s);
-    case 12: return launch_cc_n<T, T, 12>(op, y, x, c0, c1, s);
-    case 13: return launch_cc_n<T, T, 13>(op, y, x, c0, c1, s);
-    case 14: return launch_cc_n<T, T, 14>(op, y, x, c0, c1, s);
-    case 15: return launch_cc_n<T, T, 15>(op, y, x, c0, c1, s);
-    case 16: return launch_cc_n<T, T, 16>(op, y, x, c0, c1, s);
+    case 9: return launch_cc_n<T, T, 9>(op, y, x, c0, c1, s, b);
+    case 10: return launch_cc_n<T, T, 10>(op, y, x, c0, c1, s, b);
+    case 11: return launch_cc_n<T, T, 11>(op, y, x, c0, c1, s, b);
+    case 12: return launch_cc_n<T, T, 12>(op, y, x, c0, c1, s, b);
+    case 13: return launch_cc_n<T, T, 13>(op, y, x, c0, c1, s, b);
+    case 14: return launch_cc_n<T, T, 14>(op, y, x, c0, c1, s, b);
+    case 15: return launch_cc_n<T, T, 15>(op, y, x, c0, c1, s, b);
+    case 16: return launch_cc_n<T, T, 16>(op, y, x, c0, c1, s, b);
   }
   return cudaErrorInvalidValue;
 }
@@ -46,10 +46,10 @@ cudaError_t prepare_apply_cc_high(const tp_op_s* op) {
 }
 
 cudaError_t launch_apply_cc_high(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const void* b) {
   switch (op->prec) {
-    case TP_FP64: return launch_high_t<double>(op, y, x, c0, c1, s);
-    case TP_FP32: return launch_high_t<float>(op, y, x, c0, c1, s);
+    case TP_FP64: return launch_high_t<double>(op, y, x, c0, c1, s, b);
+    case TP_FP32: return launch_high_t<float>(op, y, x, c0, c1, s, b);
     default: break;
   }
   return cudaErrorInvalidValue;

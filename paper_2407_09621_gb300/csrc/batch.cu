@@ -126,7 +126,7 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     set_error("tp_batch_solve: need problems, count >= 1 and a results array");
     return TP_ERR_INVALID_ARG;
   }
-  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0};
+  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0, TP_SMOOTHER_CHEBYSHEV};
   if (opts) o = *opts;
   if (o.streams < 1 || o.streams > 64 || o.restart < 1 || !(o.rtol > 0) || o.maxit < 1) {
     set_error("tp_batch_solve: invalid options (streams 1..64, restart >= 1, rtol > 0, maxit >= 1)");
@@ -144,7 +144,7 @@ extern "C" tp_status tp_batch_solve(const tp_batch_problem* probs, int count, co
     if (st == TP_OK) st = tp_dg_laplace_create(&it.op, it.mesh, p.k, TP_FP64, &oo);
     if (st != TP_OK) break;
     it.ndofs = it.op->ndofs;
-    tp_mg_opts mo{3, 15.0, 1.1, 0.0, 4, o.mg_precision, 20, o.kernel, o.ec, TP_FP16, TP_SMOOTHER_CHEBYSHEV};
+    tp_mg_opts mo{3, 15.0, 1.1, 0.0, 4, o.mg_precision, 20, o.kernel, o.ec, TP_FP16, o.smoother};
     st = tp_mg_create(&it.mg, it.op, &mo);
     if (st == TP_OK) st = tp_fgmres_create(&it.solver, it.op, it.mg, o.restart);
     if (st == TP_OK) st = cuda_status(cudaMalloc(&it.b, sizeof(double) * it.ndofs), "tp_batch_solve");
@@ -210,7 +210,7 @@ extern "C" tp_status tp_batch_solve_solvers(const tp_solver* solvers, double* co
     set_error("tp_batch_solve_solvers: need solvers, x and b arrays and count >= 1");
     return TP_ERR_INVALID_ARG;
   }
-  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0};
+  tp_batch_opts o{TP_FP32, TP_KERNEL_CUDA_CORE, 0, 30, 1e-10, 300, 8, 0, TP_SMOOTHER_CHEBYSHEV};
   if (opts) o = *opts;
   if (o.streams < 1 || o.streams > 64 || !(o.rtol > 0) || o.maxit < 1) {
     set_error("tp_batch_solve_solvers: invalid options (streams 1..64, rtol > 0, maxit >= 1)");

@@ -27,6 +27,7 @@ namespace tp {
 
 tp_status cuda_status(int err, const char* what);
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_residual(const tp_op_s* op, void* r, const void* b, const void* x, cudaStream_t s);
 size_t elem_bytes(tp_precision p);
 // vertex-patch smoother (schwarz.cu)
 bool vp_colour_nonempty(const int nc[3], int c);
@@ -520,9 +521,11 @@ static cudaError_t sub_t(long long n, void* r, const void* b, const void* t, cud
   return multi_axpy<T>(n, (T*)r, 0.0, v, c, 2, s);
 }
 
-// r = b - A x  (t is scratch)
+// r = b - A x: fused into the CUDA-core apply's store, else A x into the scratch t and a
+// difference pass
 static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, const void* b, const void* x, void* t,
                             cudaStream_t s) {
+  if (L.op->opts.kernel != TP_KERNEL_TENSOR) return launch_residual(L.op, r, b, x, s);
   cudaError_t e = launch_apply(L.op, t, x, s);
   if (e != cudaSuccess) return e;
   TP_DISPATCH_PREC(mg->prec, return sub_t<T>(L.ndofs, r, b, t, s))

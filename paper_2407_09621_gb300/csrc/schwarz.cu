@@ -18,8 +18,8 @@
 //
 // Work layout: P^2 threads per patch; in every phase a thread owns one line of the patch tensor
 // along the contracted direction (rows padded to P + 1 against bank conflicts). Phases: S_x^T,
-// S_y^T, then along z S_z^T, the scaling and S_z in registers, then S_y, and S_x with the update
-// of x.
+// S_y^T, then along z S_z^T, the scaling and S_z, then S_y and S_x; the patch tensor is read from
+// r and added to x cell by cell, so that a warp's accesses are contiguous.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -71,15 +71,25 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
       if (tid < P) sL[d][tid] = Ltab[(d * 4 + t[d]) * kMaxP + tid];
     }
   }
-  // the patch's cells: (v - 1 + lx, v - 1 + ly, v - 1 + lz), lx, ly, lz in {0, 1}
+  // The patch's cells are (v - 1 + lx, v - 1 + ly, v - 1 + lz), lx, ly, lz in {0, 1}. Global
+  // accesses walk the patch cell by cell (e = lc * n^3 + node: a warp reads contiguous values of
+  // one cell) and map each value to its patch coordinates (Z, Y, X).
   const long long c0 = ((long long)(vz - 1) * D.ny + (vy - 1)) * D.nx + (vx - 1);
-  auto gidx = [&](int Z, int Y, int X) {
-    const long long cell = c0 + ((long long)(Z / N) * D.ny + (Y / N)) * D.nx + (X / N);
-    return cell * N3 + ((Z % N) * N + (Y % N)) * N + (X % N);
+  auto gaddr = [&](int e) {
+    const int lc = e / N3;
+    return (c0 + ((long long)(lc >> 2) * D.ny + ((lc >> 1) & 1)) * D.nx + (lc & 1)) * N3 + e % N3;
   };
-  for (int e = tid; e < P * P * P; e += P * P) {
-    const int Z = e / (P * P), Y = (e / P) % P, X = e % P;
-    bufA[(Z * P + Y) * R + X] = r[gidx(Z, Y, X)];
+  auto saddr = [&](int e) {
+    const int lc = e / N3, node = e % N3;
+    const int X = (lc & 1) * N + node % N, Y = ((lc >> 1) & 1) * N + (node / N) % N, Z = (lc >> 2) * N + node / (N * N);
+    return (Z * P + Y) * R + X;
+  };
+  {
+    T v[P];  // all P loads in flight before the shared stores
+#pragma unroll
+    for (int j = 0; j < P; ++j) v[j] = __ldg(r + gaddr(tid + j * P * P));
+#pragma unroll
+    for (int j = 0; j < P; ++j) bufA[saddr(tid + j * P * P)] = v[j];
   }
   __syncthreads();
   // One line of the patch tensor in registers, in[m], contracted per output node o:
@@ -141,7 +151,7 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
     bufB[(p * P + Y) * R + q] = s;
   }
   __syncthreads();
-  // S_x along x-lines (Z = p, Y = q) and x_P += the correction
+  // S_x along x-lines (Z = p, Y = q): bufB -> bufA
 #pragma unroll
   for (int a = 0; a < P; ++a) in[a] = bufB[(p * P + q) * R + a];
 #pragma unroll 2
@@ -149,8 +159,16 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
     T s = sS[0][X * P] * in[0];
 #pragma unroll
     for (int a = 1; a < P; ++a) s = fma(sS[0][X * P + a], in[a], s);
-    T* px = x + gidx(p, q, X);
-    *px += s;
+    bufA[(p * P + q) * R + X] = s;
+  }
+  __syncthreads();
+  // x_P += the correction, cell by cell like the gather
+  {
+    T v[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) v[j] = x[gaddr(tid + j * P * P)];
+#pragma unroll
+    for (int j = 0; j < P; ++j) x[gaddr(tid + j * P * P)] = v[j] + bufA[saddr(tid + j * P * P)];
   }
 }
 

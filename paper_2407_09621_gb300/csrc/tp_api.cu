@@ -28,7 +28,7 @@ tp_status cuda_status(int err, const char* what) {
 
 cudaError_t launch_apply_cc(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
-                                  cudaStream_t s);
+                                  cudaStream_t s, const void* b);
 cudaError_t launch_apply_dmma_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
                                     cudaStream_t s);
 cudaError_t prepare_apply_cc(const tp_op_s* op);
@@ -46,6 +46,13 @@ cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t
   if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc(op, y, x, s);
   if (op->prec == TP_FP64) return launch_apply_dmma(op, y, x, s);
   return op->use_umma ? launch_apply_umma(op, y, x, s) : launch_apply_tc(op, y, x, s);
+}
+
+// r = b - A x in one pass where the CUDA-core kernel runs (its store takes b); other kernel
+// families return cudaErrorNotSupported and the caller forms A x and the difference.
+cudaError_t launch_residual(const tp_op_s* op, void* r, const void* b, const void* x, cudaStream_t s) {
+  if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc_range(op, r, x, 0, op->ncells, s, b);
+  return cudaErrorNotSupported;
 }
 
 int cc_tile_cells(int n, int v);
@@ -283,7 +290,7 @@ tp_status apply_host_pipelined(tp_op_s* op, void* y_host, const void* x_host, cu
   auto z_at = [&](int i) { return (long long)nz * i / kChunks; };  // chunk i = slabs [z_at(i), z_at(i+1))
   auto launch = [&](long long c0, long long c1, cudaStream_t st) {
     return op->opts.kernel == TP_KERNEL_TENSOR ? launch_apply_dmma_range(op, op->hy, op->hx, c0, c1, st)
-                                               : launch_apply_cc_range(op, op->hy, op->hx, c0, c1, st);
+                                               : launch_apply_cc_range(op, op->hy, op->hx, c0, c1, st, nullptr);
   };
   tp_status st = cuda_status(cudaEventRecord(P.start, s), "tp_apply_host");
   for (cudaStream_t q : {P.in, P.comp, P.out})

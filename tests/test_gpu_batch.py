@@ -18,15 +18,15 @@ def _exact(modes):
                                for a, p, q, r in modes)
 
 
-@pytest.mark.parametrize("autotune", [0, 1])
-def test_small_uneven_batch_matches_oracle(autotune):
+@pytest.mark.parametrize("autotune,smoother", [(0, 0), (1, 0), (0, 1)])
+def test_small_uneven_batch_matches_oracle(autotune, smoother):
     from paper_2407_09621_gb300 import _lib
     probs = batch_problems(count=6, seed_base=2000, cells_choices=(4, 6, 8), degrees=(1, 2, 3, 4, 5, 6, 7))
     xs = []
     for p in probs:
         xs.append(torch.zeros(p["dofs"], dtype=torch.float64, device="cuda"))
         p["x_ptr"] = xs[-1].data_ptr()
-    res, total = _lib.tp_batch_solve(probs, streams=4, autotune=autotune)
+    res, total = _lib.tp_batch_solve(probs, streams=4, autotune=autotune, smoother=smoother)
     assert total > 0
     for p, r, x in zip(probs, res, xs):
         c, k = p["cells"], p["k"]
