@@ -22,6 +22,7 @@
 // r and added to x cell by cell, so that a warp's accesses are contiguous.
 #include <cuda_runtime.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "tp_internal.h"
@@ -42,11 +43,33 @@ struct VPDims {
 // patches of parity p along a direction with nc cells: vertices p, p + 2, ... in [1, nc - 1]
 __host__ __device__ inline int vp_count(int p, int nc) { return p ? nc / 2 : (nc - 1) / 2; }
 
-// dynamic shared memory of the patch kernel: two padded patch tensors, three P x P bases, 3P
-// eigenvalues
+// Widest vector type that tiles a row of P values: the basis rows are read with one wide
+// shared-memory load per W coefficients (the kernel is bound by load instructions otherwise).
+template <typename T, int P> struct RowVec { using V = float2; };
+template <int P> struct RowVec<float, P> { using V = typename std::conditional<P % 4 == 0, float4, float2>::type; };
+template <int P> struct RowVec<double, P> { using V = double2; };
+
+template <typename T, int P>
+__device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&in)[P]) {
+  using V = typename RowVec<T, P>::V;
+  constexpr int W = sizeof(V) / sizeof(T);
+  const V* rv = reinterpret_cast<const V*>(row);
+  T s = T(0);
+#pragma unroll
+  for (int m = 0; m < P / W; ++m) {
+    const V c = rv[m];
+    const T* cc = reinterpret_cast<const T*>(&c);
+#pragma unroll
+    for (int w = 0; w < W; ++w) s = fma(cc[w], in[m * W + w], s);
+  }
+  return s;
+}
+
+// dynamic shared memory of the patch kernel: two padded patch tensors, six P x P bases (S^T and S
+// per direction), 3P eigenvalues
 template <typename T, int N>
 constexpr size_t vp_smem_bytes() {
-  return sizeof(T) * (2 * (2 * N) * (2 * N) * (2 * N + 1) + 3 * (2 * N) * (2 * N) + 3 * (2 * N));
+  return sizeof(T) * (2 * (2 * N) * (2 * N) * (2 * N + 1) + 6 * (2 * N) * (2 * N) + 3 * (2 * N));
 }
 
 template <typename T, int N>
@@ -57,8 +80,9 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
   extern __shared__ __align__(16) unsigned char vp_smem[];
   T* bufA = reinterpret_cast<T*>(vp_smem);
   T* bufB = bufA + P * P * R;
-  T (*sS)[P * P] = reinterpret_cast<T (*)[P * P]>(bufB + P * P * R);
-  T (*sL)[P] = reinterpret_cast<T (*)[P]>(bufB + P * P * R + 3 * P * P);
+  T (*sF)[P * P] = reinterpret_cast<T (*)[P * P]>(bufB + P * P * R);  // sF[d][a * P + m] = S_d[m][a]
+  T (*sB)[P * P] = sF + 3;                                               // sB[d][X * P + a] = S_d[X][a]
+  T (*sL)[P] = reinterpret_cast<T (*)[P]>(bufB + P * P * R + 6 * P * P);
   const int tid = threadIdx.x, p = tid / P, q = tid % P;
   const int vx = D.first[0] + 2 * (int)blockIdx.x, vy = D.first[1] + 2 * (int)blockIdx.y;
   const int vz = D.first[2] + 2 * (int)blockIdx.z;
@@ -67,7 +91,9 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
                       (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      sS[d][tid] = Stab[(size_t)(d * 4 + t[d]) * kMaxP * kMaxP + p * kMaxP + q];  // tid = X * P + a
+      const T v = Stab[(size_t)(d * 4 + t[d]) * kMaxP * kMaxP + p * kMaxP + q];  // S_d[p][q]
+      sB[d][p * P + q] = v;
+      sF[d][q * P + p] = v;
       if (tid < P) sL[d][tid] = Ltab[(d * 4 + t[d]) * kMaxP + tid];
     }
   }
@@ -92,31 +118,21 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
     for (int j = 0; j < P; ++j) bufA[saddr(tid + j * P * P)] = v[j];
   }
   __syncthreads();
-  // One line of the patch tensor in registers, in[m], contracted per output node o:
-  // sum_m S[m][o] in[m] (S^T applied) or sum_m S[o][m] in[m] (S applied); each output goes
-  // straight to shared memory.
+  // One line of the patch tensor in registers, in[m], contracted per output node o with a basis
+  // row: sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of
+  // sB); each output goes straight to shared memory.
   T in[P];
   // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
 #pragma unroll
   for (int m = 0; m < P; ++m) in[m] = bufA[(p * P + q) * R + m];
 #pragma unroll 2
-  for (int a = 0; a < P; ++a) {
-    T s = sS[0][a] * in[0];
-#pragma unroll
-    for (int m = 1; m < P; ++m) s = fma(sS[0][m * P + a], in[m], s);
-    bufB[(p * P + q) * R + a] = s;
-  }
+  for (int a = 0; a < P; ++a) bufB[(p * P + q) * R + a] = dot_row<T, P>(sF[0] + a * P, in);
   __syncthreads();
   // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
 #pragma unroll
   for (int m = 0; m < P; ++m) in[m] = bufB[(p * P + m) * R + q];
 #pragma unroll 2
-  for (int b = 0; b < P; ++b) {
-    T s = sS[1][b] * in[0];
-#pragma unroll
-    for (int m = 1; m < P; ++m) s = fma(sS[1][m * P + b], in[m], s);
-    bufA[(p * P + b) * R + q] = s;
-  }
+  for (int b = 0; b < P; ++b) bufA[(p * P + b) * R + q] = dot_row<T, P>(sF[1] + b * P, in);
   __syncthreads();
   // z-lines (b = p, a = q): S_z^T and the eigenvalue scaling into bufB, then S_z back into bufA.
   // A thread reads and writes only its own z-line here, so no barrier is needed in between.
@@ -124,43 +140,23 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
   for (int m = 0; m < P; ++m) in[m] = bufA[(m * P + p) * R + q];
   const T lxy = sL[0][q] + sL[1][p];
 #pragma unroll 2
-  for (int c = 0; c < P; ++c) {
-    T s = sS[2][c] * in[0];
-#pragma unroll
-    for (int m = 1; m < P; ++m) s = fma(sS[2][m * P + c], in[m], s);
-    bufB[(c * P + p) * R + q] = s / (lxy + sL[2][c]);
-  }
+  for (int c = 0; c < P; ++c) bufB[(c * P + p) * R + q] = dot_row<T, P>(sF[2] + c * P, in) / (lxy + sL[2][c]);
 #pragma unroll
   for (int c = 0; c < P; ++c) in[c] = bufB[(c * P + p) * R + q];
 #pragma unroll 2
-  for (int Z = 0; Z < P; ++Z) {
-    T s = sS[2][Z * P] * in[0];
-#pragma unroll
-    for (int c = 1; c < P; ++c) s = fma(sS[2][Z * P + c], in[c], s);
-    bufA[(Z * P + p) * R + q] = s;
-  }
+  for (int Z = 0; Z < P; ++Z) bufA[(Z * P + p) * R + q] = dot_row<T, P>(sB[2] + Z * P, in);
   __syncthreads();
   // S_y along y-lines (Z = p, a = q): bufA -> bufB
 #pragma unroll
   for (int b = 0; b < P; ++b) in[b] = bufA[(p * P + b) * R + q];
 #pragma unroll 2
-  for (int Y = 0; Y < P; ++Y) {
-    T s = sS[1][Y * P] * in[0];
-#pragma unroll
-    for (int b = 1; b < P; ++b) s = fma(sS[1][Y * P + b], in[b], s);
-    bufB[(p * P + Y) * R + q] = s;
-  }
+  for (int Y = 0; Y < P; ++Y) bufB[(p * P + Y) * R + q] = dot_row<T, P>(sB[1] + Y * P, in);
   __syncthreads();
   // S_x along x-lines (Z = p, Y = q): bufB -> bufA
 #pragma unroll
   for (int a = 0; a < P; ++a) in[a] = bufB[(p * P + q) * R + a];
 #pragma unroll 2
-  for (int X = 0; X < P; ++X) {
-    T s = sS[0][X * P] * in[0];
-#pragma unroll
-    for (int a = 1; a < P; ++a) s = fma(sS[0][X * P + a], in[a], s);
-    bufA[(p * P + q) * R + X] = s;
-  }
+  for (int X = 0; X < P; ++X) bufA[(p * P + q) * R + X] = dot_row<T, P>(sB[0] + X * P, in);
   __syncthreads();
   // x_P += the correction, cell by cell like the gather
   {
