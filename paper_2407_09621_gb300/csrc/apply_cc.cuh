@@ -136,13 +136,36 @@ __device__ __forceinline__ void contract_d(TC (&out)[N], const CcConst<TC, N>& P
   contract<TC, N, S>(out, mass ? P.M[d] : P.G[d], in);
 }
 
+// Shared-memory row helpers of the vector layout (rows of N floats, 16-byte aligned)
+template <int N>
+__device__ __forceinline__ void lds_row(float (&v)[N], const float* p) {
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k) {
+    const float4 t = reinterpret_cast<const float4*>(p)[k];
+    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void sts_row(float* p, const float (&v)[N]) {
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k)
+    reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+
 template <typename TS, typename TC, int N, int V, bool RES>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
 apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restrict__ b,
                 const __grid_constant__ CcConst<TC, N> P, int nx, int ny, int nz, long long c_begin, long long c_end) {
   constexpr int CPB = cc_cells_per_block<N, V>();
   constexpr int N2 = N * N, N3 = N * N * N;
-  constexpr int R = cc_pitch<TC, N>(), B = N * N * R;  // row pitch and size of a shared cell tensor
+  // Layout of a shared cell tensor: element (l, j, i) at l * PL + j * RP + i. FP32 arithmetic with
+  // n = 4, 8, 16 keeps rows unpadded and 16-byte aligned (x-lines move as float4) and pads each
+  // plane by n instead (PL = n(n + 1)), which keeps the y- and z-line phases free of bank
+  // conflicts; otherwise rows are padded to cc_pitch.
+  constexpr bool VX = sizeof(TC) == 4 && (N == 4 || N == 8 || N == 16);
+  constexpr bool VG = VX && sizeof(TS) == 4;  // the global x-rows move as float4 as well
+  constexpr int RP = VX ? N : cc_pitch<TC, N>(), PL = VX ? N * (N + 1) : N * RP;
+  constexpr int B = N * PL;  // size of a shared cell tensor
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
@@ -151,6 +174,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   TC* sX = base + (CPB + cs) * B;           // w_x, later M_y M_z w
   TC* sY = base + (2 * CPB + cs) * B;       // w_y
   TC* sZ = cc_buffers<N>() == 4 ? base + (3 * CPB + cs) * B : sU;  // M_z w
+  auto ix = [](int l, int j, int i) { return l * PL + j * RP + i; };
 
   const long long cell = c_begin + (long long)blockIdx.x * CPB + cs;  // cells [c_begin, c_end) of the mesh
   const bool valid = cell < c_end;
@@ -160,26 +184,49 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   const TS* xc = x + (valid ? cell : 0) * N3;
   const long long sy = (long long)nx * N3, sz = (long long)nx * ny * N3;
 
-  // ---- gather u (coalesced)
+  // ---- gather u (coalesced: by columns of the cell, or by x-rows of float4)
+  if constexpr (VG) {
+    TC r[N];
+    if (valid) {
 #pragma unroll
-  for (int l = 0; l < N; ++l) sU[(l * N + p) * R + q] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
+      for (int k = 0; k < N / 4; ++k) {
+        const float4 v4 = __ldg(reinterpret_cast<const float4*>(xc + p * N2 + q * N) + k);
+        r[4 * k] = v4.x; r[4 * k + 1] = v4.y; r[4 * k + 2] = v4.z; r[4 * k + 3] = v4.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) r[i] = TC(0);
+    }
+    sts_row<N>(sU + ix(p, q, 0), r);
+  } else {
+#pragma unroll
+    for (int l = 0; l < N; ++l) sU[ix(l, p, q)] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
+  }
   __syncthreads();
 
   // ---- (A) x-line (l=p, j=q) and y-line (l=p, i=q)
   {
     TC u[N], w[N];
+    if constexpr (VX) {
+      lds_row<N>(u, sU + ix(p, q, 0));
+    } else {
 #pragma unroll
-    for (int m = 0; m < N; ++m) u[m] = sU[(p * N + q) * R + m];
+      for (int m = 0; m < N; ++m) u[m] = sU[ix(p, q, m)];
+    }
     contract_d<TC, N>(w, P, false, 0, u);
     if (valid) {
       const TS* lo = cx > 0 ? xc - N3 + p * N2 + q * N : nullptr;
       const TS* hi = cx < nx - 1 ? xc + N3 + p * N2 + q * N : nullptr;
       add_faces<TS, TC, N>(w, u, lo, hi, 1, P, 0);
     }
+    if constexpr (VX) {
+      sts_row<N>(sX + ix(p, q, 0), w);
+    } else {
 #pragma unroll
-    for (int i = 0; i < N; ++i) sX[(p * N + q) * R + i] = w[i];
+      for (int i = 0; i < N; ++i) sX[ix(p, q, i)] = w[i];
+    }
 #pragma unroll
-    for (int m = 0; m < N; ++m) u[m] = sU[(p * N + m) * R + q];
+    for (int m = 0; m < N; ++m) u[m] = sU[ix(p, m, q)];
     contract_d<TC, N>(w, P, false, 1, u);
     if (valid) {
       const TS* lo = cy > 0 ? xc - sy + p * N2 + q : nullptr;
@@ -187,7 +234,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       add_faces<TS, TC, N>(w, u, lo, hi, N, P, 1);
     }
 #pragma unroll
-    for (int j = 0; j < N; ++j) sY[(p * N + j) * R + q] = w[j];
+    for (int j = 0; j < N; ++j) sY[ix(p, j, q)] = w[j];
   }
   __syncthreads();
 
@@ -195,7 +242,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   {
     TC u[N], w[N], v[N];
 #pragma unroll
-    for (int m = 0; m < N; ++m) u[m] = sU[(m * N + p) * R + q];
+    for (int m = 0; m < N; ++m) u[m] = sU[ix(m, p, q)];
     contract_d<TC, N>(w, P, false, 2, u);
     if (valid) {
       const TS* lo = cz > 0 ? xc - sz + t : nullptr;
@@ -203,10 +250,10 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       add_faces<TS, TC, N>(w, u, lo, hi, N2, P, 2);
     }
 #pragma unroll
-    for (int l = 0; l < N; ++l) w[l] += sX[(l * N + p) * R + q] + sY[(l * N + p) * R + q];
+    for (int l = 0; l < N; ++l) w[l] += sX[ix(l, p, q)] + sY[ix(l, p, q)];
     contract_d<TC, N>(v, P, true, 2, w);
 #pragma unroll
-    for (int l = 0; l < N; ++l) sZ[(l * N + p) * R + q] = v[l];
+    for (int l = 0; l < N; ++l) sZ[ix(l, p, q)] = v[l];
   }
   __syncthreads();
 
@@ -214,21 +261,37 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   {
     TC w[N], v[N];
 #pragma unroll
-    for (int m = 0; m < N; ++m) w[m] = sZ[(p * N + m) * R + q];
+    for (int m = 0; m < N; ++m) w[m] = sZ[ix(p, m, q)];
     contract_d<TC, N>(v, P, true, 1, w);
 #pragma unroll
-    for (int j = 0; j < N; ++j) sX[(p * N + j) * R + q] = v[j];
+    for (int j = 0; j < N; ++j) sX[ix(p, j, q)] = v[j];
   }
   __syncthreads();
 
   // ---- (D) x-line (l=p, j=q): M_x and scatter (y = A x, or y = b - A x when b is given)
   if (valid) {
     TC w[N], v[N];
+    if constexpr (VX) {
+      lds_row<N>(w, sX + ix(p, q, 0));
+    } else {
 #pragma unroll
-    for (int m = 0; m < N; ++m) w[m] = sX[(p * N + q) * R + m];
+      for (int m = 0; m < N; ++m) w[m] = sX[ix(p, q, m)];
+    }
     contract_d<TC, N>(v, P, true, 0, w);
     TS* yc = y + cell * N3 + p * N2 + q * N;
-    if constexpr (RES) {
+    if constexpr (VG) {
+      if constexpr (RES) {
+#pragma unroll
+        for (int k = 0; k < N / 4; ++k) {
+          const float4 b4 = __ldg(reinterpret_cast<const float4*>(b + cell * N3 + p * N2 + q * N) + k);
+          v[4 * k] = b4.x - v[4 * k]; v[4 * k + 1] = b4.y - v[4 * k + 1];
+          v[4 * k + 2] = b4.z - v[4 * k + 2]; v[4 * k + 3] = b4.w - v[4 * k + 3];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < N / 4; ++k)
+        reinterpret_cast<float4*>(yc)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else if constexpr (RES) {
       const TS* bc = b + cell * N3 + p * N2 + q * N;
 #pragma unroll
       for (int i = 0; i < N; ++i) store_as<TS, TC>(yc + i, load_as<TS, TC>(bc + i) - v[i]);
