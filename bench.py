@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
     p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
     p.add_argument("--no-tune", action="store_true", help="keep the default apply tile shape (no autotuner)")
+    p.add_argument("--vcycle-only", action="store_true",
+                   help="print only the time of one V-cycle (--k, --cells, --prec, --smoother) and exit")
+    p.add_argument("--smoother", default="chebyshev", choices=["chebyshev", "vertex_patch"])
     p.add_argument("--sweep-only", action="store_true",
                    help="print only the apply throughput for degrees 1..15 (FP64 and FP32) and exit")
     p.add_argument("--solve-only", action="store_true",
@@ -290,6 +293,41 @@ def degree_sweep(stream, precs=("fp64", "fp32"), degrees=range(1, 16), target_do
     return out
 
 
+def vcycle_bench(k, nc, prec, smoother, steps, warmup):
+    """One V-cycle (Algorithm 2) on nc^3 cells: the hierarchy of tp_mg_create in `prec` with the given
+    smoother, x = 0 and a uniform random b on the finest level; CUDA events around `steps` V-cycles
+    after `warmup` untimed ones."""
+    import torch
+    from paper_2407_09621_gb300 import _lib
+    from tp_synth import uniform_vector
+    P = {"fp64": _lib.TP_FP64, "fp32": _lib.TP_FP32, "fp16": _lib.TP_FP16, "bf16": _lib.TP_BF16}[prec]
+    DT = {"fp64": torch.float64, "fp32": torch.float32, "fp16": torch.float16, "bf16": torch.bfloat16}[prec]
+    sm = _lib.TP_SMOOTHER_VERTEX_PATCH if smoother == "vertex_patch" else _lib.TP_SMOOTHER_CHEBYSHEV
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    mg = _lib.tp_mg_create(op, precision=P, smoother=sm)
+    info = _lib.tp_mg_get_info(mg)
+    n = info["ndofs"][-1]
+    x = torch.zeros(n, dtype=DT, device="cuda")
+    b = torch.from_numpy(uniform_vector(n, seed=0)).to("cuda", DT)
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        _lib.tp_vcycle(mg, x.data_ptr(), b.data_ptr(), s.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        _lib.tp_vcycle(mg, x.data_ptr(), b.data_ptr(), s.cuda_stream)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    _lib.tp_mg_destroy(mg)
+    _lib.tp_op_destroy(op)
+    _lib.tp_mesh_destroy(mesh)
+    return {"k": k, "cells": f"{nc}^3", "dofs": n, "precision": prec, "smoother": smoother,
+            "levels": info["levels"], "ms_per_vcycle": ms}
+
+
 def solve_bench(k, nc, rtol=1e-10, half=True):
     """Sec. 7.2 Poisson solve: FP64 FGMRES(30) with a FP32 (mixed) or FP64 V-cycle preconditioner.
 
@@ -387,6 +425,10 @@ def run_ours(args):
     kdeg = args.k or K_DEG
     if args.solve_only:
         print(json.dumps({"solve_only": True, **solve_bench(kdeg, nc)}), flush=True)
+        return
+    if args.vcycle_only:
+        print(json.dumps({"vcycle_only": True, **vcycle_bench(kdeg, nc, args.prec, args.smoother, args.steps,
+                                                               args.warmup)}), flush=True)
         return
     if args.sweep_only:
         print(json.dumps({"sweep_only": True, "degree_sweep": degree_sweep(torch.cuda.current_stream())}),

@@ -39,7 +39,7 @@ typedef enum {
   TP_ERR_NONFINITE = 4,     /* a NaN/Inf was detected where the call checks for it */
   TP_ERR_NOT_CONVERGED = 5, /* an iterative solve stopped without reaching its tolerance */
   TP_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
-  TP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+  TP_ERR_UNSUPPORTED = 7    /* valid request the library does not implement */
 } tp_status;
 
 typedef enum { TP_FP64 = 0, TP_FP32 = 1, TP_FP16 = 2, TP_BF16 = 3 } tp_precision;
