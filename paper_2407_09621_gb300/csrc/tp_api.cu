@@ -231,13 +231,15 @@ using namespace tp;
 
 namespace {
 
-// Copy/compute pipeline of tp_apply_host: the cells are cut into kChunks ranges of whole z-slabs;
-// chunk i is copied in on `in`, applied on `comp` once chunks i-1..i+1 (its face neighbours) are
-// resident, and copied out on `out`, so the three overlap (H2D and D2H use separate copy engines).
-constexpr int kChunks = 8;
+// Copy/compute pipeline of tp_apply_host: the cells are cut into min(16, nz) ranges of whole
+// z-slabs (meshes with at least kMinChunks z-layers); chunk i is copied in on `in`, applied on
+// `comp` once chunks i-1..i+1 (its face neighbours) are resident, and copied out on `out`, so the
+// three overlap (H2D and D2H use separate copy engines). More chunks shorten the unoverlapped
+// first copy-in and last copy-out.
+constexpr int kMinChunks = 8, kMaxChunks = 16;
 struct HostPipe {
   cudaStream_t in = nullptr, comp = nullptr, out = nullptr;
-  cudaEvent_t start = nullptr, done = nullptr, loaded[kChunks] = {}, applied[kChunks] = {};
+  cudaEvent_t start = nullptr, done = nullptr, loaded[kMaxChunks] = {}, applied[kMaxChunks] = {};
 };
 
 void destroy_pipe(HostPipe* p) {
@@ -246,7 +248,7 @@ void destroy_pipe(HostPipe* p) {
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : {p->start, p->done})
     if (e) cudaEventDestroy(e);
-  for (int i = 0; i < kChunks; ++i) {
+  for (int i = 0; i < kMaxChunks; ++i) {
     if (p->loaded[i]) cudaEventDestroy(p->loaded[i]);
     if (p->applied[i]) cudaEventDestroy(p->applied[i]);
   }
@@ -261,7 +263,7 @@ tp_status make_pipe(HostPipe** out) {
     if (st == TP_OK) st = cuda_status(cudaStreamCreateWithFlags(s, cudaStreamNonBlocking), "tp_apply_host streams");
   for (cudaEvent_t* e : {&p->start, &p->done})
     if (st == TP_OK) st = cuda_status(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "tp_apply_host events");
-  for (int i = 0; i < kChunks && st == TP_OK; ++i) {
+  for (int i = 0; i < kMaxChunks && st == TP_OK; ++i) {
     st = cuda_status(cudaEventCreateWithFlags(&p->loaded[i], cudaEventDisableTiming), "tp_apply_host events");
     if (st == TP_OK)
       st = cuda_status(cudaEventCreateWithFlags(&p->applied[i], cudaEventDisableTiming), "tp_apply_host events");
@@ -287,7 +289,8 @@ tp_status apply_host_pipelined(tp_op_s* op, void* y_host, const void* x_host, cu
   const long long slab = (long long)op->mesh.nx * op->mesh.ny;
   const int nz = op->mesh.nz;
   const size_t cell_bytes = (size_t)(op->ndofs / op->ncells) * elem_bytes(op->prec);
-  auto z_at = [&](int i) { return (long long)nz * i / kChunks; };  // chunk i = slabs [z_at(i), z_at(i+1))
+  const int chunks = nz < kMaxChunks ? nz : kMaxChunks;
+  auto z_at = [&](int i) { return (long long)nz * i / chunks; };  // chunk i = slabs [z_at(i), z_at(i+1))
   auto launch = [&](long long c0, long long c1, cudaStream_t st) {
     return op->opts.kernel == TP_KERNEL_TENSOR ? launch_apply_dmma_range(op, op->hy, op->hx, c0, c1, st)
                                                : launch_apply_cc_range(op, op->hy, op->hx, c0, c1, st, nullptr);
@@ -306,9 +309,9 @@ tp_status apply_host_pipelined(tp_op_s* op, void* y_host, const void* x_host, cu
     return r;
   };
   if (st == TP_OK) st = copy_in(0);
-  for (int i = 0; i < kChunks && st == TP_OK; ++i) {
-    if (i + 1 < kChunks) st = copy_in(i + 1);
-    const int need = i + 1 < kChunks ? i + 1 : i;  // the chunk above must be resident (face neighbours)
+  for (int i = 0; i < chunks && st == TP_OK; ++i) {
+    if (i + 1 < chunks) st = copy_in(i + 1);
+    const int need = i + 1 < chunks ? i + 1 : i;  // the chunk above must be resident (face neighbours)
     if (st == TP_OK) st = cuda_status(cudaStreamWaitEvent(P.comp, P.loaded[need], 0), "tp_apply_host");
     if (st == TP_OK) st = cuda_status(launch(z_at(i) * slab, z_at(i + 1) * slab, P.comp), "tp_apply_host launch");
     if (st == TP_OK) st = cuda_status(cudaEventRecord(P.applied[i], P.comp), "tp_apply_host");
@@ -522,7 +525,7 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
   }
   cudaStream_t s = (cudaStream_t)stream;
   const bool ranged = op->opts.kernel != TP_KERNEL_TENSOR || op->prec == TP_FP64;
-  if (ranged && op->mesh.nz >= kChunks) return apply_host_pipelined(op, y_host, x_host, s);
+  if (ranged && op->mesh.nz >= kMinChunks) return apply_host_pipelined(op, y_host, x_host, s);
   tp_status st = cuda_status(cudaMemcpyAsync(op->hx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host H2D");
   if (st == TP_OK) st = cuda_status(launch_apply(op, op->hy, op->hx, s), "tp_apply_host launch");
   if (st == TP_OK) st = cuda_status(cudaMemcpyAsync(y_host, op->hy, bytes, cudaMemcpyDeviceToHost, s), "tp_apply_host D2H");
