@@ -312,6 +312,34 @@ def test_vertex_patch_smoother_matches_oracle(prec, k, dims):
         g.close()
 
 
+@pytest.mark.parametrize("prec,k,kernel", [("fp64", 2, 1), ("fp32", 3, 1), ("fp32", 3, 2)])
+def test_vertex_patch_smoother_on_anisotropic_box(prec, k, kernel):
+    """Cells of different widths per direction (each direction's patch eigenbases from its own h and
+    penalty), on CUDA-core or tensor-core (mma.sync, FP32 vectors) level operators."""
+    from oracle.schwarz import VertexPatchSmoother
+    from oracle.sipg import assemble
+    from paper_2407_09621_gb300 import _lib
+    dims, lengths = (4, 6, 2), (0.7, 1.3, 0.45)
+    mesh = _lib.tp_mesh_create(*dims, *lengths)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    # the tensor-core level operator with FP32 vectors runs with the error correction of Algorithm 1
+    mg = _lib.tp_mg_create(op, coarse_cells=1, precision=PREC[prec], kernel=kernel, ec=int(kernel == 2), smoother=VP)
+    try:
+        info = _lib.tp_mg_get_info(mg)
+        fl = info["levels"] - 1
+        n = info["ndofs"][fl]
+        b, x0 = uniform_vector(n, seed=27), uniform_vector(n, seed=28)
+        x = torch.from_numpy(x0).to("cuda", DT[prec])
+        _lib.tp_mg_smooth(mg, fl, x.data_ptr(), torch.from_numpy(b).to("cuda", DT[prec]).data_ptr())
+        torch.cuda.synchronize()
+        ref = VertexPatchSmoother(assemble(Mesh(*dims, *lengths), k), k, dims).smooth(x0, b)
+        assert rel_l2(x.double().cpu().numpy(), ref) < (1e-12 if prec == "fp64" else 5e-5 if kernel == 1 else 2e-4)
+    finally:
+        _lib.tp_mg_destroy(mg)
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("k", [1, 4, 5, 7])
 def test_vertex_patch_single_patch_level_solves_exactly(prec, k):
