@@ -16,8 +16,8 @@
 // thread block per patch adds its correction x_P += A_P^{-1} r_P without atomics. The sweep
 // over colours, with the residual r = b - A x formed before each colour, is in mg.cu.
 //
-// Work layout: P^2 threads per patch; in every phase a thread owns one line of the patch tensor
-// along the contracted direction (rows padded to P + 1 against bank conflicts). Phases: S_x^T,
+// Work layout: P^2 / 2 threads per patch; in every phase a thread owns two lines of the patch
+// tensor along the contracted direction (rows padded to P + 1 against bank conflicts). Phases: S_x^T,
 // S_y^T, then along z S_z^T, the scaling and S_z, then S_y and S_x; the patch tensor is read from
 // r and added to x cell by cell, so that a warp's accesses are contiguous.
 #include <cuda_runtime.h>
@@ -49,20 +49,24 @@ template <typename T, int P> struct RowVec { using V = float2; };
 template <int P> struct RowVec<float, P> { using V = typename std::conditional<P % 4 == 0, float4, float2>::type; };
 template <int P> struct RowVec<double, P> { using V = double2; };
 
+// Two dot products of one basis row with two lines: each wide load of the row serves both.
 template <typename T, int P>
-__device__ __forceinline__ T dot_row(const T* __restrict__ row, const T (&in)[P]) {
+__device__ __forceinline__ void dot_row2(const T* __restrict__ row, const T (&a)[P], const T (&b)[P], T& sa, T& sb) {
   using V = typename RowVec<T, P>::V;
   constexpr int W = sizeof(V) / sizeof(T);
   const V* rv = reinterpret_cast<const V*>(row);
-  T s = T(0);
+  sa = T(0);
+  sb = T(0);
 #pragma unroll
   for (int m = 0; m < P / W; ++m) {
     const V c = rv[m];
     const T* cc = reinterpret_cast<const T*>(&c);
 #pragma unroll
-    for (int w = 0; w < W; ++w) s = fma(cc[w], in[m * W + w], s);
+    for (int w = 0; w < W; ++w) {
+      sa = fma(cc[w], a[m * W + w], sa);
+      sb = fma(cc[w], b[m * W + w], sb);
+    }
   }
-  return s;
 }
 
 // dynamic shared memory of the patch kernel: two padded patch tensors, six P x P bases (S^T and S
@@ -72,18 +76,20 @@ constexpr size_t vp_smem_bytes() {
   return sizeof(T) * (2 * (2 * N) * (2 * N) * (2 * N + 1) + 6 * (2 * N) * (2 * N) + 3 * (2 * N));
 }
 
+// P^2 / 2 threads per patch; in every phase a thread owns two lines of the contracted direction,
+// lines p0 and p0 + P/2 of the outer index, so that each basis row it loads serves two lines.
 template <typename T, int N>
-__global__ void __launch_bounds__(4 * N * N)
+__global__ void __launch_bounds__(2 * N * N)
 vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
                 VPDims D) {
-  constexpr int P = 2 * N, R = P + 1, N3 = N * N * N;
+  constexpr int P = 2 * N, R = P + 1, N3 = N * N * N, H = P / 2, NT = P * H;
   extern __shared__ __align__(16) unsigned char vp_smem[];
   T* bufA = reinterpret_cast<T*>(vp_smem);
   T* bufB = bufA + P * P * R;
   T (*sF)[P * P] = reinterpret_cast<T (*)[P * P]>(bufB + P * P * R);  // sF[d][a * P + m] = S_d[m][a]
   T (*sB)[P * P] = sF + 3;                                               // sB[d][X * P + a] = S_d[X][a]
   T (*sL)[P] = reinterpret_cast<T (*)[P]>(bufB + P * P * R + 6 * P * P);
-  const int tid = threadIdx.x, p = tid / P, q = tid % P;
+  const int tid = threadIdx.x, p0 = tid / P, p1 = p0 + H, q = tid % P;
   const int vx = D.first[0] + 2 * (int)blockIdx.x, vy = D.first[1] + 2 * (int)blockIdx.y;
   const int vz = D.first[2] + 2 * (int)blockIdx.z;
   {
@@ -91,9 +97,13 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
                       (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const T v = Stab[(size_t)(d * 4 + t[d]) * kMaxP * kMaxP + p * kMaxP + q];  // S_d[p][q]
-      sB[d][p * P + q] = v;
-      sF[d][q * P + p] = v;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * NT, X = e / P, a = e % P;
+        const T v = Stab[(size_t)(d * 4 + t[d]) * kMaxP * kMaxP + X * kMaxP + a];  // S_d[X][a]
+        sB[d][X * P + a] = v;
+        sF[d][a * P + X] = v;
+      }
       if (tid < P) sL[d][tid] = Ltab[(d * 4 + t[d]) * kMaxP + tid];
     }
   }
@@ -111,60 +121,104 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
     return (Z * P + Y) * R + X;
   };
   {
-    T v[P];  // all P loads in flight before the shared stores
+    T v[2 * P];  // all loads in flight before the shared stores
 #pragma unroll
-    for (int j = 0; j < P; ++j) v[j] = __ldg(r + gaddr(tid + j * P * P));
+    for (int j = 0; j < 2 * P; ++j) v[j] = __ldg(r + gaddr(tid + j * NT));
 #pragma unroll
-    for (int j = 0; j < P; ++j) bufA[saddr(tid + j * P * P)] = v[j];
+    for (int j = 0; j < 2 * P; ++j) bufA[saddr(tid + j * NT)] = v[j];
   }
   __syncthreads();
-  // One line of the patch tensor in registers, in[m], contracted per output node o with a basis
-  // row: sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of
-  // sB); each output goes straight to shared memory.
-  T in[P];
+  // Two lines of the patch tensor in registers, contracted per output node o with a basis row:
+  // sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of sB);
+  // each output goes straight to shared memory.
+  T i0[P], i1[P], s0, s1;
   // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
 #pragma unroll
-  for (int m = 0; m < P; ++m) in[m] = bufA[(p * P + q) * R + m];
+  for (int m = 0; m < P; ++m) {
+    i0[m] = bufA[(p0 * P + q) * R + m];
+    i1[m] = bufA[(p1 * P + q) * R + m];
+  }
 #pragma unroll 2
-  for (int a = 0; a < P; ++a) bufB[(p * P + q) * R + a] = dot_row<T, P>(sF[0] + a * P, in);
+  for (int a = 0; a < P; ++a) {
+    dot_row2<T, P>(sF[0] + a * P, i0, i1, s0, s1);
+    bufB[(p0 * P + q) * R + a] = s0;
+    bufB[(p1 * P + q) * R + a] = s1;
+  }
   __syncthreads();
   // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
 #pragma unroll
-  for (int m = 0; m < P; ++m) in[m] = bufB[(p * P + m) * R + q];
+  for (int m = 0; m < P; ++m) {
+    i0[m] = bufB[(p0 * P + m) * R + q];
+    i1[m] = bufB[(p1 * P + m) * R + q];
+  }
 #pragma unroll 2
-  for (int b = 0; b < P; ++b) bufA[(p * P + b) * R + q] = dot_row<T, P>(sF[1] + b * P, in);
+  for (int b = 0; b < P; ++b) {
+    dot_row2<T, P>(sF[1] + b * P, i0, i1, s0, s1);
+    bufA[(p0 * P + b) * R + q] = s0;
+    bufA[(p1 * P + b) * R + q] = s1;
+  }
   __syncthreads();
   // z-lines (b = p, a = q): S_z^T and the eigenvalue scaling into bufB, then S_z back into bufA.
-  // A thread reads and writes only its own z-line here, so no barrier is needed in between.
+  // A thread reads and writes only its own z-lines here, so no barrier is needed in between.
 #pragma unroll
-  for (int m = 0; m < P; ++m) in[m] = bufA[(m * P + p) * R + q];
-  const T lxy = sL[0][q] + sL[1][p];
+  for (int m = 0; m < P; ++m) {
+    i0[m] = bufA[(m * P + p0) * R + q];
+    i1[m] = bufA[(m * P + p1) * R + q];
+  }
+  {
+    const T l0 = sL[0][q] + sL[1][p0], l1 = sL[0][q] + sL[1][p1];
 #pragma unroll 2
-  for (int c = 0; c < P; ++c) bufB[(c * P + p) * R + q] = dot_row<T, P>(sF[2] + c * P, in) / (lxy + sL[2][c]);
+    for (int c = 0; c < P; ++c) {
+      dot_row2<T, P>(sF[2] + c * P, i0, i1, s0, s1);
+      bufB[(c * P + p0) * R + q] = s0 / (l0 + sL[2][c]);
+      bufB[(c * P + p1) * R + q] = s1 / (l1 + sL[2][c]);
+    }
+  }
 #pragma unroll
-  for (int c = 0; c < P; ++c) in[c] = bufB[(c * P + p) * R + q];
+  for (int c = 0; c < P; ++c) {
+    i0[c] = bufB[(c * P + p0) * R + q];
+    i1[c] = bufB[(c * P + p1) * R + q];
+  }
 #pragma unroll 2
-  for (int Z = 0; Z < P; ++Z) bufA[(Z * P + p) * R + q] = dot_row<T, P>(sB[2] + Z * P, in);
+  for (int Z = 0; Z < P; ++Z) {
+    dot_row2<T, P>(sB[2] + Z * P, i0, i1, s0, s1);
+    bufA[(Z * P + p0) * R + q] = s0;
+    bufA[(Z * P + p1) * R + q] = s1;
+  }
   __syncthreads();
   // S_y along y-lines (Z = p, a = q): bufA -> bufB
 #pragma unroll
-  for (int b = 0; b < P; ++b) in[b] = bufA[(p * P + b) * R + q];
+  for (int b = 0; b < P; ++b) {
+    i0[b] = bufA[(p0 * P + b) * R + q];
+    i1[b] = bufA[(p1 * P + b) * R + q];
+  }
 #pragma unroll 2
-  for (int Y = 0; Y < P; ++Y) bufB[(p * P + Y) * R + q] = dot_row<T, P>(sB[1] + Y * P, in);
+  for (int Y = 0; Y < P; ++Y) {
+    dot_row2<T, P>(sB[1] + Y * P, i0, i1, s0, s1);
+    bufB[(p0 * P + Y) * R + q] = s0;
+    bufB[(p1 * P + Y) * R + q] = s1;
+  }
   __syncthreads();
   // S_x along x-lines (Z = p, Y = q): bufB -> bufA
 #pragma unroll
-  for (int a = 0; a < P; ++a) in[a] = bufB[(p * P + q) * R + a];
+  for (int a = 0; a < P; ++a) {
+    i0[a] = bufB[(p0 * P + q) * R + a];
+    i1[a] = bufB[(p1 * P + q) * R + a];
+  }
 #pragma unroll 2
-  for (int X = 0; X < P; ++X) bufA[(p * P + q) * R + X] = dot_row<T, P>(sB[0] + X * P, in);
+  for (int X = 0; X < P; ++X) {
+    dot_row2<T, P>(sB[0] + X * P, i0, i1, s0, s1);
+    bufA[(p0 * P + q) * R + X] = s0;
+    bufA[(p1 * P + q) * R + X] = s1;
+  }
   __syncthreads();
   // x_P += the correction, cell by cell like the gather
   {
-    T v[P];
+    T v[2 * P];
 #pragma unroll
-    for (int j = 0; j < P; ++j) v[j] = x[gaddr(tid + j * P * P)];
+    for (int j = 0; j < 2 * P; ++j) v[j] = x[gaddr(tid + j * NT)];
 #pragma unroll
-    for (int j = 0; j < P; ++j) x[gaddr(tid + j * P * P)] = v[j] + bufA[saddr(tid + j * P * P)];
+    for (int j = 0; j < 2 * P; ++j) x[gaddr(tid + j * NT)] = v[j] + bufA[saddr(tid + j * NT)];
   }
 }
 
@@ -176,7 +230,7 @@ cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, c
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
-  vp_patch_kernel<T, N><<<grid, 4 * N * N, vp_smem_bytes<T, N>(), s>>>(
+  vp_patch_kernel<T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
       static_cast<T*>(x), static_cast<const T*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D);
   return cudaGetLastError();
 }
