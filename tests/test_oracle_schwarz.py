@@ -55,6 +55,14 @@ def test_single_patch_mesh_is_solved_exactly(k):
     assert _rel(x, spla.spsolve(A.tocsc(), b)) < 1e-12
 
 
+def test_single_patch_exact_on_anisotropic_box_with_paper_penalty():
+    dims, lengths, k = (2, 2, 2), (0.7, 1.3, 0.45), 2
+    A = assemble(Mesh(*dims, *lengths), k, "paper")
+    b = np.random.default_rng(4).uniform(-1, 1, A.shape[0])
+    x = VertexPatchSmoother(A, k, dims).smooth(np.random.default_rng(5).uniform(-1, 1, A.shape[0]), b)
+    assert _rel(x, spla.spsolve(A.tocsc(), b)) < 1e-12
+
+
 def test_patch_residual_vanishes_after_its_colour():
     # 3 x 3 x 3 cells: interior vertices 1, 2 per direction, so every colour holds one patch;
     # after that colour's update the residual is zero on the patch's DoFs
