@@ -22,6 +22,7 @@
 namespace tp {
 tp_status cuda_status(int err, const char* what);
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+cudaError_t launch_residual(const tp_op_s* op, void* r, const void* b, const void* x, cudaStream_t s);
 cudaError_t mg_vcycle(const tp_mg_s* mg, int l, void* x, const void* b, int x_zero, cudaStream_t s);
 int mg_finest_level(const tp_mg_s* mg);
 tp_precision mg_precision(const tp_mg_s* mg);
@@ -40,6 +41,7 @@ struct tp_solver_s {
   void* px = nullptr;  // preconditioner output
   double* partial = nullptr;
   double* dots = nullptr;
+  int* flag = nullptr;  // device word of the zero test of the initial guess
   std::vector<double> history;
   int reorth = 0;  // second Gram-Schmidt passes in the last solve
   // the preconditioner V-cycle (fixed input pb, output px) captured once as a CUDA graph
@@ -57,6 +59,7 @@ static void solver_free(tp_solver_s* s) {
   if (s->px) cudaFree(s->px);
   if (s->partial) cudaFree(s->partial);
   if (s->dots) cudaFree(s->dots);
+  if (s->flag) cudaFree(s->flag);
   if (s->vcycle_graph) cudaGraphExecDestroy(s->vcycle_graph);
 }
 
@@ -115,6 +118,7 @@ tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart) {
   }
   if (st == TP_OK) st = cuda_status(cudaMalloc(&s->partial, sizeof(double) * (kMaxMulti + 1) * dot_blocks(s->n)), "tp_fgmres_create: scratch");
   if (st == TP_OK) st = cuda_status(cudaMalloc(&s->dots, sizeof(double) * 3 * (restart + 2)), "tp_fgmres_create: scratch");
+  if (st == TP_OK) st = cuda_status(cudaMalloc(&s->flag, sizeof(int)), "tp_fgmres_create: scratch");
   if (st != TP_OK) {
     solver_free(s);
     delete s;
@@ -170,13 +174,39 @@ cudaError_t norm_to_host(Ctx& c, const double* w, double* out) {
   return e;
 }
 
-// out = b - A x
+// out = b - A x (one pass where the operator's kernel stores the residual form itself)
 cudaError_t residual64(Ctx& c, double* out, const double* b, const double* x) {
+  if (c.s->A->opts.kernel != TP_KERNEL_TENSOR) return launch_residual(c.s->A, out, b, x, c.st);
   cudaError_t e = launch_apply(c.s->A, c.s->w, x, c.st);
   const double coef[2] = {1.0, -1.0};
   const double* v[2] = {b, c.s->w};
   if (e == cudaSuccess) e = multi_axpy<double>(c.s->n, out, 0.0, v, coef, 2, c.st);
   return e;
+}
+
+// *flag = 1 if any entry of x differs from zero (NaN included); every writer writes the same value.
+__global__ void any_nonzero_kernel(const double* __restrict__ x, long long n, int* __restrict__ flag) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!(x[i] == 0.0)) {
+      *flag = 1;
+      return;
+    }
+}
+
+// r0 = b - A x0; a zero initial guess (the usual x0 = 0) gives r0 = b without an apply, exactly as
+// the apply would (A 0 = 0 and b - 0 = b in floating point).
+cudaError_t initial_residual(Ctx& c, double* out, const double* b, const double* x) {
+  cudaError_t e = cudaMemsetAsync(c.s->flag, 0, sizeof(int), c.st);
+  if (e == cudaSuccess) {
+    any_nonzero_kernel<<<stream_blocks(c.s->n), 256, 0, c.st>>>(x, c.s->n, c.s->flag);
+    e = cudaGetLastError();
+  }
+  int nz = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nz, c.s->flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.st);
+  if (e != cudaSuccess) return e;
+  if (nz) return residual64(c, out, b, x);
+  return cudaMemcpyAsync(out, b, sizeof(double) * c.s->n, cudaMemcpyDeviceToDevice, c.st);
 }
 
 }  // namespace
@@ -197,7 +227,7 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int its = 0, restarts = 0, converged = 0;
   double beta0 = 0.0, rel = 1.0;
-  cudaError_t e = residual64(c, s->V[0], b, x);
+  cudaError_t e = initial_residual(c, s->V[0], b, x);
   if (e == cudaSuccess) e = norm_to_host(c, s->V[0], &beta0);
   if (e != cudaSuccess) return cuda_status(e, "tp_fgmres_solve");
   if (!std::isfinite(beta0)) { set_error("tp_fgmres_solve: non-finite initial residual"); return TP_ERR_NONFINITE; }

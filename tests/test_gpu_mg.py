@@ -175,6 +175,37 @@ def test_fgmres_solution_matches_exact_discrete_solution(mg_prec, k, nc):
     assert abs(info["iterations"] - its) <= 2
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_fgmres_nonzero_initial_guess(kernel):
+    """x0 near the solution: the initial residual is b - A x0 (the zero test of x0 must see it),
+    on the CUDA-core FP64 operator (residual fused into the apply) and on the DMMA operator (apply,
+    then the difference)."""
+    from paper_2407_09621_gb300 import _lib
+    k, nc = 3, 16
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64, kernel=kernel)
+    mg = _lib.tp_mg_create(op, coarse_cells=2, precision=PREC["fp32"])
+    solver = _lib.tp_fgmres_create(op, mg, 30)
+    try:
+        f = rhs_sine(k, nc, nc, nc)
+        u = FastDiag(k, nc, nc, nc).solve(f)
+        b = torch.from_numpy(f).cuda()
+        x = torch.from_numpy(u + 1e-3 * uniform_vector(len(u), seed=31)).cuda()
+        st, info = _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), 1e-8, 100)
+        torch.cuda.synchronize()
+        assert info["converged"] == 1 and info["iterations"] >= 1
+        assert rel_l2(x.cpu().numpy(), u) < 1e-9
+        x0 = torch.zeros_like(b)  # and from zero, the same solution
+        st, info0 = _lib.tp_fgmres_solve(solver, x0.data_ptr(), b.data_ptr(), 1e-10, 100)
+        torch.cuda.synchronize()
+        assert info0["converged"] == 1 and rel_l2(x0.cpu().numpy(), u) < 1e-8
+    finally:
+        _lib.tp_solver_destroy(solver)
+        _lib.tp_mg_destroy(mg)
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
+
+
 def test_fgmres_without_preconditioner_reports_not_converged():
     from paper_2407_09621_gb300 import _lib
     mesh = _lib.tp_mesh_create(4, 4, 4)
