@@ -6,6 +6,14 @@ cube, 134,217,728 DoFs, x ~ U[-1, 1] (seed 0); one step = one tp_apply
 launch. Vectors are 1.07 GB each, far larger than the 129 MB L2, so no L2
 flush is needed between steps. Metric: GDoF/s (DoFs of all ranks / time).
 
+Output: one JSON line per secondary measurement ({"section": ...}: the 8^3
+latency case with the oracle's CSR SpMV on one and on all host cores, the
+per-precision apply sweep on ~33M DoFs with relative errors, the other FP64
+applies, the Sec. 7.2 Poisson solves, the 32-problem batch, the degree
+sweep), then the headline as the LAST line (compact: value, roofline,
+cpu_baseline, e2e, clocks, a summary of the solves). --out FILE also writes
+everything as one JSON document.
+
 --impl reference times the CPU oracle (oracle/sipg.py block apply) on a
 bounded slab sample of the same workload on the host cores.
 Multi-GPU (torchrun): every rank applies its own independent replica
@@ -15,14 +23,12 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
 import tempfile
 import time
 
-import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -52,6 +58,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
+    p.add_argument("--extras", default="latency,precision,fp64,solve,batch,sweep",
+                   help="comma-separated secondary sections to run (default: all)")
+    p.add_argument("--out", default=None, help="also write the headline and every section to this JSON file")
     p.add_argument("--kernel-only", action="store_true",
                    help="only the warm-up and timed applies (for profiler captures of a smaller case)")
     p.add_argument("--cells", type=int, default=None, help="cells per direction (default 128)")
@@ -134,6 +143,27 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def bench_lib():
+    """libtp_bench.so (include/tp_bench.h): the FMA-pipe peak probe, measurement support only."""
+    import ctypes
+    lib = ctypes.CDLL(os.path.join(ROOT, "paper_2407_09621_gb300", "libtp_bench.so"))
+    lib.tp_bench_fma_peak.restype = ctypes.c_int
+    lib.tp_bench_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.tp_bench_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+def fma_peak(precision, stream):
+    """Measured FMA-pipe rate (TFLOP/s) of precision 0 (FP64) or 1 (FP32) on the current GPU."""
+    import ctypes
+    lib = bench_lib()
+    out = ctypes.c_double()
+    st = lib.tp_bench_fma_peak(precision, ctypes.byref(out), ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise RuntimeError(f"tp_bench_fma_peak: {lib.tp_bench_last_error().decode()}")
+    return out.value
+
+
 # the device-code sources of each kernel whose ncu counters a profile summary records
 KERNEL_SOURCES = {
     "apply_cc": ["apply_cc.cu", "apply_cc.cuh", "apply_common.cuh"],
@@ -151,18 +181,19 @@ def kernel_sha256(kernel):
     return h.hexdigest()
 
 
-def profile_traffic(kernel, summary):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel's sources are unchanged since."""
-    path = os.path.join(ROOT, "profiles", summary)
-    if not os.path.exists(path):
+def profile_traffic(kernel, sidecar):
+    """DRAM bytes per full-size launch (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture,
+    scaled by the units processed) from the JSON sidecar of a profile summary, if the kernel's sources
+    are unchanged since the capture; None otherwise."""
+    path = os.path.join(ROOT, "profiles", sidecar)
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
-    text = open(path).read()
-    h = kernel_sha256(kernel)
-    m_h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    m_t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-    if not (m_h and m_t) or m_h.group(1) != h:
+    if rec.get("source_sha256") != kernel_sha256(kernel):
         return None
-    return float(m_t.group(1))
+    return rec.get("traffic_bytes_per_launch_full_size")
 
 
 def oracle_sample(seconds=10.0):
@@ -182,6 +213,40 @@ def oracle_sample(seconds=10.0):
     return {"value": reps * len(x) / t_total / 1e9, "unit": "GDoF/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle block apply (numpy/BLAS, FP64) on a {SLAB[0]}x{SLAB[1]}x{SLAB[2]}-cell slab, "
                       f"k={K_DEG}, {len(x)} DoFs, {reps} reps, {t_total:.1f} s"}
+
+
+def csr_baseline_8cubed(k=3, nc=8, seconds=1.5):
+    """CPU side of the 8^3-cell, k=3 latency case: y = A x with the oracle's assembled CSR matrix
+    (oracle/sipg.py assemble), SciPy on one core and the oracle's C/OpenMP SpMV on all host cores,
+    each repeated for ~`seconds`."""
+    from oracle.sipg import Mesh, assemble
+    from oracle.spmv import csr_arrays, csr_spmv_omp, omp_threads
+    from tp_synth import uniform_vector
+    A = assemble(Mesh(nc, nc, nc), k)
+    x = uniform_vector(A.shape[0], seed=0)
+    out = {"dofs": A.shape[0], "nnz": int(A.nnz)}
+
+    def timed(fn):
+        fn()
+        reps, t = 0, 0.0
+        while t < seconds:
+            t0 = time.perf_counter()
+            fn()
+            t += time.perf_counter() - t0
+            reps += 1
+        return t / reps
+
+    dt1 = timed(lambda: A @ x)
+    out["scipy_1core"] = {"us_per_apply": dt1 * 1e6, "gdofs": A.shape[0] / dt1 / 1e9, "cores": 1}
+    try:
+        arr = csr_arrays(A)
+        cores = len(os.sched_getaffinity(0))
+        dtn = timed(lambda: csr_spmv_omp(arr, x, threads=cores))
+        out["omp_all_cores"] = {"us_per_apply": dtn * 1e6, "gdofs": A.shape[0] / dtn / 1e9, "cores": cores,
+                                "omp_default_threads": omp_threads()}
+    except (OSError, RuntimeError) as e:
+        out["omp_all_cores"] = {"unavailable": str(e).splitlines()[0]}
+    return out
 
 
 def run_reference(args):
@@ -212,6 +277,7 @@ def run_reference(args):
     }), flush=True)
 
 
+
 def time_applies(op, y, x, steps, warmup, stream):
     import torch
     for _ in range(warmup):
@@ -227,40 +293,103 @@ def time_applies(op, y, x, steps, warmup, stream):
     return per, ev[0][0].elapsed_time(ev[-1][1])
 
 
-def secondary(stream):
-    """A few steps of the other apply configurations (same kernel family), reported beside the headline."""
+
+def latency_8cubed(stream, reps=200):
+    """Sec. 8 small case: FP64 apply, k=3, 8^3 cells (32,768 DoFs, 262 KB per vector, L2-resident);
+    every apply timed on its own with CUDA events (median) and `reps` back to back."""
+    import torch
+    from paper_2407_09621_gb300 import DGLaplace
+    from tp_synth import uniform_vector
+    op = DGLaplace(8, 8, 8, 3, "fp64")
+    x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda")
+    y = torch.empty_like(x)
+    per, total_ms = time_applies(op, y, x, reps, 10, stream)
+    out = {"workload": "FP64 apply, k=3, 8^3 cells (32,768 DoFs), x ~ U[-1,1] seed 0", "dofs": op.ndofs,
+           "us_per_apply_median": 1e3 * statistics.median(per),
+           "us_per_apply_back_to_back": 1e3 * total_ms / reps,
+           "gdofs_back_to_back": op.ndofs * reps / (total_ms * 1e-3) / 1e9, "tile_cells": op.info["tile_cells"]}
+    op.close()
+    return out
+
+
+def fp64_applies(stream, peak):
+    """The other FP64 applies of the 134M-DoF configuration: k=7 on 64^3 cells (DFMA), and both
+    degrees through the DMMA (mma.sync f64) kernel, the paper's FP64 tensor-core path."""
     import torch
     from paper_2407_09621_gb300 import DGLaplace, _lib
     from tp_synth import uniform_vector
     out = []
-    CC, TC = 1, 2
-    runs = [(7, 64, "fp64", CC, 0), (3, 128, "fp64", TC, 0), (7, 64, "fp64", TC, 0),
-            (3, 80, "fp32", CC, 0), (3, 80, "fp16", CC, 0), (3, 80, "bf16", CC, 0),
-            (7, 40, "fp32", CC, 0), (7, 40, "fp16", CC, 0),
-            (3, 80, "fp16", TC, 0), (3, 80, "fp16", TC, 1), (3, 80, "bf16", TC, 0),
-            (3, 128, "fp16", TC, 0), (3, 128, "fp16", TC, 1), (3, 128, "bf16", TC, 0),
-            (3, 80, "fp32", TC, 1), (2, 107, "fp16", TC, 0)]
-    paths = {0: "cuda_core", 1: "mma.sync f16/bf16", 2: "tcgen05 (TMA + TMEM)", 3: "mma.sync f64 (DMMA)"}
-    fp64_peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
-    for k, nc, prec, kern, ec in runs:
-        op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec, autotune=1)
-        x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
+    names = {0: "cuda_core_dfma", 3: "dmma_mma_sync_f64"}
+    for k, nc, kern in ((7, 64, _lib.TP_KERNEL_CUDA_CORE), (3, 128, _lib.TP_KERNEL_TENSOR),
+                        (7, 64, _lib.TP_KERNEL_TENSOR)):
+        op = DGLaplace(nc, nc, nc, k, "fp64", kernel=kern, autotune=1)
+        x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda")
         y = torch.empty_like(x)
         per, _ = time_applies(op, y, x, 10, 3, stream)
-        op.check()
         ms = statistics.mean(per)
-        gbs = 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6
-        row = {"k": k, "cells": f"{nc}^3", "precision": prec, "kernel": paths[op.info["tensor_path"]],
-               "ec": ec if prec != "bf16" or kern != TC else 1, "dofs": op.ndofs, "ms": ms,
-               "gdofs": op.ndofs / ms / 1e6, "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / PEAKS["hbm_gbs"],
-               "tile_cells": op.info["tile_cells"]}
-        if prec == "fp64":
-            tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
-            row.update({"fp64_tflops": tf, "fp64_frac_of_measured_dfma": tf / fp64_peak})
-        out.append(row)
+        tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
+        out.append({"k": k, "cells": nc, "kernel": names[op.info["tensor_path"]], "ms": ms,
+                    "gdofs": op.ndofs / ms / 1e6, "flops_per_dof": op.info["flops_per_dof"], "tflops": tf,
+                    "frac_of_dfma_peak": tf / peak})
         op.close()
         del x, y
     return out
+
+
+# Sec. 8 precision sweep: about 33M DoFs per degree
+SWEEP_MESHES = ((2, 107), (3, 80), (4, 64), (5, 54), (7, 40))
+
+
+def precision_sweep(stream):
+    """Apply throughput and per-apply relative l2 error (Sec. 5.2) for k in {2,3,4,5,7} on ~33M DoFs with
+    FP32, FP16 and BF16 vectors (FP32 accumulation), on the CUDA-core kernel and on every tensor-core
+    path the library builds for that degree and precision. x ~ U[-1,1] seed 0 in FP64, rounded to the
+    storage type; the error is taken against the FP64 apply of the FP64 x on the same GPU (the FP64
+    apply itself matches the CPU oracle to 1e-12 in the GPU tests), so input rounding is included."""
+    import torch
+    from paper_2407_09621_gb300 import DGLaplace, TPError, _lib
+    from tp_synth import uniform_vector
+    paths = {0: "cuda_core", 1: "mma.sync", 2: "tcgen05", 3: "dmma", 4: "tcgen05_sumfact"}
+    rows = []
+    for k, nc in SWEEP_MESHES:
+        op64 = DGLaplace(nc, nc, nc, k, "fp64")
+        x64 = torch.from_numpy(uniform_vector(op64.ndofs, seed=0)).to("cuda")
+        y64 = torch.empty_like(x64)
+        op64.apply(y64, x64, stream)
+        torch.cuda.synchronize()
+        ref_norm = float(torch.linalg.vector_norm(y64))
+        op64.close()
+        variants = [(p, _lib.TP_KERNEL_CUDA_CORE, 0) for p in ("fp32", "fp16", "bf16")]
+        variants += [(p, _lib.TP_KERNEL_TENSOR, ec) for p in ("fp16", "bf16") for ec in (0, 1)]
+        seen = set()
+        for prec, kern, ec in variants:
+            try:
+                op = DGLaplace(nc, nc, nc, k, prec, kernel=kern, ec=ec)
+            except TPError as e:
+                if e.status == _lib.TP_ERR_UNSUPPORTED:
+                    continue
+                raise
+            key = (prec, op.info["tensor_path"], op.info["kernel"], ec if prec != "bf16" else -1)
+            if key in seen:  # BF16 tensor paths always refine: ec = 0 and 1 are the same operator
+                op.close()
+                continue
+            seen.add(key)
+            x = x64.to(op.dtype)
+            y = torch.empty_like(x)
+            per, _ = time_applies(op, y, x, 10, 3, stream)
+            op.check()
+            err = float(torch.linalg.vector_norm(y.double() - y64)) / ref_norm
+            ms = statistics.mean(per)
+            gbs = 2 * op.info["elem_bytes"] * op.ndofs / ms / 1e6
+            rows.append({"k": k, "cells": nc, "dofs": op.ndofs, "precision": prec,
+                         "kernel": paths.get(op.info["tensor_path"], op.info["tensor_path"]),
+                         "ec": ec if prec != "bf16" or kern != _lib.TP_KERNEL_TENSOR else 1,
+                         "ms": round(ms, 5), "gdofs": round(op.ndofs / ms / 1e6, 2),
+                         "hbm_frac_of_measured": round(gbs / PEAKS["hbm_gbs"], 4), "rel_l2_err": err})
+            op.close()
+            del x, y
+        del x64, y64
+    return rows
 
 
 def degree_sweep(stream, precs=("fp64", "fp32"), degrees=range(1, 16), target_dofs=1 << 26):
@@ -268,10 +397,9 @@ def degree_sweep(stream, precs=("fp64", "fp32"), degrees=range(1, 16), target_do
     experiment of the paper's appendix): a cube mesh of about 2^26 DoFs per degree (vectors larger
     than L2), tile shape autotuned where n <= 8, 8 timed applies after 2 warm-ups."""
     import torch
-    from paper_2407_09621_gb300 import DGLaplace, _lib
+    from paper_2407_09621_gb300 import DGLaplace
     from tp_synth import uniform_vector
-    peaks = {p: _lib.tp_bench_fma_peak(_lib.TP_FP64 if p == "fp64" else _lib.TP_FP32, stream.cuda_stream)
-             for p in precs}
+    peaks = {p: fma_peak(0 if p == "fp64" else 1, stream) for p in precs}
     out = []
     for prec in precs:
         for k in degrees:
@@ -411,6 +539,22 @@ def batch_bench(count=32, streams=8):
                              "iterations_max": max(r["iterations"] for r in res_v)}}
 
 
+
+def solve_summary(solves):
+    """Compact per-problem view of solve_bench results for the headline line."""
+    out = {}
+    for s in solves or []:
+        best = s["best_mixed"]
+        fp64 = min(s["fp64_vcycle"]["seconds"], s["fp64_vertex_patch"]["seconds"])
+        out[f"k{s['k']}_{s['cells'].split('^')[0]}"] = {
+            "mixed_s": round(best["seconds"], 4), "mixed_run": best["run"],
+            "mixed_iters": s[best["run"]]["iterations"], "fp64_s": round(fp64, 4),
+            "speedup": round(best["speedup_vs_fastest_fp64"], 2),
+            "l2_mixed": s[best["run"]]["l2_error"], "l2_fp64": s["fp64_vcycle"]["l2_error"],
+            "l2_within_rule": bool(s[best["run"]]["l2_within_rule"])}
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local_rank = dist_env()
@@ -418,7 +562,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
-    from paper_2407_09621_gb300 import DGLaplace, _lib
+    from paper_2407_09621_gb300 import DGLaplace
     from tp_synth import uniform_vector
 
     nc = args.cells or NC
@@ -467,9 +611,9 @@ def run_ours(args):
     total_ms = max_over_ranks(total_ms, world, "cuda")
     value = job_throughput(ndofs, args.steps, world, total_ms * 1e-3)
 
-    # end to end through the public C ABI with host buffers (copies inside the timed region)
-    # per-call wall times; the reported figure uses their median (isolated host-side stalls of
-    # tens of ms, unrelated to the call, appear on the shared hosts), the mean is reported beside it
+    # end to end through the public C ABI with host buffers (copies inside the timed region);
+    # per-call wall times, the reported figure their median (isolated host-side stalls of tens of
+    # ms, unrelated to the call, appear on shared hosts), the mean reported beside it
     e2e_steps = max(3, min(args.steps, 10))
     op.apply_host(y_host, x_host)
     e2e_times = []
@@ -485,43 +629,60 @@ def run_ours(args):
     avg_launch_ms = statistics.mean(per)
     flops_launch = op.info["flops_per_dof"] * ndofs
     achieved = flops_launch / (avg_launch_ms * 1e-3) / 1e12
-    peak = _lib.tp_bench_fma_peak(_lib.TP_FP64, stream.cuda_stream)
-    traffic = profile_traffic("apply_cc", "apply_cc_fp64_k3_128cubed.md")
-
+    peak = fma_peak(0, stream)
+    traffic = profile_traffic("apply_cc", "apply_cc_fp64_k3_128cubed.json")
+    tile_cells = op.info["tile_cells"]
+    flops_per_dof = op.info["flops_per_dof"]
+    op.close()
+    del x, y
     if rank != 0:
         return
-    extra = None if args.no_extra else secondary(stream)
-    solves = None if args.no_extra else [solve_bench(3, 128), solve_bench(7, 64), solve_bench(3, 64),
-                                         solve_bench(7, 32)]
-    batch = None if args.no_extra else batch_bench()
-    sweep = None if args.no_extra else degree_sweep(stream)
+
+    sections = {}
+    wanted = [] if args.no_extra else [e for e in args.extras.split(",") if e]
+
+    def section(name, fn):
+        if name not in wanted:
+            return None
+        t0 = time.perf_counter()
+        res = fn()
+        sections[name] = res
+        print(json.dumps({"section": name, "seconds": round(time.perf_counter() - t0, 1), "result": res}),
+              flush=True)
+        return res
+
+    section("latency", lambda: {"gpu": latency_8cubed(stream), "cpu_oracle_csr": csr_baseline_8cubed()})
+    section("precision", lambda: precision_sweep(stream))
+    section("fp64", lambda: fp64_applies(stream, peak))
+    solves = section("solve", lambda: [solve_bench(3, 128), solve_bench(7, 64), solve_bench(3, 64, half=False),
+                                       solve_bench(7, 32, half=False)])
+    section("batch", lambda: batch_bench())
+    section("sweep", lambda: degree_sweep(stream))
     cpu = oracle_sample() if world == 1 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "k": K_DEG, "cells": [NC, NC, NC], "dofs": ndofs,
-                   "l2": "inputs (1.07 GB per vector) larger than L2, no flush", "parallelism": f"replicas x{world}",
-                   "kernel": "apply_cc (FP64 DFMA sum factorization)", "tile_cells": op.info["tile_cells"],
-                   "autotune": not args.no_tune},
+        "config": {"workload": WORKLOAD, "k": kdeg, "cells": nc, "dofs": ndofs,
+                   "l2": "inputs larger than L2 (1.07 GB per vector), no flush", "parallelism": f"replicas x{world}",
+                   "kernel": "apply_cc (FP64 DFMA sum factorization)", "tile_cells": tile_cells},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_source": "FP64 DFMA pipe, measured live by tp_bench_fma_peak (register-only FMA chains)",
-                     "flops_per_dof": op.info["flops_per_dof"],
-                     "hbm_gbs_algorithmic": 16.0 * ndofs / (avg_launch_ms * 1e-3) / 1e9},
+                     "peak_source": "FP64 DFMA pipe measured live (libtp_bench FMA probe)",
+                     "flops_per_dof": flops_per_dof, "algorithmic_bytes": 16 * ndofs},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": e2e_bytes,
-                "statistic": f"median of {e2e_steps} calls", "mean_value": job_throughput(ndofs, 1, world, e2e_mean),
-                "d2h_bytes_per_step": e2e_bytes},
+        "e2e": {"value": e2e_value, "unit": "GDoF/s", "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes,
+                "statistic": f"median of {e2e_steps} tp_apply_host calls",
+                "mean_value": job_throughput(ndofs, 1, world, e2e_mean)},
         "gpu_launches": args.steps,
         "clocks": clk,
-        "extra": extra,
-        "solve": solves,
-        "batch": batch,
-        "degree_sweep": sweep,
     }
+    if solves:
+        line["poisson_solve"] = solve_summary(solves[:2])
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump({"headline": line, "sections": sections}, f, indent=1)
     print(json.dumps(line), flush=True)
-    op.close()
 
 
 def main():

@@ -48,9 +48,13 @@ typedef enum { TP_FP64 = 0, TP_FP32 = 1, TP_FP16 = 2, TP_BF16 = 3 } tp_precision
  * h the cell width normal to the face, on interior and boundary faces alike. */
 typedef enum { TP_PENALTY_CONFIG = 0, TP_PENALTY_PAPER = 1 } tp_penalty;
 
-/* Kernel family for tp_apply. AUTO picks the fastest measured family for the
- * precision; CUDA_CORE forces the FMA-pipe sum-factorization kernel (the
- * paper's CUDA-core comparator, App. A); TENSOR forces the tensor-core kernel. */
+/* Kernel family for tp_apply. AUTO picks, per precision and degree, the family
+ * that measured fastest on GB300: the tcgen05 tensor kernel for FP16/BF16
+ * vectors at k = 3 (on meshes whose cell count plus one xy-slab stays below
+ * 2^31), the CUDA-core kernel otherwise (FP64: the DFMA kernel beats DMMA,
+ * which shares the FP64 pipe; FP32: the CUDA-core kernel beats mma.sync).
+ * CUDA_CORE forces the FMA-pipe sum-factorization kernel (the paper's CUDA-core
+ * comparator, App. A); TENSOR forces the tensor-core kernel. */
 typedef enum { TP_KERNEL_AUTO = 0, TP_KERNEL_CUDA_CORE = 1, TP_KERNEL_TENSOR = 2 } tp_kernel;
 
 typedef struct {
@@ -84,7 +88,12 @@ typedef struct {
  * ec = 1 every operand is split as in Algorithm 1: a = a_h + da*2^-s with
  * s = 11 for FP16 and 8 for BF16, and a*b = a_h b_h + (da b_h + a_h db)*2^-s).
  * BF16 vectors always use the split (8 significand bits are too few for the
- * 5e-3 per-apply tolerance otherwise). */
+ * 5e-3 per-apply tolerance otherwise).
+ * FP32 vectors on the half-precision tensor paths reach FP32 accuracy (relative
+ * l2 error <= 1e-5 per apply) only with FP16 operands and ec = 1. The other
+ * combinations are APPROXIMATE operators (tp_op_info_t.approximate = 1): with
+ * FP16 operands ec = 0 stays within 5e-3 and ec = 2 or 3 in between; with BF16
+ * operands ec = 1 stays within 1e-4 and ec = 0 within 2e-2. */
 
 typedef struct tp_mesh_s* tp_mesh;
 typedef struct tp_op_s* tp_op;
@@ -101,6 +110,8 @@ typedef struct {
                              3 = mma.sync f64 (DMMA); 0 for the CUDA-core kernel */
   int tile_cells;         /* cells per thread block (CUDA-core, DMMA) or per tile (tcgen05) of the
                              apply launch; 0 for the mma.sync kernel */
+  int approximate;        /* 1: FP32 vectors on a tensor path that does not reach FP32 accuracy
+                             (see the tensor kernel note above); 0 otherwise */
 } tp_op_info_t;
 
 /* Uniform Cartesian mesh of [0,lx]x[0,ly]x[0,lz] with nx*ny*nz cells
@@ -129,33 +140,48 @@ tp_status tp_op_destroy(tp_op op);
  * face operations, scatter) as one kernel launch, asynchronous on `stream`.
  * x and y are DEVICE pointers owned by the caller, ndofs entries of the
  * operator's precision in the layout above, 16-byte aligned, not
- * overlapping. Errors: TP_ERR_INVALID_ARG (NULL/unaligned/overlapping
- * pointers), TP_ERR_CUDA (launch failure). Ownership: nothing is retained. */
+ * overlapping. The operator's device (current at its creation) must be the
+ * current device. Errors: TP_ERR_INVALID_ARG (NULL/unaligned/overlapping
+ * pointers, another device current), TP_ERR_CUDA (launch failure).
+ * Ownership: nothing is retained. */
 tp_status tp_apply(tp_op op, void* y, const void* x, void* stream);
 
 /* y = A x with HOST vectors: copies x to a library-owned device buffer,
  * applies, copies y back, and synchronizes `stream` before returning.
  * Pinned host memory gives the fastest copies; pageable memory works.
  * The staging buffers (2*ndofs entries) are allocated on first use and kept
- * until tp_op_destroy. Errors as tp_apply, plus TP_ERR_OOM. */
+ * until tp_op_destroy. The operator's device must be current. Errors as
+ * tp_apply, plus TP_ERR_OOM. */
 tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream);
 
 /* y = A x with HOST vectors, allocating no device memory. The paper has no
  * counterpart: this is for callers that cannot call cudaMalloc, such as a
  * process whose device memory is all handed out by its own fixed pool or
  * budget, or a caller that must not meet the allocator's latency or its
- * out-of-memory failure mid-run. (tp_dg_laplace_create allocates no device
- * memory either, so such a caller can build the operator and use this.)
+ * out-of-memory failure mid-run. Operator creation itself allocates nothing
+ * on the device only for the CUDA-core kernel (TP_KERNEL_AUTO or
+ * TP_KERNEL_CUDA_CORE resolving to it) with autotune = 0; the tensor kernels
+ * allocate their operand matrices (mma.sync: 2 x 64 x 64 entries; tcgen05:
+ * 7 or 14 blocks of 64 x 64 entries and one status word) and autotune = 1
+ * allocates two proxy vectors of about 128 MB while it times the tile shapes.
  * Staging goes through one static device array of 2*TP_NOALLOC_MAX_BYTES
  * bytes (x half, y half) that every GPU loading the library holds until the
- * process exits; vectors larger than TP_NOALLOC_MAX_BYTES bytes are rejected
- * with TP_ERR_INVALID_ARG before any GPU work. The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture. Every
- * call shares the array: calls that overlap on the GPU (other threads, other
- * streams) race and must be serialized by the caller. Each call overwrites
- * both halves completely, so nothing carries over. Synchronizes `stream`
- * before returning. Errors as tp_apply_host (never TP_ERR_OOM). */
+ * process exits. CUDA loads a library's device code lazily by default, so
+ * the array is committed on a device by the first call on that device (or
+ * when the library loads, with CUDA_MODULE_LOADING=EAGER): make that first
+ * call before the caller's pool reserves the device's memory; if the array
+ * cannot be placed, the call fails with TP_ERR_CUDA and a message saying so.
+ * The first call on a device also looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process (the cached address does not survive cudaDeviceReset); make that
+ * first call before any stream capture. Vectors larger than
+ * TP_NOALLOC_MAX_BYTES bytes are rejected with TP_ERR_INVALID_ARG before any
+ * GPU work, and so is a call made while another device than the operator's
+ * is current. Every call shares the array: calls that overlap on the GPU
+ * (other threads, other streams) race and must be serialized by the caller.
+ * Each call overwrites both halves completely, so nothing carries over.
+ * Synchronizes `stream` before returning. Errors as tp_apply_host (never
+ * TP_ERR_OOM). */
 #define TP_NOALLOC_MAX_BYTES (8 * 1024 * 1024)
 tp_status tp_apply_host_noalloc(tp_op op, void* y_host, const void* x_host, void* stream);
 
@@ -278,6 +304,9 @@ typedef struct {
                               owned by the solver, valid until the next solve or destroy */
   int history_len;
   int reorthogonalizations;/* Arnoldi steps with the second Gram-Schmidt pass (every step) */
+  int vcycle_graph;        /* 1 if every preconditioner application of this solve was one launch of
+                              the V-cycle's captured CUDA graph; 0 if the V-cycle ran as direct
+                              launches (capture unavailable) or there is no preconditioner */
 } tp_solve_info;
 
 /* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's

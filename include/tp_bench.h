@@ -1,5 +1,9 @@
 /*
- * libtp measurement support (not part of the method).
+ * libtp_bench -- measurement support (not part of the method).
+ *
+ * A separate shared library (paper_2407_09621_gb300/libtp_bench.so), built
+ * beside libtp.so by the same build step; the method's library does not
+ * contain these functions.
  *
  * The paper reports arithmetic rates against the hardware peak of the pipe a
  * kernel runs on (Sec. 4.2, Sec. 6). The FP64 and FP32 FMA-pipe peaks of the
@@ -22,8 +26,12 @@ extern "C" {
  * best of 5 timed launches after 2 warm-ups, CUDA-event timed.
  * *tflops receives flops/s / 1e12 (FMA = 2 flops). Allocates and frees a
  * small device buffer. Blocks until done. Errors: TP_ERR_INVALID_ARG (NULL
- * out, other precisions), TP_ERR_CUDA, TP_ERR_OOM. */
+ * out, other precisions), TP_ERR_CUDA, TP_ERR_OOM; the message is in
+ * tp_bench_last_error(). */
 tp_status tp_bench_fma_peak(int precision, double* tflops, void* stream);
+
+/* Text of the last error of this library on the calling thread ("" if none). */
+const char* tp_bench_last_error(void);
 
 #ifdef __cplusplus
 }

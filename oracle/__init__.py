@@ -17,9 +17,13 @@ equation and algorithm numbers are those of the paper's LaTeX source):
                  side and L2 error of the Poisson problem (Sec. 7.2).
 * ``mg``      -- transfer operators, Chebyshev-Jacobi smoother, Algorithm 2
                  V-cycle and flexible GMRES (Sec. 7).
-* ``ec``      -- Algorithm 1 (error-corrected half-precision product).
-* ``spmv_omp.c`` -- a plain C/OpenMP CSR SpMV over the oracle's CSR arrays,
-                 used only to time the oracle on all host cores.
+* ``schwarz`` -- vertex-patch multiplicative Schwarz smoother (Sec. 7.1).
+* ``spmv``, ``spmv_omp.c`` -- CSR SpMV of the assembled matrix through SciPy
+                 (one core) and plain C/OpenMP (all host cores), used only to
+                 time the oracle for the CPU baseline.
+
+The error correction of Algorithm 1 has no oracle function: its GPU results
+are checked against the FP64 oracle's products directly.
 
 Parity status of every function is stated in its module header.
 """

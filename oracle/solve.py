@@ -12,6 +12,10 @@ u = sin(pi x) sin(pi y) sin(pi z), i.e. f = 3 pi^2 u and g = 0.
 * ``rhs_sine``: b_a = int f phi_a; f is separable, so b = 3 pi^2 b1 (x) b1 (x) b1
   with b1 the 1D load vector of sin(pi x), integrated by 30-point Gauss per
   cell (exact to rounding for k <= 7).
+* ``rhs_modes``: the same for a sum of sine modes (the batched problems);
+  pinned against ``rhs_sine`` for the single mode (1, 1, 1) and against the
+  closed-form integrals of the k = 1 basis for modes with p, q, r distinct
+  (tests/test_oracle_basis.py).
 * ``l2_error``: || u_h - u ||_L2 by per-cell tensor Gauss quadrature with k+4
   points per direction (the expanded form ||u_h||^2 - 2(u_h,u) + ||u||^2
   cancels to about 1e-8 and is not used). Pinned by the O(h^(k+1))

@@ -14,7 +14,7 @@ import re
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtp.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-HEADERS = [os.path.join(INCLUDE, f) for f in ("tp.h", "tp_bench.h")]
+HEADERS = [os.path.join(INCLUDE, f) for f in ("tp.h", "tp_test.h")]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_CUDA, TP_ERR_OOM = 0, 1, 2, 3
 TP_ERR_NONFINITE, TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_UNSUPPORTED = 4, 5, 6, 7
@@ -47,7 +47,7 @@ class tp_op_info_t(ctypes.Structure):
     _fields_ = [("ncells", ctypes.c_longlong), ("ndofs", ctypes.c_longlong), ("k", ctypes.c_int),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double),
-                ("tensor_path", ctypes.c_int), ("tile_cells", ctypes.c_int)]
+                ("tensor_path", ctypes.c_int), ("tile_cells", ctypes.c_int), ("approximate", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -62,7 +62,6 @@ _sig = {
     "tp_op_destroy": (ctypes.c_int, [_vp]),
     "tp_apply": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "tp_apply_host": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
-    "tp_bench_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(lib, _name)
@@ -70,10 +69,10 @@ for _name, (_res, _args) in _sig.items():
     _f.argtypes = _args
 
 
-def header_functions():
-    """Names of every function the public headers declare."""
+def header_functions(headers=None):
+    """Names of every function the given headers (default: include/tp.h) declare."""
     text = ""
-    for h in HEADERS:
+    for h in headers or HEADERS:
         with open(h) as f:
             text += f.read()
     return sorted(set(re.findall(r"^\s*(?:tp_status|const char\s*\*|void)\s+(tp_\w+)\s*\(", text, re.M)))
@@ -124,12 +123,6 @@ def tp_apply_host(op, y_ptr, x_ptr, stream=0):
     _check(lib.tp_apply_host(op, _vp(y_ptr), _vp(x_ptr), _vp(stream)))
 
 
-def tp_bench_fma_peak(precision, stream=0):
-    out = ctypes.c_double()
-    _check(lib.tp_bench_fma_peak(precision, ctypes.byref(out), _vp(stream)))
-    return out.value
-
-
 # ---------------------------------------------------------------- multigrid / FGMRES
 TP_MAX_LEVELS = 16
 TP_SMOOTHER_CHEBYSHEV, TP_SMOOTHER_VERTEX_PATCH = 0, 1
@@ -152,7 +145,7 @@ class tp_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("converged", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_len", ctypes.c_int),
-                ("reorthogonalizations", ctypes.c_int)]
+                ("reorthogonalizations", ctypes.c_int), ("vcycle_graph", ctypes.c_int)]
 
 
 _sig2 = {
@@ -236,7 +229,7 @@ def tp_fgmres_solve(solver, x_ptr, b_ptr, rtol=1e-10, maxit=200, stream=0, raise
     d = {"iterations": info.iterations, "restarts": info.restarts, "converged": info.converged,
          "rel_residual": info.rel_residual, "true_rel_residual": info.true_rel_residual,
          "history": [info.history[i] for i in range(info.history_len)] if info.history else [],
-         "reorthogonalizations": info.reorthogonalizations}
+         "reorthogonalizations": info.reorthogonalizations, "vcycle_graph": info.vcycle_graph}
     if st != TP_OK and raise_on_error:
         raise TPError(st, lib.tp_last_error().decode())
     return st, d
@@ -262,6 +255,15 @@ lib.tp_op_check.argtypes = [_vp]
 
 def tp_op_check(op):
     _check(lib.tp_op_check(op))
+
+
+lib.tp_test_set_wait_fault.restype = ctypes.c_int
+lib.tp_test_set_wait_fault.argtypes = [_vp, ctypes.c_int, ctypes.c_double]
+
+
+def tp_test_set_wait_fault(op, withhold_first_copy, wait_limit_s):
+    """Failure-injection hook of include/tp_test.h (tests of the bounded device waits only)."""
+    _check(lib.tp_test_set_wait_fault(op, int(withhold_first_copy), float(wait_limit_s)))
 
 
 lib.tp_batch_solve_solvers.restype = ctypes.c_int

@@ -1,7 +1,9 @@
 """Build libtp.so in-tree for sm_103a (GB300) with nvcc; no cmake.
 
 Every translation unit is compiled in parallel, then linked into
-``paper_2407_09621_gb300/libtp.so`` with the CUDA runtime linked statically.
+``paper_2407_09621_gb300/libtp.so`` (the method, include/tp.h) with the CUDA
+runtime linked statically; the measurement-support unit ``bench_probe.cu``
+(include/tp_bench.h) is linked on its own into ``libtp_bench.so``.
 Run ``python paper_2407_09621_gb300/build.py`` (it does not import the package,
 which needs the library to exist).
 """
@@ -13,6 +15,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtp.so")
+OUT_BENCH = os.path.join(HERE, "libtp_bench.so")
+BENCH_SOURCES = ("bench_probe.cu",)
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
@@ -57,12 +61,15 @@ def build(verbose=False, extra_flags=()):
 
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", OUT] + objs + ["-lrt", "-ldl", "-lpthread"]
-    if verbose:
-        print(" ".join(cmd), flush=True)
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    is_bench = [os.path.basename(s) in BENCH_SOURCES for s in srcs]
+    for out, group in ((OUT, [o for o, b in zip(objs, is_bench) if not b]),
+                       (OUT_BENCH, [o for o, b in zip(objs, is_bench) if b])):
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", out] + group + ["-lrt", "-ldl", "-lpthread"]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link of {out} failed:\n{r.stdout}\n{r.stderr}")
     return OUT
 
 

@@ -46,6 +46,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "../../include/tp_test.h"
 #include "tp_internal.h"
 
 namespace tp {
@@ -88,17 +89,18 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-// Bounded wait (about one second, and at most kWaitLimit polls) for the phase of `bar` with
-// the given parity. Gives up early when another role has raised the abort flag; on its own
-// timeout it raises the flag and records `code`.
-__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort, int* err, int code) {
+// Bounded wait (at most limit_ns, one second by default, and at most kWaitLimit polls) for the
+// phase of `bar` with the given parity. Gives up early when another role has raised the abort
+// flag; on its own timeout it raises the flag and records `code`.
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort, int* err, int code,
+                                         uint64_t limit_ns) {
   if (try_wait(bar, parity)) return true;
   const uint64_t t0 = now_ns();
   for (int it = 0; it < kWaitLimit; ++it) {
     if (try_wait(bar, parity)) return true;
     if ((it & 31) == 31) {
       if (*abort) return false;
-      if (now_ns() - t0 > 1000000000ull) break;
+      if (now_ns() - t0 > limit_ns) break;
       __nanosleep(64);
     }
   }
@@ -282,7 +284,12 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       bool ok = true;
       for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         for (int b = 0; b < 7; ++b) {
-          if (!(ok = wait_bar(empty(slot), ph ^ 1u, abort, err, 1))) break;
+          if (!(ok = wait_bar(empty(slot), ph ^ 1u, abort, err, 1, P.wait_ns))) break;
+          if (P.test_withhold && blockIdx.x == 0 && t == 0 && b == 0) {
+            // failure-injection tests: this slot never fills, so the waits on it run out
+            if (++slot == S) { slot = 0; ph ^= 1u; }
+            continue;
+          }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(slot)), "r"(kTileBytes)
                        : "memory");
           const int row = (int)(t * kRows + offs[b]);  // may be negative or past the end: zero fill
@@ -310,16 +317,16 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       bool ok = true;
       for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
         const int a = it & 1;
-        if (!(ok = wait_bar(acce(a), ((it >> 1) & 1) ^ 1u, abort, err, 2))) break;
+        if (!(ok = wait_bar(acce(a), ((it >> 1) & 1) ^ 1u, abort, err, 2, P.wait_ns))) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t bm = tile_bmask(t * kRows, P);
         const uint32_t dt = tmem + 64u * a;
         for (int b = 0; b < 7; ++b) {
           if (bm >> b & 1u) {
-            ok = wait_bar(ready(slot), (rdy >> slot) & 1u, abort, err, 3);
+            ok = wait_bar(ready(slot), (rdy >> slot) & 1u, abort, err, 3, P.wait_ns);
             rdy ^= 1u << slot;
           } else {
-            ok = wait_bar(full(slot), ph, abort, err, 3);
+            ok = wait_bar(full(slot), ph, abort, err, 3, P.wait_ns);
           }
           if (!ok) break;
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -372,7 +379,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       }
       const bool any = bnd[0] | bnd[1] | bnd[2] | bnd[3] | bnd[4] | bnd[5];
       float u[64];
-      if (!(ok = wait_bar(full(slot), ph, abort, err, 4))) break;
+      if (!(ok = wait_bar(full(slot), ph, abort, err, 4, P.wait_ns))) break;
       if (any) {
         const unsigned char* own = sA + slot * kTileBytes;
 #pragma unroll
@@ -388,7 +395,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
 #pragma unroll
       for (int b = 1; b < 7; ++b) {
         if (bm >> b & 1u) {
-          if (!(ok = wait_bar(full(slot), ph, abort, err, 4))) break;
+          if (!(ok = wait_bar(full(slot), ph, abort, err, 4, P.wait_ns))) break;
           if (bnd[b - 1]) write_ghost<TO>(sA + slot * kTileBytes, row, u, (b - 1) >> 1, (b - 1) & 1, P);
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
           arrive(ready(slot));
@@ -404,7 +411,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int a = it & 1;
       // warp-uniform decision: the TMEM loads below are .sync.aligned
-      if (!__all_sync(0xffffffffu, wait_bar(accf(a), (it >> 1) & 1, abort, err, 7))) break;
+      if (!__all_sync(0xffffffffu, wait_bar(accf(a), (it >> 1) & 1, abort, err, 7, P.wait_ns))) break;
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       uint32_t r[64];
       const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * a;
@@ -525,6 +532,8 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   P.ncells = op->ncells;
   P.out_scale = (float)(1.0 / sc);
   P.lo_scale = 1.0f;
+  P.wait_ns = 1000000000ull;
+  P.test_withhold = 0;
   const Ref1D& R = op->ref;
   for (int d = 0; d < 3; ++d) {
     const double g2h = 2.0 * op->dir[d].gamma * op->dir[d].h;
@@ -582,3 +591,19 @@ cudaError_t launch_apply_umma(const tp_op_s* op, void* y, const void* x, cudaStr
 }
 
 }  // namespace tp
+
+extern "C" tp_status tp_test_set_wait_fault(tp_op op, int withhold_first_copy, double wait_limit_s) {
+  using namespace tp;
+  if (!op) { set_error("tp_test_set_wait_fault: NULL op"); return TP_ERR_INVALID_ARG; }
+  if (!(wait_limit_s >= 0.0) || wait_limit_s > 60.0) {
+    set_error("tp_test_set_wait_fault: wait limit must be in [0, 60] seconds");
+    return TP_ERR_INVALID_ARG;
+  }
+  if (!op->use_umma || op->opts.kernel != TP_KERNEL_TENSOR) {
+    set_error("tp_test_set_wait_fault: the operator does not run the tcgen05 apply");
+    return TP_ERR_UNSUPPORTED;
+  }
+  op->umma_params.test_withhold = withhold_first_copy ? 1 : 0;
+  op->umma_params.wait_ns = wait_limit_s > 0.0 ? (unsigned long long)(wait_limit_s * 1e9) : 1000000000ull;
+  return TP_OK;
+}

@@ -47,6 +47,7 @@ struct tp_solver_s {
   // the preconditioner V-cycle (fixed input pb, output px) captured once as a CUDA graph
   cudaGraphExec_t vcycle_graph = nullptr;
   bool graph_tried = false;
+  int graph_launches = 0, direct_vcycles = 0;  // preconditioner applications of the current solve
 };
 
 using namespace tp;
@@ -86,7 +87,11 @@ static bool capture_vcycle(tp_solver_s* s) {
 
 static cudaError_t run_vcycle(tp_solver_s* s, cudaStream_t st) {
   if (!s->graph_tried) capture_vcycle(s);
-  if (s->vcycle_graph) return cudaGraphLaunch(s->vcycle_graph, st);
+  if (s->vcycle_graph) {
+    ++s->graph_launches;
+    return cudaGraphLaunch(s->vcycle_graph, st);
+  }
+  ++s->direct_vcycles;
   return tp::mg_vcycle(s->mg, tp::mg_finest_level(s->mg), s->px, s->pb, 1, st);
 }
 
@@ -223,6 +228,7 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
   const double pscale = std::sqrt((double)n);  // v_j has unit norm: scale to O(1) entries for low precision
   s->history.clear();
   s->reorth = 0;
+  s->graph_launches = s->direct_vcycles = 0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h(m + 2), h2(m + 2);
   auto Hij = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   int its = 0, restarts = 0, converged = 0;
@@ -363,6 +369,7 @@ extern "C" tp_status tp_fgmres_solve(tp_solver s, double* x, const double* b, do
     info->history = s->history.data();
     info->history_len = (int)s->history.size();
     info->reorthogonalizations = s->reorth;
+    info->vcycle_graph = s->graph_launches > 0 && s->direct_vcycles == 0;
   }
   if (status == TP_OK && !converged) {
     set_error("tp_fgmres_solve: not converged after %d iterations (relative residual %.3e)", its, rel);

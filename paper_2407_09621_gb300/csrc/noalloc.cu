@@ -5,9 +5,11 @@
 // whose device memory is handed out by its own fixed pool or budget (every
 // byte reserved up front), or a caller that must not hit the allocator's
 // latency or its out-of-memory failure in the middle of its work. This
-// variant stages through a statically sized array that the CUDA runtime
-// places in device memory when the library's module is loaded, so the call
-// itself only copies and launches.
+// variant stages through a statically sized array in device memory, so the
+// call itself only copies and launches. CUDA loads this file's module lazily
+// (by default), so the array is placed on a device at the first call there,
+// when cudaGetSymbolAddress needs it; that call then fails cleanly if the
+// device has no room left for it.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,7 +28,8 @@ size_t elem_bytes(tp_precision p);
 static __device__ __align__(256) unsigned char g_noalloc_stage[2 * TP_NOALLOC_MAX_BYTES];
 
 // Device address of g_noalloc_stage per device ordinal, looked up once per
-// device (the name is a host-side stand-in, not a device address).
+// device (the name is a host-side stand-in, not a device address). Kept for
+// the life of the process: it does not survive cudaDeviceReset.
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[256] = {};
 
@@ -41,8 +44,14 @@ static tp_status noalloc_stage_address(void** out) {
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
-    st = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_stage), "tp_apply_host_noalloc: cudaGetSymbolAddress");
-    if (st != TP_OK) return st;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("tp_apply_host_noalloc: the static staging array (%d bytes) is unavailable on device %d: "
+                "loading it failed (%s); make the first call on a device before its memory is reserved",
+                2 * TP_NOALLOC_MAX_BYTES, dev, cudaGetErrorString(e));
+      return TP_ERR_CUDA;
+    }
     g_noalloc_addr[dev] = p;
   }
   *out = g_noalloc_addr[dev];
@@ -68,8 +77,15 @@ extern "C" tp_status tp_apply_host_noalloc(tp_op op, void* y_host, const void* x
     set_error("tp_apply_host_noalloc: x and y overlap");
     return TP_ERR_INVALID_ARG;
   }
+  int dev = -1;
+  tp_status st = cuda_status(cudaGetDevice(&dev), "tp_apply_host_noalloc: cudaGetDevice");
+  if (st != TP_OK) return st;
+  if (dev != op->device) {
+    set_error("tp_apply_host_noalloc: device %d is current, the operator lives on device %d", dev, op->device);
+    return TP_ERR_INVALID_ARG;
+  }
   void* base = nullptr;
-  tp_status st = noalloc_stage_address(&base);
+  st = noalloc_stage_address(&base);
   if (st != TP_OK) return st;
   // Both halves are fully overwritten by every call (copy in, kernel out): nothing needs clearing.
   unsigned char* dx = static_cast<unsigned char*>(base);

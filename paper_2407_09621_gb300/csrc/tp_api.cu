@@ -382,6 +382,16 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: ec must be 0 (off), 1 (both operands), 2 (matrix) or 3 (vector)");
     return TP_ERR_INVALID_ARG;
   }
+  const long long ncells = (long long)m->nx * m->ny * m->nz;
+  if (o.kernel == TP_KERNEL_AUTO) {
+    // The fastest family measured on GB300 for each precision: FP16/BF16 vectors at k = 3 run on
+    // tcgen05 (386 / 301 GDoF/s at 128^3 cells against 230 / 223 on the CUDA-core kernel), where its
+    // TMA row coordinates fit in int32; FP64 stays on DFMA (DMMA shares the FP64 pipe and is slower)
+    // and FP32 on the CUDA-core kernel (the mma.sync path is slower); everything else is CUDA-core.
+    const long long reach = ncells + (long long)m->nx * m->ny + 128;
+    o.kernel = ((p == TP_FP16 || p == TP_BF16) && k == 3 && reach < (1LL << 31)) ? TP_KERNEL_TENSOR
+                                                                                 : TP_KERNEL_CUDA_CORE;
+  }
   if (o.kernel == TP_KERNEL_TENSOR && p == TP_FP64) {
     if (k != 3 && k != 7) {
       set_error("tp_dg_laplace_create: the FP64 tensor (DMMA) kernel supports k = 3 and k = 7");
@@ -410,7 +420,6 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: degrees above %d need the CUDA-core kernel and FP64 or FP32 vectors", kMaxN - 1);
     return TP_ERR_UNSUPPORTED;
   }
-  const long long ncells = (long long)m->nx * m->ny * m->nz;
   const long long n3 = (long long)(k + 1) * (k + 1) * (k + 1);
   if (ncells > (1LL << 62) / n3) { set_error("tp_dg_laplace_create: DoF count overflows"); return TP_ERR_INVALID_ARG; }
   tp_op_s* op = new (std::nothrow) tp_op_s();
@@ -420,7 +429,6 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   op->n = k + 1;
   op->prec = p;
   op->opts = o;
-  if (op->opts.kernel == TP_KERNEL_AUTO) op->opts.kernel = TP_KERNEL_CUDA_CORE;
   op->ncells = ncells;
   op->ndofs = ncells * n3;
   op->ref = make_ref1d(k);
@@ -460,6 +468,10 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n >= 5 && centro;
   info->flops_per_dof = apply_flops_per_dof(op->n, eo);
   info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
+  // FP32 vectors on the half-precision tensor paths: FP32 accuracy (1e-5 per apply) only with FP16
+  // operands and both operands refined (Algorithm 1, ec = 1)
+  info->approximate = op->prec == TP_FP32 && op->opts.kernel == TP_KERNEL_TENSOR &&
+                      !(op->opts.tc_type == TP_FP16 && op->opts.ec == 1);
   info->tile_cells = info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 3 ? dmma_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 2 ? 128 : 0;
@@ -492,6 +504,19 @@ tp_status tp_op_destroy(tp_op op) {
   return TP_OK;
 }
 
+// The operator's constants, matrices and status word live on the device that was current at its
+// creation; a launch with another device current would read memory that device never filled.
+static tp_status check_device(tp_op op, const char* who) {
+  int dev = -1;
+  tp_status st = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != TP_OK) return st;
+  if (dev != op->device) {
+    set_error("%s: device %d is current, the operator lives on device %d", who, dev, op->device);
+    return TP_ERR_INVALID_ARG;
+  }
+  return TP_OK;
+}
+
 static tp_status check_vectors(tp_op op, const void* y, const void* x, const char* who) {
   if (!op) { set_error("%s: op is NULL", who); return TP_ERR_INVALID_ARG; }
   if (!x || !y) { set_error("%s: NULL vector", who); return TP_ERR_INVALID_ARG; }
@@ -499,7 +524,7 @@ static tp_status check_vectors(tp_op op, const void* y, const void* x, const cha
   const size_t bytes = (size_t)op->ndofs * elem_bytes(op->prec);
   const uintptr_t xa = (uintptr_t)x, ya = (uintptr_t)y;
   if (xa < ya + bytes && ya < xa + bytes) { set_error("%s: x and y overlap", who); return TP_ERR_INVALID_ARG; }
-  return TP_OK;
+  return check_device(op, who);
 }
 
 tp_status tp_apply(tp_op op, void* y, const void* x, void* stream) {
@@ -513,6 +538,8 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
   const size_t bytes = (size_t)op->ndofs * elem_bytes(op->prec);
   const uintptr_t xa = (uintptr_t)x_host, ya = (uintptr_t)y_host;
   if (xa < ya + bytes && ya < xa + bytes) { set_error("tp_apply_host: x and y overlap"); return TP_ERR_INVALID_ARG; }
+  tp_status dst = check_device(op, "tp_apply_host");
+  if (dst != TP_OK) return dst;
   if (op->hbytes < bytes) {
     if (op->hx) cudaFree(op->hx);
     if (op->hy) cudaFree(op->hy);

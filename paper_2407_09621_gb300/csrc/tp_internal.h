@@ -72,6 +72,8 @@ struct UmmaParams {
   float lo_scale;   // scale of the low-part products (1: they share the accumulator)
   float gh[3][4];   // high-side ghost functional for w_1 per direction
   float gl[3][4];   // low-side ghost functional for w_{n-2}
+  unsigned long long wait_ns;  // limit of every bounded wait on the pipeline barriers (1 s by default)
+  int test_withhold;           // failure-injection tests only: CTA 0 skips its first input-tile copy
 };
 
 void set_error(const char* fmt, ...);

@@ -16,6 +16,23 @@ def test_header_functions_are_exported():
         assert hasattr(_lib, name), f"{name} has no Python binding"
 
 
+def test_bench_support_library_is_separate():
+    """The FMA-peak probe (include/tp_bench.h) lives in libtp_bench.so, not in the method's library."""
+    import os
+    hdr = os.path.join(_lib.INCLUDE, "tp_bench.h")
+    names = _lib.header_functions([hdr])
+    assert "tp_bench_fma_peak" in names
+    bench = ctypes.CDLL(os.path.join(_lib.HERE, "libtp_bench.so"))
+    for name in names:
+        assert hasattr(bench, name), f"{name} declared in include/tp_bench.h but not exported"
+    assert not hasattr(_lib.lib, "tp_bench_fma_peak")
+    bench.tp_bench_fma_peak.restype = ctypes.c_int
+    bench.tp_bench_fma_peak.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    bench.tp_bench_last_error.restype = ctypes.c_char_p
+    assert bench.tp_bench_fma_peak(0, None, None) == _lib.TP_ERR_INVALID_ARG
+    assert b"NULL" in bench.tp_bench_last_error()
+
+
 def test_mesh_validation():
     with pytest.raises(_lib.TPError) as e:
         _lib.tp_mesh_create(0, 4, 4)

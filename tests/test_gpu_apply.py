@@ -65,14 +65,48 @@ def test_fp64_paper_penalty_and_anisotropic_box(pen):
     assert rel_l2(y, A @ x) < TOL["fp64"]
 
 
+def _auto_differs(k, prec):
+    """AUTO resolves to tcgen05 for FP16/BF16 vectors at k = 3 and to the CUDA-core kernel elsewhere."""
+    return k == 3 and prec in ("fp16", "bf16")
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
-def test_low_precision_against_fp64_oracle(prec, k):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_low_precision_against_fp64_oracle(prec, k, kernel):
+    if kernel == 1 and not _auto_differs(k, prec):
+        pytest.skip("AUTO already is the CUDA-core kernel here")
     dims = (5, 3, 4)
     m = Mesh(*dims)
     x = uniform_vector(m.ncells * (k + 1) ** 3, seed=10 + k)
-    y = _gpu_apply(dims, k, prec, x)
+    y = _gpu_apply(dims, k, prec, x, kernel=kernel)
     assert rel_l2(y, BlockOperator(m, k).apply(x)) < TOL[prec]
+
+
+@pytest.mark.parametrize("k,prec,family,path", [(3, "fp16", 2, 2), (3, "bf16", 2, 2), (3, "fp64", 1, 0),
+                                                (3, "fp32", 1, 0), (2, "fp16", 1, 0), (7, "bf16", 1, 0),
+                                                (7, "fp64", 1, 0), (12, "fp32", 1, 0)])
+def test_auto_kernel_selection(k, prec, family, path):
+    """TP_KERNEL_AUTO takes the family measured fastest for the precision and degree."""
+    from paper_2407_09621_gb300 import DGLaplace
+    op = DGLaplace(3, 2, 4, k, prec)
+    try:
+        assert op.info["kernel"] == family and op.info["tensor_path"] == path
+        assert op.info["approximate"] == 0
+    finally:
+        op.close()
+
+
+@pytest.mark.parametrize("tc_type,ec,approx", [(2, 1, 0), (2, 0, 1), (2, 2, 1), (2, 3, 1), (3, 1, 1), (3, 0, 1)])
+def test_fp32_tensor_operators_flag_their_accuracy(tc_type, ec, approx):
+    """FP32 vectors on the half-precision tensor path reach FP32 accuracy only with FP16 operands
+    and both operands refined; every other combination reports itself as approximate."""
+    from paper_2407_09621_gb300 import DGLaplace
+    op = DGLaplace(3, 3, 3, 3, "fp32", kernel=TENSOR, ec=ec, tc_type=tc_type)
+    try:
+        assert op.info["approximate"] == approx
+    finally:
+        op.close()
 
 
 def test_apply_is_deterministic_fp64():
@@ -153,11 +187,14 @@ def test_config1_full_size_fp64_sampled_and_rank1(k, nc):
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
 @pytest.mark.parametrize("k,nc", [(2, 107), (3, 80), (4, 64), (5, 54), (7, 40)])
-def test_config2_precision_sweep_sampled(prec, k, nc):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_config2_precision_sweep_sampled(prec, k, nc, kernel):
+    if kernel == 1 and not _auto_differs(k, prec):
+        pytest.skip("AUTO already is the CUDA-core kernel here")
     dims = (nc, nc, nc)
     m = Mesh(*dims)
     x = uniform_vector(m.ncells * (k + 1) ** 3, seed=0)
-    y = _gpu_apply(dims, k, prec, x)
+    y = _gpu_apply(dims, k, prec, x, kernel=kernel)
     cells = sample_cells(m.ncells, 512, seed=2, nx=nc, ny=nc, nz=nc)
     ref = BlockOperator(m, k).rows(x, cells)
     assert rel_l2(y.reshape(m.ncells, -1)[cells], ref) < TOL[prec]

@@ -445,3 +445,47 @@ def test_vertex_patch_rejects_half_precision():
     finally:
         _lib.tp_op_destroy(op)
         _lib.tp_mesh_destroy(mesh)
+
+
+def _gpu_solve_l2(k, nc, prec, smoother):
+    """FP64 FGMRES(30) to rtol 1e-10 with one V-cycle of `prec` and `smoother`; the L2 error of the
+    solution against u = sin(pi x) sin(pi y) sin(pi z), evaluated on the GPU (tp_l2_error_sines,
+    checked against the oracle's l2_error in test_rhs_and_l2_error_match_oracle)."""
+    from paper_2407_09621_gb300 import _lib
+    mesh = _lib.tp_mesh_create(nc, nc, nc)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    mg = _lib.tp_mg_create(op, precision=PREC[prec], smoother=smoother)
+    solver = _lib.tp_fgmres_create(op, mg, 30)
+    try:
+        n = _lib.tp_op_get_info(op)["ndofs"]
+        b = torch.empty(n, dtype=torch.float64, device="cuda")
+        _lib.tp_rhs_sines(op, b.data_ptr())
+        x = torch.zeros_like(b)
+        st, info = _lib.tp_fgmres_solve(solver, x.data_ptr(), b.data_ptr(), 1e-10, 300)
+        assert info["converged"] == 1
+        return _lib.tp_l2_error_sines(op, x.data_ptr()), info
+    finally:
+        _lib.tp_solver_destroy(solver)
+        _lib.tp_mg_destroy(mg)
+        _lib.tp_op_destroy(op)
+        _lib.tp_mesh_destroy(mesh)
+        torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("k,nc", [(3, 128), (7, 64)])
+def test_config3_full_size_mixed_solve_meets_l2_rule(k, nc):
+    """The two 134M-DoF Poisson solves of Sec. 7.2's setting: the mixed solve (FP32 vertex-patch
+    V-cycle) meets the L2 rule against the all-FP64 solve (FP64 Chebyshev V-cycle). The FP64 error is
+    anchored to the oracle: at k = 3 within a factor 2 of the exact discrete solution's error on
+    (nc/2)^3 cells divided by 2^(k+1) (the O(h^(k+1)) rate), at k = 7 at the FP64 round-off floor."""
+    e64, info64 = _gpu_solve_l2(k, nc, "fp64", 0)
+    e_mixed, info_mixed = _gpu_solve_l2(k, nc, "fp32", VP)
+    if k == 3:
+        h = nc // 2
+        u = FastDiag(k, h, h, h).solve(rhs_sine(k, h, h, h))
+        e_anchor = l2_error(u, k, h, h, h, sine_exact) / 2 ** (k + 1)
+        assert 0.5 * e_anchor < e64 < 2.0 * e_anchor, (e64, e_anchor)
+    else:
+        assert e64 < 3e-11
+    assert info_mixed["iterations"] <= 8
+    assert _l2_rule(e_mixed, e64), (e_mixed, e64)

@@ -72,3 +72,44 @@ def test_reference_matrices_integrals(k):
     np.testing.assert_allclose(r.Khat @ np.ones(k + 1), 0, atol=1e-11)
     np.testing.assert_allclose(r.v0, np.eye(k + 1)[0], atol=1e-15)
     np.testing.assert_allclose(r.v1, np.eye(k + 1)[-1], atol=1e-15)
+
+
+def test_rhs_modes_single_mode_is_the_paper_right_hand_side():
+    from oracle.solve import rhs_modes, rhs_sine
+    for k, dims in ((1, (3, 4, 2)), (3, (2, 2, 3))):
+        np.testing.assert_allclose(rhs_modes(k, *dims, [(1.0, 1, 1, 1)]), rhs_sine(k, *dims), rtol=1e-14, atol=0)
+
+
+def test_rhs_modes_against_closed_form_integrals_k1():
+    """k = 1: the Gauss-Lobatto basis on a cell [a, a + h] is phi_0 = (a + h - x)/h, phi_1 = (x - a)/h,
+    whose integrals against sin(w x) have closed forms; the load vector of
+    f = a pi^2 (p^2 + q^2 + r^2) sin(p pi x) sin(q pi y) sin(r pi z) is their tensor product, placed at
+    g = ((cz ny + cy) nx + cx) 8 + (l 2 + j) 2 + i. Two modes with p, q, r all different."""
+    from oracle.solve import rhs_modes
+
+    def b1(w, nc):
+        h = 1.0 / nc
+        out = np.zeros((nc, 2))
+        for c in range(nc):
+            a = c * h
+            s = (np.sin(w * (a + h)) - np.sin(w * a)) / (h * w * w)
+            out[c, 0] = np.cos(w * a) / w - s
+            out[c, 1] = -np.cos(w * (a + h)) / w + s
+        return out
+
+    nx, ny, nz = 3, 2, 4
+    modes = [(0.7, 1, 2, 3), (-1.3, 3, 1, 2)]
+    expect = np.zeros(nx * ny * nz * 8)
+    for a, p, q, r in modes:
+        bx, by, bz = b1(p * np.pi, nx), b1(q * np.pi, ny), b1(r * np.pi, nz)
+        coef = a * np.pi ** 2 * (p * p + q * q + r * r)
+        for cz in range(nz):
+            for cy in range(ny):
+                for cx in range(nx):
+                    for l in range(2):
+                        for j in range(2):
+                            for i in range(2):
+                                g = ((cz * ny + cy) * nx + cx) * 8 + (l * 2 + j) * 2 + i
+                                expect[g] += coef * bx[cx, i] * by[cy, j] * bz[cz, l]
+    got = rhs_modes(1, nx, ny, nz, modes)
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-13 * np.abs(expect).max())

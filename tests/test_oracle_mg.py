@@ -114,3 +114,26 @@ def test_fgmres_with_vcycle_reaches_discrete_solution():
     assert hist[-1] <= 1e-10
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) < 1e-8
     assert its < 30
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_vcycle_without_smoothing_is_the_two_grid_correction(k):
+    """One V-cycle over two levels with the smoother switched off and the exact coarse solve is
+    x1 = x0 + P A_c^{-1} P^T (b - A x0), with A and A_c the matrices assembled on the fine and the
+    coarse mesh (rediscretized, Algorithm 2) and the error e1 = (I - P A_c^{-1} P^T A) e0. Checked
+    against dense linear algebra on the assembled matrices: a restriction by P instead of P^T, a
+    scaled correction or a coarse operator of the wrong mesh would each fail."""
+    nc = 4
+    mg = VCycle(k, nc, coarse_nc=2)
+    mg.smooth = lambda l, b, x, post=False: x  # no pre- or post-smoothing
+    A = assemble(Mesh(nc, nc, nc), k).toarray()
+    Ac = assemble(Mesh(2, 2, 2), k).toarray()
+    P = prolongation(k, 2, 2, 2).toarray()
+    rng = np.random.default_rng(7 + k)
+    b, x0 = rng.standard_normal((2, A.shape[0]))
+    x1 = mg.vcycle(1, b, x0)
+    expect = x0 + P @ np.linalg.solve(Ac, P.T @ (b - A @ x0))
+    np.testing.assert_allclose(x1, expect, rtol=0, atol=1e-11 * np.abs(expect).max())
+    xs = np.linalg.solve(A, b)
+    e0, e1 = xs - x0, xs - x1
+    np.testing.assert_allclose(e1, e0 - P @ np.linalg.solve(Ac, P.T @ (A @ e0)), atol=1e-10 * np.abs(e0).max())
