@@ -18,6 +18,8 @@ equation and algorithm numbers are those of the paper's LaTeX source):
 * ``mg``      -- transfer operators, Chebyshev-Jacobi smoother, Algorithm 2
                  V-cycle and flexible GMRES (Sec. 7).
 * ``schwarz`` -- vertex-patch multiplicative Schwarz smoother (Sec. 7.1).
+* ``patchwise`` -- the operator evaluated patch by patch over vertex patches
+                 (Sec. 2.1, Eq. (9) with 2(k+1)-point 1D patch factors).
 * ``spmv``, ``spmv_omp.c`` -- CSR SpMV of the assembled matrix through SciPy
                  (one core) and plain C/OpenMP (all host cores), used only to
                  time the oracle for the CPU baseline.
