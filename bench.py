@@ -9,7 +9,8 @@ flush is needed between steps. Metric: GDoF/s (DoFs of all ranks / time).
 Output: one JSON line per secondary measurement ({"section": ...}: the 8^3
 latency case with the oracle's CSR SpMV on one and on all host cores, the
 per-precision apply sweep on ~33M DoFs with relative errors, the other FP64
-applies, the Sec. 7.2 Poisson solves, the 32-problem batch, the degree
+applies, the paper's patch-wise evaluation beside the cell-wise one, the
+Sec. 7.2 Poisson solves, the 32-problem batch, the degree
 sweep), then the headline as the LAST line (compact: value, roofline,
 cpu_baseline, e2e, clocks, a summary of the solves). --out FILE also writes
 everything as one JSON document.
@@ -58,7 +59,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extra", action="store_true", help="skip the secondary configurations")
-    p.add_argument("--extras", default="latency,precision,fp64,solve,batch,sweep",
+    p.add_argument("--extras", default="latency,precision,fp64,patchwise,solve,batch,sweep",
                    help="comma-separated secondary sections to run (default: all)")
     p.add_argument("--out", default=None, help="also write the headline and every section to this JSON file")
     p.add_argument("--kernel-only", action="store_true",
@@ -334,6 +335,36 @@ def fp64_applies(stream, peak):
         op.close()
         del x, y
     return out
+
+
+def patchwise_applies(stream, peaks):
+    """The paper's patch-wise evaluation (Sec. 2.1, TP_KERNEL_PATCH: vertex patches of 2x2x2 cells, N = 2(k+1))
+    beside the cell-wise kernel, k = 3 (N = 8) and k = 7 (N = 16) on 16.8M DoFs, FP64 and FP32. Flops per DoF
+    are the patch-wise count (224 (k+1) + 8; Table 4 lists 1702-1843 at N = 16)."""
+    import torch
+    from paper_2407_09621_gb300 import DGLaplace, _lib
+    from tp_synth import uniform_vector
+    rows = []
+    for k, nc in ((3, 64), (7, 32)):
+        for prec in ("fp64", "fp32"):
+            x = None
+            for kern in (_lib.TP_KERNEL_PATCH, _lib.TP_KERNEL_CUDA_CORE):
+                op = DGLaplace(nc, nc, nc, k, prec, kernel=kern)
+                if x is None:
+                    x = torch.from_numpy(uniform_vector(op.ndofs, seed=0)).to("cuda", op.dtype)
+                y = torch.empty_like(x)
+                per, _ = time_applies(op, y, x, 5, 2, stream)
+                ms = statistics.mean(per)
+                tf = op.info["flops_per_dof"] * op.ndofs / ms / 1e9
+                rows.append({"k": k, "N": 2 * (k + 1) if kern == _lib.TP_KERNEL_PATCH else k + 1, "cells": nc,
+                             "precision": prec, "kernel": "patch" if kern == _lib.TP_KERNEL_PATCH else "cell",
+                             "ms": round(ms, 4), "gdofs": round(op.ndofs / ms / 1e6, 3),
+                             "flops_per_dof": op.info["flops_per_dof"], "tflops": round(tf, 4),
+                             "frac_of_fma_peak": round(tf / peaks[prec], 4)})
+                op.close()
+                del y
+            del x
+    return rows
 
 
 # Sec. 8 precision sweep: about 33M DoFs per degree
@@ -654,6 +685,7 @@ def run_ours(args):
     section("latency", lambda: {"gpu": latency_8cubed(stream), "cpu_oracle_csr": csr_baseline_8cubed()})
     section("precision", lambda: precision_sweep(stream))
     section("fp64", lambda: fp64_applies(stream, peak))
+    section("patchwise", lambda: patchwise_applies(stream, {"fp64": peak, "fp32": fma_peak(1, stream)}))
     solves = section("solve", lambda: [solve_bench(3, 128), solve_bench(7, 64), solve_bench(3, 64, half=False),
                                        solve_bench(7, 32, half=False)])
     section("batch", lambda: batch_bench())

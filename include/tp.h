@@ -54,8 +54,17 @@ typedef enum { TP_PENALTY_CONFIG = 0, TP_PENALTY_PAPER = 1 } tp_penalty;
  * 2^31), the CUDA-core kernel otherwise (FP64: the DFMA kernel beats DMMA,
  * which shares the FP64 pipe; FP32: the CUDA-core kernel beats mma.sync).
  * CUDA_CORE forces the FMA-pipe sum-factorization kernel (the paper's CUDA-core
- * comparator, App. A); TENSOR forces the tensor-core kernel. */
-typedef enum { TP_KERNEL_AUTO = 0, TP_KERNEL_CUDA_CORE = 1, TP_KERNEL_TENSOR = 2 } tp_kernel;
+ * comparator, App. A); TENSOR forces the tensor-core kernel. PATCH evaluates the
+ * operator patch-wise, the paper's form (Sec. 2.1): over the vertex patches of
+ * 2 x 2 x 2 cells, each patch applying the Kronecker sum of Eq. (9) with 1D
+ * factors of size N = 2(k+1) that hold its share of the cell integrals (half of
+ * an interior cell's, all of a first or last cell's) and the faces it owns (the
+ * face at its vertex, and the boundary faces in the first and last patch), the
+ * patch results summed over eight colours of disjoint patches. The sum is the
+ * same operator; every DoF is computed in up to eight patches, 224(k+1) + 8
+ * flops per DoF. FP64 and FP32 vectors, k <= 7, at least two cells per
+ * direction; on the FMA pipes. */
+typedef enum { TP_KERNEL_AUTO = 0, TP_KERNEL_CUDA_CORE = 1, TP_KERNEL_TENSOR = 2, TP_KERNEL_PATCH = 3 } tp_kernel;
 
 typedef struct {
   int penalty;  /* tp_penalty */
@@ -107,9 +116,9 @@ typedef struct {
   size_t elem_bytes;      /* bytes per vector entry */
   double flops_per_dof;   /* algorithmic flops per DoF of one tp_apply (FMA = 2) */
   int tensor_path;        /* tensor kernel only: 1 = mma.sync f16/bf16, 2 = tcgen05 (TMA + TMEM),
-                             3 = mma.sync f64 (DMMA); 0 for the CUDA-core kernel */
-  int tile_cells;         /* cells per thread block (CUDA-core, DMMA) or per tile (tcgen05) of the
-                             apply launch; 0 for the mma.sync kernel */
+                             3 = mma.sync f64 (DMMA); 0 for the CUDA-core and patch-wise kernels */
+  int tile_cells;         /* cells per thread block (CUDA-core, DMMA; 8 for the patch-wise kernel: one
+                             vertex patch) or per tile (tcgen05) of the apply launch; 0 for mma.sync */
   int approximate;        /* 1: FP32 vectors on a tensor path that does not reach FP32 accuracy
                              (see the tensor kernel note above); 0 otherwise */
 } tp_op_info_t;
@@ -237,7 +246,8 @@ typedef struct {
   int precision;     /* TP_FP64, TP_FP32 (default), TP_FP16 or TP_BF16 */
   int power_iters;   /* power iterations for the lmax estimate (default 20) */
   int kernel;        /* apply kernel of the level operators: TP_KERNEL_CUDA_CORE (default) or
-                        TP_KERNEL_TENSOR (FP32/FP16/BF16 vectors, k = 2, 3; otherwise CUDA-core) */
+                        TP_KERNEL_TENSOR (FP32/FP16/BF16 vectors, k = 2, 3; otherwise CUDA-core);
+                        TP_KERNEL_PATCH is rejected (TP_ERR_UNSUPPORTED) */
   int ec;            /* tensor kernel with Algorithm 1 error correction */
   int tc_type;       /* tensor operand type: TP_FP16 (default) or TP_BF16 */
   int smoother;      /* TP_SMOOTHER_CHEBYSHEV (default) or TP_SMOOTHER_VERTEX_PATCH */

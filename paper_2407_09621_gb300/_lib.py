@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID_ARG", 2: "TP_ERR_CUDA", 3: "TP_ER
                 7: "TP_ERR_UNSUPPORTED"}
 TP_FP64, TP_FP32, TP_FP16, TP_BF16 = 0, 1, 2, 3
 TP_PENALTY_CONFIG, TP_PENALTY_PAPER = 0, 1
-TP_KERNEL_AUTO, TP_KERNEL_CUDA_CORE, TP_KERNEL_TENSOR = 0, 1, 2
+TP_KERNEL_AUTO, TP_KERNEL_CUDA_CORE, TP_KERNEL_TENSOR, TP_KERNEL_PATCH = 0, 1, 2, 3
 
 
 class TPError(RuntimeError):

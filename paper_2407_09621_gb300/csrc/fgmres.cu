@@ -181,7 +181,7 @@ cudaError_t norm_to_host(Ctx& c, const double* w, double* out) {
 
 // out = b - A x (one pass where the operator's kernel stores the residual form itself)
 cudaError_t residual64(Ctx& c, double* out, const double* b, const double* x) {
-  if (c.s->A->opts.kernel != TP_KERNEL_TENSOR) return launch_residual(c.s->A, out, b, x, c.st);
+  if (c.s->A->opts.kernel == TP_KERNEL_CUDA_CORE) return launch_residual(c.s->A, out, b, x, c.st);
   cudaError_t e = launch_apply(c.s->A, c.s->w, x, c.st);
   const double coef[2] = {1.0, -1.0};
   const double* v[2] = {b, c.s->w};

@@ -525,7 +525,7 @@ static cudaError_t sub_t(long long n, void* r, const void* b, const void* t, cud
 // difference pass
 static cudaError_t residual(const tp_mg_s* mg, const tp_mg_level& L, void* r, const void* b, const void* x, void* t,
                             cudaStream_t s) {
-  if (L.op->opts.kernel != TP_KERNEL_TENSOR) return launch_residual(L.op, r, b, x, s);
+  if (L.op->opts.kernel == TP_KERNEL_CUDA_CORE) return launch_residual(L.op, r, b, x, s);
   cudaError_t e = launch_apply(L.op, t, x, s);
   if (e != cudaSuccess) return e;
   TP_DISPATCH_PREC(mg->prec, return sub_t<T>(L.ndofs, r, b, t, s))
@@ -708,6 +708,10 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   if (o.smoother != TP_SMOOTHER_CHEBYSHEV && o.smoother != TP_SMOOTHER_VERTEX_PATCH) {
     set_error("tp_mg_create: smoother must be TP_SMOOTHER_CHEBYSHEV or TP_SMOOTHER_VERTEX_PATCH");
     return TP_ERR_INVALID_ARG;
+  }
+  if (o.kernel == TP_KERNEL_PATCH) {
+    set_error("tp_mg_create: the level operators take the CUDA-core or tensor kernels, not the patch-wise one");
+    return TP_ERR_UNSUPPORTED;
   }
   if (o.smoother == TP_SMOOTHER_VERTEX_PATCH && o.precision != TP_FP64 && o.precision != TP_FP32) {
     set_error("tp_mg_create: the vertex-patch smoother takes FP64 or FP32 multigrid vectors");

@@ -40,9 +40,12 @@ cudaError_t prepare_apply_dmma(const tp_op_s* op);
 cudaError_t launch_apply_dmma(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 cudaError_t prepare_apply_umma(tp_op_s* op);
 cudaError_t launch_apply_umma(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
+tp_status prepare_apply_patch(tp_op_s* op);
+cudaError_t launch_apply_patch(const tp_op_s* op, void* y, const void* x, cudaStream_t s);
 
 // the apply kernel family chosen at creation
 cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
+  if (op->opts.kernel == TP_KERNEL_PATCH) return launch_apply_patch(op, y, x, s);
   if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc(op, y, x, s);
   if (op->prec == TP_FP64) return launch_apply_dmma(op, y, x, s);
   return op->use_umma ? launch_apply_umma(op, y, x, s) : launch_apply_tc(op, y, x, s);
@@ -51,7 +54,7 @@ cudaError_t launch_apply(const tp_op_s* op, void* y, const void* x, cudaStream_t
 // r = b - A x in one pass where the CUDA-core kernel runs (its store takes b); other kernel
 // families return cudaErrorNotSupported and the caller forms A x and the difference.
 cudaError_t launch_residual(const tp_op_s* op, void* r, const void* b, const void* x, cudaStream_t s) {
-  if (op->opts.kernel != TP_KERNEL_TENSOR) return launch_apply_cc_range(op, r, x, 0, op->ncells, s, b);
+  if (op->opts.kernel == TP_KERNEL_CUDA_CORE) return launch_apply_cc_range(op, r, x, 0, op->ncells, s, b);
   return cudaErrorNotSupported;
 }
 
@@ -68,6 +71,7 @@ size_t elem_bytes(tp_precision p);
 static tp_status autotune_apply(tp_op_s* op) {
   const bool dm = op->opts.kernel == TP_KERNEL_TENSOR && op->prec == TP_FP64;
   if (op->opts.kernel == TP_KERNEL_TENSOR && !dm) return TP_OK;  // tcgen05 / mma.sync: fixed tiles
+  if (op->opts.kernel == TP_KERNEL_PATCH) return TP_OK;           // one patch per thread block
   if (op->n > kMaxN) return TP_OK;                                 // n > 8: one tile shape
   const long long eb = (long long)elem_bytes(op->prec);
   const long long n3 = (long long)op->n * op->n * op->n;
@@ -370,7 +374,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: unknown penalty mode %d", o.penalty);
     return TP_ERR_INVALID_ARG;
   }
-  if (o.kernel < TP_KERNEL_AUTO || o.kernel > TP_KERNEL_TENSOR) {
+  if (o.kernel < TP_KERNEL_AUTO || o.kernel > TP_KERNEL_PATCH) {
     set_error("tp_dg_laplace_create: unknown kernel family %d", o.kernel);
     return TP_ERR_INVALID_ARG;
   }
@@ -416,6 +420,16 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: error correction needs the tensor kernel");
     return TP_ERR_UNSUPPORTED;
   }
+  if (o.kernel == TP_KERNEL_PATCH) {
+    if ((p != TP_FP64 && p != TP_FP32) || k > kMaxN - 1) {
+      set_error("tp_dg_laplace_create: the patch-wise kernel takes FP64 or FP32 vectors and k <= %d", kMaxN - 1);
+      return TP_ERR_UNSUPPORTED;
+    }
+    if (m->nx < 2 || m->ny < 2 || m->nz < 2) {
+      set_error("tp_dg_laplace_create: the patch-wise kernel needs at least two cells per direction");
+      return TP_ERR_UNSUPPORTED;
+    }
+  }
   if (k + 1 > kMaxN && (o.kernel == TP_KERNEL_TENSOR || (p != TP_FP64 && p != TP_FP32))) {
     set_error("tp_dg_laplace_create: degrees above %d need the CUDA-core kernel and FP64 or FP32 vectors", kMaxN - 1);
     return TP_ERR_UNSUPPORTED;
@@ -443,8 +457,11 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     fill_const(op->c64, op);
     fill_const(op->c32, op);
   }
-  st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
-                   "apply kernel set-up");
+  if (op->opts.kernel == TP_KERNEL_PATCH)
+    st = prepare_apply_patch(op);
+  else
+    st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
+                     "apply kernel set-up");
   if (st == TP_OK && o.autotune) st = autotune_apply(op);
   if (st != TP_OK) {
     tp_op_destroy(op);
@@ -465,14 +482,15 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->elem_bytes = elem_bytes(op->prec);
   // the CUDA-core kernel takes the even-odd path (the DMMA and tensor kernels do not)
   const int centro = op->n > kMaxN ? op->c64h.centro : op->c64.centro;
-  const bool eo = op->opts.kernel != TP_KERNEL_TENSOR && op->n >= 5 && centro;
-  info->flops_per_dof = apply_flops_per_dof(op->n, eo);
+  const bool eo = op->opts.kernel == TP_KERNEL_CUDA_CORE && op->n >= 5 && centro;
+  info->flops_per_dof = op->opts.kernel == TP_KERNEL_PATCH ? 224.0 * op->n + 8.0 : apply_flops_per_dof(op->n, eo);
   info->tensor_path = op->opts.kernel != TP_KERNEL_TENSOR ? 0 : (op->prec == TP_FP64 ? 3 : (op->use_umma ? 2 : 1));
   // FP32 vectors on the half-precision tensor paths: FP32 accuracy (1e-5 per apply) only with FP16
   // operands and both operands refined (Algorithm 1, ec = 1)
   info->approximate = op->prec == TP_FP32 && op->opts.kernel == TP_KERNEL_TENSOR &&
                       !(op->opts.tc_type == TP_FP16 && op->opts.ec == 1);
-  info->tile_cells = info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)
+  info->tile_cells = op->opts.kernel == TP_KERNEL_PATCH ? 8
+                     : info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 3 ? dmma_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 2 ? 128 : 0;
   return TP_OK;
@@ -500,6 +518,7 @@ tp_status tp_op_destroy(tp_op op) {
   if (op->tc_mats) cudaFree(op->tc_mats);
   if (op->umma_mats) cudaFree(op->umma_mats);
   if (op->umma_err) cudaFree(op->umma_err);
+  if (op->pw_mats) cudaFree(op->pw_mats);
   delete op;
   return TP_OK;
 }
@@ -551,7 +570,7 @@ tp_status tp_apply_host(tp_op op, void* y_host, const void* x_host, void* stream
     op->hbytes = bytes;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  const bool ranged = op->opts.kernel != TP_KERNEL_TENSOR || op->prec == TP_FP64;
+  const bool ranged = op->opts.kernel == TP_KERNEL_CUDA_CORE || (op->opts.kernel == TP_KERNEL_TENSOR && op->prec == TP_FP64);
   if (ranged && op->mesh.nz >= kMinChunks) return apply_host_pipelined(op, y_host, x_host, s);
   tp_status st = cuda_status(cudaMemcpyAsync(op->hx, x_host, bytes, cudaMemcpyHostToDevice, s), "tp_apply_host H2D");
   if (st == TP_OK) st = cuda_status(launch_apply(op, op->hy, op->hx, s), "tp_apply_host launch");

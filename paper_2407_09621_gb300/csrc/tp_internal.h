@@ -103,6 +103,7 @@ struct tp_op_s {
   bool use_umma = false;        // tensor kernel runs on tcgen05 (k = 3, FP16/BF16 vectors)
   void* umma_mats = nullptr;    // its seven block matrices (and low parts) on the device
   int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)
+  void* pw_mats = nullptr;      // patch-wise kernel: its 3 x 4 pairs of 1D patch factors (device)
   tp::UmmaParams umma_params;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
   const void* hconst_high(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64h : (const void*)&c32h; }

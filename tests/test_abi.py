@@ -56,6 +56,21 @@ def test_operator_argument_validation():
             with pytest.raises(_lib.TPError) as e:
                 _lib.tp_dg_laplace_create(m, k, p, kernel=kern)
             assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+        # patch-wise kernel: FP64/FP32, k <= 7, at least two cells per direction (checked before any CUDA call)
+        for k, p in ((3, _lib.TP_FP16), (2, _lib.TP_BF16), (8, _lib.TP_FP64)):
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_dg_laplace_create(m, k, p, kernel=_lib.TP_KERNEL_PATCH)
+            assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+        thin = _lib.tp_mesh_create(3, 1, 4)
+        try:
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_dg_laplace_create(thin, 3, _lib.TP_FP64, kernel=_lib.TP_KERNEL_PATCH)
+            assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+        finally:
+            _lib.tp_mesh_destroy(thin)
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_dg_laplace_create(m, 3, _lib.TP_FP64, kernel=4)
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
         with pytest.raises(_lib.TPError) as e:
             _lib.tp_dg_laplace_create(m, 3, 9)
         assert e.value.status == _lib.TP_ERR_INVALID_ARG
