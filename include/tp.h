@@ -50,8 +50,7 @@ typedef enum { TP_PENALTY_CONFIG = 0, TP_PENALTY_PAPER = 1 } tp_penalty;
 
 /* Kernel family for tp_apply. AUTO picks, per precision and degree, the family
  * that measured fastest on GB300: the tcgen05 tensor kernel for FP16/BF16
- * vectors at k = 3 (on meshes whose cell count plus one xy-slab stays below
- * 2^31), the CUDA-core kernel otherwise (FP64: the DFMA kernel beats DMMA,
+ * vectors at k = 3, the CUDA-core kernel otherwise (FP64: the DFMA kernel beats DMMA,
  * which shares the FP64 pipe; FP32: the CUDA-core kernel beats mma.sync).
  * CUDA_CORE forces the FMA-pipe sum-factorization kernel (the paper's CUDA-core
  * comparator, App. A); TENSOR forces the tensor-core kernel. PATCH evaluates the
@@ -87,9 +86,10 @@ typedef struct {
  * Blackwell tensor cores (tcgen05.mma, operands staged by TMA, FP32 accumulators in
  * TMEM): each cell row of the output is the sum of seven dense 64 x 64 blocks of
  * Eq. (2)/(9) (the interior diagonal block and one per face neighbour) applied to
- * the cell's and its six neighbours' coefficients, boundary faces through a ghost
- * row; with ec = 1 (always for BF16) the blocks are split as in Algorithm 1 into
- * a second accumulator. Otherwise `mma.sync` m16n8k16 with FP32 accumulation for
+ * the cell's and its six neighbours' coefficients (zero outside the mesh), and a
+ * second launch adds the rank-2 boundary-face corrections of boundary cells on
+ * the FMA pipes in FP32 (so boundary entries are rounded to the storage type
+ * twice); with ec = 1 (always for BF16) the blocks are split as in Algorithm 1. Otherwise `mma.sync` m16n8k16 with FP32 accumulation for
  * degrees k = 2, 3 (n <= 4, cells padded to 4^3): per cell W = K3 u with
  * K3 = G_z(+)G_y(+)G_x and V = (M_z(x)M_y(x)M_x) W as dense 64 x 64 products, the
  * rank-2 face terms added to W on the FMA pipes in FP32 between them. Vectors may

@@ -6,26 +6,25 @@
 // and one block per face neighbour, e.g. A_{c,c+x} = M_z(x)M_y(x)L^{c,c+1}_x. So
 //   v_c = sum over the seven blocks b of A_b u_{nb_b(c)},
 // a GEMM whose rows are cells: D (cells x 64) = sum_b U_b (cells x 64) A_b^T, each U_b the input
-// tile shifted by the neighbour's cell offset (+-1, +-nx, +-nx*ny). The cell-major layout makes
-// every U_b a plain 128-byte-per-row tile that TMA loads directly (rows outside the mesh are
-// zero-filled). A boundary face is handled with a ghost neighbour: the missing neighbour's row is
-// replaced by a line-wise linear map of the cell's own row (two nonzero layers along the normal),
-// chosen so that A_{c,nb} ghost = (boundary-face term - interior-face term) of the diagonal:
-//   high side: w_0 = -u_{n-1},  w_1 = (d1.u + (2 g h) u_{n-1} + d0[0] u_{n-1}) / d0[1]
-//   low side:  w_{n-1} = -u_0,  w_{n-2} = (d0.u - (2 g h) u_0 + d1[n-1] u_0) / d1[n-2]
-// (g the penalty, h the cell width, d0/d1 the basis derivatives at the ends). Every cell then
-// uses the same seven blocks.
+// tile shifted by the neighbour's cell offset. A tile is a 3D box of BX x BY x BZ = 128 cells of
+// the mesh (the shape that wastes the fewest cells on the mesh's edges), loaded by TMA through a
+// 4D tensor map over (64 values, nx, ny, nz): each of the seven input tiles is the same box shifted
+// by one cell along one axis, one 128-byte row per cell, and cells outside the mesh arrive as
+// zeros. A missing neighbour therefore contributes nothing, and every cell is first computed with
+// the interior diagonal block. A boundary cell differs from that only by its boundary faces: the
+// 1D block of a cell on the low (high) end of direction d is L + dL_0 (L + dL_1) with the rank-2
+//   dL_0 = (v0 d0^T + d0 v0^T)/(2h),  dL_1 = -(v1 d1^T + d1 v1^T)/(2h),
+// so a second, small kernel adds (M (x) M (x) dL) u_c for each boundary face of each boundary
+// cell on the FMA pipes (rank 2 along the normal, the mass tensor along the two tangents).
 //
-// One CTA per SM, persistent over tiles of 128 cells, warp-specialized so that loads, products
-// and stores of consecutive tiles overlap:
+// One CTA per SM, persistent over tiles, warp-specialized so that loads, products and stores of
+// consecutive tiles overlap:
 //   warp 0      TMA producer: streams the seven input tiles of every output tile through a ring
-//               of 16 KB shared-memory slots (zero fill outside the mesh);
+//               of 16 KB shared-memory slots;
 //   warp 1      MMA issuer: per slot four tcgen05.mma (M = 128, N = 64, K = 16) into one of two
 //               TMEM accumulators, then tcgen05.commit releases the slot;
-//   warps 2-5   ghost patches: for tiles that hold boundary cells, read the own tile's rows and
-//               write the ghost rows into the neighbour slots before the MMA reads them;
-//   warps 6-9   epilogue: tcgen05.ld of the finished accumulator (one cell row per thread),
-//               scale, round to the storage type and store.
+//   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one cell row per thread),
+//               scale, round to the storage type and store the rows of cells inside the mesh.
 // Algorithm 1 error correction splits each block matrix into a high part and the rounded
 // remainder; both products accumulate into the same FP32 accumulator. The input vector is
 // already in the operand type, so only the matrix needs the split (two products instead of
@@ -56,7 +55,7 @@ namespace umma {
 constexpr int kRows = 128;            // cells per tile (UMMA M)
 constexpr int kTileBytes = kRows * 128;
 constexpr int kMatBytes = 64 * 128;   // one 64 x 64 16-bit block matrix
-constexpr int kThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-5 patches, warps 6-9 epilogue
+constexpr int kThreads = 192;         // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kWaitLimit = 1 << 22;
 
 using Params = UmmaParams;
@@ -68,7 +67,7 @@ template <bool EC>
 __host__ __device__ constexpr int nslots() { return EC ? 7 : 10; }
 template <bool EC>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kTileBytes + 8 * (3 * nslots<EC>() + 5) + 16;
+  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kTileBytes + 8 * (2 * nslots<EC>() + 5) + 16;
 }
 
 __device__ __forceinline__ uint32_t s2u(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -165,60 +164,15 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return
                  "=r"(r[base + 28]), "=r"(r[base + 29]), "=r"(r[base + 30]), "=r"(r[base + 31])          \
                : "r"(ta))
 
-// Ghost row for direction d and side (1 = high, 0 = low) from the own row u (64 values, index
-// (l*4 + j)*4 + i), written into the swizzled tile row r.
-template <typename TO>
-__device__ __forceinline__ void write_ghost(unsigned char* tile, int r, const float (&u)[64], int d, int side,
-                                            const Params& P) {
-  float w[64];
-#pragma unroll
-  for (int e = 0; e < 64; ++e) w[e] = 0.f;
-  const int stride = d == 0 ? 1 : (d == 1 ? 4 : 16);
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      // line start for tangential indices (a, b)
-      const int s0 = d == 0 ? (a * 16 + b * 4) : (d == 1 ? (a * 16 + b) : (a * 4 + b));
-      if (side) {
-        float t = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) t = fmaf(P.gh[d][m], u[s0 + m * stride], t);
-        w[s0] = -u[s0 + 3 * stride];
-        w[s0 + stride] = t;
-      } else {
-        float t = 0.f;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) t = fmaf(P.gl[d][m], u[s0 + m * stride], t);
-        w[s0 + 3 * stride] = -u[s0];
-        w[s0 + 2 * stride] = t;
-      }
-    }
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    uint4 v;
-    TO* h = reinterpret_cast<TO*>(&v);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(w[c * 8 + q]);
-    *reinterpret_cast<uint4*>(tile + sw_off(r, c)) = v;
-  }
-}
-
-// Which of the seven input tiles of the tile starting at cell c0 need ghost patches: bit b
-// (1..6 = x-, x+, y-, y+, z-, z+) if a cell of the tile lies on that side of the mesh, bit 0 if
-// any does (the patch warps then also read the own tile).
-__device__ __forceinline__ uint32_t tile_bmask(long long c0, const Params& P) {
-  const long long c1 = (c0 + kRows < P.ncells ? c0 + kRows : P.ncells) - 1;
-  const long long nx = P.nx, ny = P.ny, nxy = nx * ny;
-  uint32_t m = 0;
-  if ((c1 / nx) * nx >= c0) m |= 1u << 1;                 // cx == 0
-  if (((c1 + 1) / nx) * nx >= c0 + 1) m |= 1u << 2;       // cx == nx-1
-  const long long q0 = c0 / nx, q1 = c1 / nx;             // rows of cells along y (all slabs)
-  if ((q1 / ny) * ny >= q0) m |= 1u << 3;                 // cy == 0
-  if (((q1 + 1) / ny) * ny >= q0 + 1) m |= 1u << 4;       // cy == ny-1
-  if (c0 < nxy) m |= 1u << 5;                             // cz == 0
-  if (c1 >= (long long)(P.nz - 1) * nxy) m |= 1u << 6;    // cz == nz-1
-  return m ? (m | 1u) : 0u;
+// Cell of row r of tile t (x fastest within the box, boxes x fastest over the mesh); false if the
+// cell lies outside the mesh (a partial box on the mesh's far edges).
+__device__ __forceinline__ bool tile_cell(long long t, int r, const Params& P, long long& cell) {
+  const int tx = (int)(t % P.tiles[0]), ty = (int)((t / P.tiles[0]) % P.tiles[1]);
+  const int tz = (int)(t / ((long long)P.tiles[0] * P.tiles[1]));
+  const int cx = tx * P.box[0] + r % P.box[0], cy = ty * P.box[1] + (r / P.box[0]) % P.box[1];
+  const int cz = tz * P.box[2] + r / (P.box[0] * P.box[1]);
+  cell = ((long long)cz * P.ny + cy) * P.nx + cx;
+  return cx < P.nx && cy < P.ny && cz < P.nz;
 }
 
 template <typename TO, bool EC>
@@ -231,23 +185,21 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   unsigned char* sB = base;                      // NMAT block matrices, [out n][in k], swizzled
   unsigned char* sA = base + NMAT * kMatBytes;   // S input-tile slots
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kTileBytes);
-  // full[S] (TMA landed), ready[S] (ghost rows written), empty[S] (MMAs done with the slot),
-  // accf[2] (accumulator complete), acce[2] (accumulator read), drain
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 * S + 5);
+  // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[2] (accumulator complete),
+  // acce[2] (accumulator read), drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar0 = s2u(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
-  auto ready = [&](int s) { return bar0 + 8u * (S + s); };
-  auto empty = [&](int s) { return bar0 + 8u * (2 * S + s); };
-  auto accf = [&](int a) { return bar0 + 8u * (3 * S + a); };
-  auto acce = [&](int a) { return bar0 + 8u * (3 * S + 2 + a); };
-  const uint32_t drain = bar0 + 8u * (3 * S + 4);
+  auto empty = [&](int s) { return bar0 + 8u * (S + s); };
+  auto accf = [&](int a) { return bar0 + 8u * (2 * S + a); };
+  auto acce = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
+  const uint32_t drain = bar0 + 8u * (2 * S + 4);
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(ready(s)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
     }
     for (int a = 0; a < 2; ++a) {
@@ -272,17 +224,18 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const long long ntiles = (P.ncells + kRows - 1) / kRows;
-  const long long sy = P.nx, sz = (long long)P.nx * P.ny;
+  const long long ntiles = (long long)P.tiles[0] * P.tiles[1] * P.tiles[2];
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const long long offs[7] = {0, -1, 1, -sy, sy, -sz, sz};
+      const int offs[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
       int slot = 0;
       uint32_t ph = 0, issued = 0, iph = 0;  // per-slot: issued at least once, parity of the last issue
       bool ok = true;
       for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int cx = (int)(t % P.tiles[0]) * P.box[0], cy = (int)((t / P.tiles[0]) % P.tiles[1]) * P.box[1];
+        const int cz = (int)(t / ((long long)P.tiles[0] * P.tiles[1])) * P.box[2];
         for (int b = 0; b < 7; ++b) {
           if (!(ok = wait_bar(empty(slot), ph ^ 1u, abort, err, 1, P.wait_ns))) break;
           if (P.test_withhold && blockIdx.x == 0 && t == 0 && b == 0) {
@@ -292,10 +245,11 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
           }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(slot)), "r"(kTileBytes)
                        : "memory");
-          const int row = (int)(t * kRows + offs[b]);  // may be negative or past the end: zero fill
+          // the box may start one cell outside the mesh: those cells arrive as zeros
           asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-              ::"r"(s2u(sA + slot * kTileBytes)), "l"((uint64_t)&tmx), "r"(0), "r"(row), "r"(full(slot))
+              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+              ::"r"(s2u(sA + slot * kTileBytes)), "l"((uint64_t)&tmx), "r"(0), "r"(cx + offs[b][0]),
+                "r"(cy + offs[b][1]), "r"(cz + offs[b][2]), "r"(full(slot))
               : "memory");
           issued |= 1u << slot;
           iph = (iph & ~(1u << slot)) | (ph << slot);
@@ -313,22 +267,15 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       // D F32, A/B F16 (0) or BF16 (1), both K-major, N = 64, M = 128
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
       int slot = 0, it = 0;
-      uint32_t ph = 0, rdy = 0;  // rdy: per-slot parity of the ready barriers (used only when patched)
+      uint32_t ph = 0;
       bool ok = true;
       for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
         const int a = it & 1;
         if (!(ok = wait_bar(acce(a), ((it >> 1) & 1) ^ 1u, abort, err, 2, P.wait_ns))) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t bm = tile_bmask(t * kRows, P);
         const uint32_t dt = tmem + 64u * a;
         for (int b = 0; b < 7; ++b) {
-          if (bm >> b & 1u) {
-            ok = wait_bar(ready(slot), (rdy >> slot) & 1u, abort, err, 3, P.wait_ns);
-            rdy ^= 1u << slot;
-          } else {
-            ok = wait_bar(full(slot), ph, abort, err, 3, P.wait_ns);
-          }
-          if (!ok) break;
+          if (!(ok = wait_bar(full(slot), ph, abort, err, 3, P.wait_ns))) break;
           asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks) {
@@ -356,53 +303,6 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
                    : "memory");
       drain_bar(drain, 0, err, 6);
     }
-  } else if (warp < 6) {
-    // ---------------------------------------------------------------- ghost patches
-    const int row = tid - 64;
-    int slot = 0;
-    uint32_t ph = 0;
-    bool ok = true;
-    for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const uint32_t bm = tile_bmask(t * kRows, P);
-      if (!bm) {
-        slot += 7;
-        while (slot >= S) { slot -= S; ph ^= 1u; }
-        continue;
-      }
-      const long long cell = t * kRows + row;
-      bool bnd[6] = {false, false, false, false, false, false};
-      if (cell < P.ncells) {
-        const int cx = (int)(cell % P.nx), cy = (int)((cell / P.nx) % P.ny), cz = (int)(cell / sz);
-        bnd[0] = cx == 0; bnd[1] = cx == P.nx - 1;
-        bnd[2] = cy == 0; bnd[3] = cy == P.ny - 1;
-        bnd[4] = cz == 0; bnd[5] = cz == P.nz - 1;
-      }
-      const bool any = bnd[0] | bnd[1] | bnd[2] | bnd[3] | bnd[4] | bnd[5];
-      float u[64];
-      if (!(ok = wait_bar(full(slot), ph, abort, err, 4, P.wait_ns))) break;
-      if (any) {
-        const unsigned char* own = sA + slot * kTileBytes;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint4 v = *reinterpret_cast<const uint4*>(own + sw_off(row, c));
-          const TO* h = reinterpret_cast<const TO*>(&v);
-#pragma unroll
-          for (int q = 0; q < 8; ++q) u[c * 8 + q] = to_f<TO>(h[q]);
-        }
-      }
-      arrive(ready(slot));
-      if (++slot == S) { slot = 0; ph ^= 1u; }
-#pragma unroll
-      for (int b = 1; b < 7; ++b) {
-        if (bm >> b & 1u) {
-          if (!(ok = wait_bar(full(slot), ph, abort, err, 4, P.wait_ns))) break;
-          if (bnd[b - 1]) write_ghost<TO>(sA + slot * kTileBytes, row, u, (b - 1) >> 1, (b - 1) & 1, P);
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          arrive(ready(slot));
-        }
-        if (++slot == S) { slot = 0; ph ^= 1u; }
-      }
-    }
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q4 = warp & 3;  // this warp may read TMEM lanes 32*q4 .. 32*q4+31
@@ -420,8 +320,8 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       arrive(acce(a));
-      const long long cell = t * kRows + row;
-      if (cell < P.ncells) {
+      long long cell;
+      if (tile_cell(t, row, P, cell)) {
         uint4* dst = reinterpret_cast<uint4*>(y + cell * 64);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -439,6 +339,82 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128));
   }
+}
+
+// Boundary-face corrections (FP32 arithmetic): one block of 64 threads per cell of the six boundary
+// faces, enumerated face by face (x-, x+, y-, y+, z-, z+); a cell on several faces is handled by
+// the block of the first of them, which adds the corrections of all its faces. For direction d
+// with normal index nrm and tangential indices (t1, t2) of a node, face side 0 and 1:
+//   S_a[t1, t2] = beta . u(t1, t2, :),  S_b[t1, t2] = u(t1, t2, end)   (beta = d0, end 0 / d1, end 3)
+//   y(nrm, t1, t2) += s hh (e_end[nrm] (M_t1 (x) M_t2) S_a + beta[nrm] (M_t1 (x) M_t2) S_b),  s = +1 / -1.
+template <typename TO>
+__global__ void __launch_bounds__(64) umma_fix_kernel(TO* __restrict__ y, const TO* __restrict__ x,
+                                                      const __grid_constant__ UmmaFixParams F) {
+  const int tid = threadIdx.x;
+  const long long fx = (long long)F.ny * F.nz, fy = (long long)F.nx * F.nz, fz = (long long)F.nx * F.ny;
+  long long b = blockIdx.x;
+  int f, cx, cy, cz;
+  if (b < 2 * fx) {
+    f = (int)(b / fx);
+    const long long i = b % fx;
+    cx = f ? F.nx - 1 : 0; cy = (int)(i % F.ny); cz = (int)(i / F.ny);
+  } else if ((b -= 2 * fx) < 2 * fy) {
+    f = 2 + (int)(b / fy);
+    const long long i = b % fy;
+    cy = f == 3 ? F.ny - 1 : 0; cx = (int)(i % F.nx); cz = (int)(i / F.nx);
+  } else {
+    b -= 2 * fy;
+    f = 4 + (int)(b / fz);
+    const long long i = b % fz;
+    cz = f == 5 ? F.nz - 1 : 0; cx = (int)(i % F.nx); cy = (int)(i / F.nx);
+  }
+  const bool on[6] = {cx == 0, cx == F.nx - 1, cy == 0, cy == F.ny - 1, cz == 0, cz == F.nz - 1};
+  for (int g = 0; g < f; ++g)
+    if (on[g]) return;  // block-uniform: an earlier face's block owns this cell
+  __shared__ float u[64];
+  __shared__ float Sab[2][16];
+  const long long cell = ((long long)cz * F.ny + cy) * F.nx + cx;
+  u[tid] = to_f<TO>(x[cell * 64 + tid]);
+  __syncthreads();
+  const int l = tid >> 4, j = (tid >> 2) & 3, i = tid & 3;
+  float acc = 0.f;
+  for (int g = f; g < 6; ++g) {
+    if (!on[g]) continue;
+    const int d = g >> 1, side = g & 1, end = side ? 3 : 0;
+    const float* beta = side ? F.d1 : F.d0;
+    if (tid < 16) {
+      const int t1 = tid >> 2, t2 = tid & 3;
+      float sa = 0.f;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int node = d == 0 ? (t1 * 4 + t2) * 4 + m : (d == 1 ? (t1 * 4 + m) * 4 + t2 : (m * 4 + t1) * 4 + t2);
+        sa = fmaf(beta[m], u[node], sa);
+      }
+      const int nend = d == 0 ? (t1 * 4 + t2) * 4 + end : (d == 1 ? (t1 * 4 + end) * 4 + t2 : (end * 4 + t1) * 4 + t2);
+      Sab[0][tid] = sa;
+      Sab[1][tid] = u[nend];
+    }
+    __syncthreads();
+    // this thread's node as (normal, tangent 1, tangent 2) and the tangential mass matrices
+    const int nrm = d == 0 ? i : (d == 1 ? j : l);
+    const int t1 = d == 2 ? j : l, t2 = d == 0 ? j : i;
+    const float* M1 = F.M[d == 2 ? 1 : 2];
+    const float* M2 = F.M[d == 0 ? 1 : 0];
+    float wa = 0.f, wb = 0.f;
+#pragma unroll
+    for (int b1 = 0; b1 < 4; ++b1)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2) {
+        const float m = M1[t1 * 4 + b1] * M2[t2 * 4 + b2];
+        wa = fmaf(m, Sab[0][b1 * 4 + b2], wa);
+        wb = fmaf(m, Sab[1][b1 * 4 + b2], wb);
+      }
+    const float sg = side ? -F.hh[d] : F.hh[d];
+    acc = fmaf(sg, (nrm == end ? wa : 0.f) + beta[nrm] * wb, acc);
+    __syncthreads();
+  }
+  const long long g = cell * 64 + tid;
+  y[g] = from_f<TO>(to_f<TO>(y[g]) + acc);
 }
 
 }  // namespace umma
@@ -503,6 +479,8 @@ static std::vector<double> umma_blocks(const tp_op_s* op) {
   return B;
 }
 
+static void umma_box(int nx, int ny, int nz, int box[3], int tiles[3]);
+
 template <typename TO, bool EC>
 static cudaError_t umma_prepare_t(tp_op_s* op) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
@@ -534,15 +512,18 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   P.lo_scale = 1.0f;
   P.wait_ns = 1000000000ull;
   P.test_withhold = 0;
-  const Ref1D& R = op->ref;
+  umma_box(op->mesh.nx, op->mesh.ny, op->mesh.nz, P.box, P.tiles);
+  UmmaFixParams& F = op->umma_fix;
+  memset(&F, 0, sizeof(F));
   for (int d = 0; d < 3; ++d) {
-    const double g2h = 2.0 * op->dir[d].gamma * op->dir[d].h;
-    for (int m = 0; m < 4; ++m) {
-      const double e3 = m == 3, e0 = m == 0;
-      P.gh[d][m] = (float)((R.d1[m] + g2h * e3 + R.d0[0] * e3) / R.d0[1]);
-      P.gl[d][m] = (float)((R.d0[m] - g2h * e0 + R.d1[3] * e0) / R.d1[2]);
-    }
+    for (int e = 0; e < 16; ++e) F.M[d][e] = (float)op->dir[d].M[e];
+    F.hh[d] = (float)(0.5 / op->dir[d].h);
   }
+  for (int m = 0; m < 4; ++m) {
+    F.d0[m] = (float)op->ref.d0[m];
+    F.d1[m] = (float)op->ref.d1[m];
+  }
+  F.nx = op->mesh.nx; F.ny = op->mesh.ny; F.nz = op->mesh.nz;
   int sms = 0;
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->device);
   if (err != cudaSuccess) return err;
@@ -551,31 +532,56 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
                               (int)umma::smem_bytes<EC>());
 }
 
+// Tile shape: the box of 128 cells (powers of two along x, y, z) that pads the mesh the least,
+// the longest x extent among equals (contiguous rows for the copies and the stores).
+static void umma_box(int nx, int ny, int nz, int box[3], int tiles[3]) {
+  long long best = -1;
+  for (int bx = 1; bx <= 128; bx *= 2)
+    for (int by = 1; bx * by <= 128; by *= 2) {
+      const int bz = 128 / (bx * by);
+      const long long tx = (nx + bx - 1) / bx, ty = (ny + by - 1) / by, tz = (nz + bz - 1) / bz;
+      const long long cost = tx * ty * tz;
+      if (best < 0 || cost < best || (cost == best && bx > box[0])) {
+        best = cost;
+        box[0] = bx; box[1] = by; box[2] = bz;
+        tiles[0] = (int)tx; tiles[1] = (int)ty; tiles[2] = (int)tz;
+      }
+    }
+}
+
 template <typename TO, bool EC>
 static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cudaStream_t s) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
+  const umma::Params& P = op->umma_params;
   CUtensorMap tm;
-  cuuint64_t dims[2] = {64, (cuuint64_t)op->ncells};
-  cuuint64_t strides[1] = {128};
-  cuuint32_t box[2] = {64, (cuuint32_t)umma::kRows}, estr[2] = {1, 1};
+  // (64 values, nx, ny, nz) with boxes of (64, BX, BY, BZ): one 128-byte row per cell
+  cuuint64_t dims[4] = {64, (cuuint64_t)op->mesh.nx, (cuuint64_t)op->mesh.ny, (cuuint64_t)op->mesh.nz};
+  cuuint64_t strides[3] = {128, 128ull * op->mesh.nx, 128ull * op->mesh.nx * op->mesh.ny};
+  cuuint32_t box[4] = {64, (cuuint32_t)P.box[0], (cuuint32_t)P.box[1], (cuuint32_t)P.box[2]};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       std::is_same<TO, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  if (enc(&tm, dt, 2, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  if (enc(&tm, dt, 4, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
       CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const long long tiles = (op->ncells + umma::kRows - 1) / umma::kRows;
+  const long long tiles = (long long)P.tiles[0] * P.tiles[1] * P.tiles[2];
   const int grid = (int)(tiles < op->sm_count ? tiles : op->sm_count);
   umma::apply_umma_kernel<TO, EC><<<grid, umma::kThreads, umma::smem_bytes<EC>(), s>>>(
-      tm, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), op->umma_params, op->umma_err);
+      tm, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P, op->umma_err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const UmmaFixParams& F = op->umma_fix;
+  const long long fix_blocks = 2 * ((long long)F.ny * F.nz + (long long)F.nx * F.nz + (long long)F.nx * F.ny);
+  if (fix_blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  umma::umma_fix_kernel<TO><<<(unsigned)fix_blocks, 64, 0, s>>>(static_cast<TO*>(y), static_cast<const TO*>(x), F);
   return cudaGetLastError();
 }
 
-// TMA row coordinates (cell index + neighbour offset) must fit in int32.
+// the tcgen05 apply: k = 3 with FP16/BF16 vectors (per-axis TMA coordinates are int32: any mesh)
 bool umma_supported(const tp_op_s* op) {
-  const long long reach = op->ncells + (long long)op->mesh.nx * op->mesh.ny + umma::kRows;
-  return op->n == 4 && (op->prec == TP_FP16 || op->prec == TP_BF16) && reach < (1LL << 31);
+  return op->n == 4 && (op->prec == TP_FP16 || op->prec == TP_BF16);
 }
 
 cudaError_t prepare_apply_umma(tp_op_s* op) {

@@ -389,12 +389,10 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   const long long ncells = (long long)m->nx * m->ny * m->nz;
   if (o.kernel == TP_KERNEL_AUTO) {
     // The fastest family measured on GB300 for each precision: FP16/BF16 vectors at k = 3 run on
-    // tcgen05 (386 / 301 GDoF/s at 128^3 cells against 230 / 223 on the CUDA-core kernel), where its
-    // TMA row coordinates fit in int32; FP64 stays on DFMA (DMMA shares the FP64 pipe and is slower)
-    // and FP32 on the CUDA-core kernel (the mma.sync path is slower); everything else is CUDA-core.
-    const long long reach = ncells + (long long)m->nx * m->ny + 128;
-    o.kernel = ((p == TP_FP16 || p == TP_BF16) && k == 3 && reach < (1LL << 31)) ? TP_KERNEL_TENSOR
-                                                                                 : TP_KERNEL_CUDA_CORE;
+    // tcgen05 (faster than the CUDA-core kernel at every measured size); FP64 stays on DFMA (DMMA
+    // shares the FP64 pipe and is slower) and FP32 on the CUDA-core kernel (the mma.sync path is
+    // slower); everything else is CUDA-core.
+    o.kernel = ((p == TP_FP16 || p == TP_BF16) && k == 3) ? TP_KERNEL_TENSOR : TP_KERNEL_CUDA_CORE;
   }
   if (o.kernel == TP_KERNEL_TENSOR && p == TP_FP64) {
     if (k != 3 && k != 7) {
