@@ -341,18 +341,24 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   }
 }
 
-// Boundary-face corrections (FP32 arithmetic): one block of 64 threads per cell of the six boundary
-// faces, enumerated face by face (x-, x+, y-, y+, z-, z+); a cell on several faces is handled by
-// the block of the first of them, which adds the corrections of all its faces. For direction d
-// with normal index nrm and tangential indices (t1, t2) of a node, face side 0 and 1:
-//   S_a[t1, t2] = beta . u(t1, t2, :),  S_b[t1, t2] = u(t1, t2, end)   (beta = d0, end 0 / d1, end 3)
-//   y(nrm, t1, t2) += s hh (e_end[nrm] (M_t1 (x) M_t2) S_a + beta[nrm] (M_t1 (x) M_t2) S_b),  s = +1 / -1.
+// Boundary-face corrections (FP32 arithmetic). The cells of the six boundary faces are enumerated
+// face by face (x-, x+, y-, y+, z-, z+), one 16-lane group per slot; a cell on several faces is
+// handled by the group of the first of them, which adds the corrections of all its faces one after
+// the other. For direction d lane a = (t1, t2) owns the cell's line along d at the tangential
+// indices (t1, t2), with side 0 (low) / 1 (high) of the face:
+//   S_a = beta . u(t1, t2, :),  S_b = u(t1, t2, end)        (beta = d0, end 0 / beta = d1, end 3)
+//   W = (M_t1 (x) M_t2) S  over the 16 lines (shuffles),
+//   y(t1, t2, m) += s hh (e_end[m] W_a + beta[m] W_b),  s = +1 / -1.
+constexpr int kFixCells = 8;  // 16-lane groups per block of 128 threads
+
 template <typename TO>
-__global__ void __launch_bounds__(64) umma_fix_kernel(TO* __restrict__ y, const TO* __restrict__ x,
-                                                      const __grid_constant__ UmmaFixParams F) {
-  const int tid = threadIdx.x;
+__global__ void __launch_bounds__(16 * kFixCells) umma_fix_kernel(TO* __restrict__ y, const TO* __restrict__ x,
+                                                                  const __grid_constant__ UmmaFixParams F) {
   const long long fx = (long long)F.ny * F.nz, fy = (long long)F.nx * F.nz, fz = (long long)F.nx * F.ny;
-  long long b = blockIdx.x;
+  long long b = (long long)blockIdx.x * kFixCells + (threadIdx.x >> 4);
+  if (b >= 2 * (fx + fy + fz)) return;  // group-uniform
+  const int lane = threadIdx.x & 15, t1 = lane >> 2, t2 = lane & 3;
+  const unsigned gmask = 0xffffu << (threadIdx.x & 16);  // the lanes of this group
   int f, cx, cy, cz;
   if (b < 2 * fx) {
     f = (int)(b / fx);
@@ -370,51 +376,40 @@ __global__ void __launch_bounds__(64) umma_fix_kernel(TO* __restrict__ y, const 
   }
   const bool on[6] = {cx == 0, cx == F.nx - 1, cy == 0, cy == F.ny - 1, cz == 0, cz == F.nz - 1};
   for (int g = 0; g < f; ++g)
-    if (on[g]) return;  // block-uniform: an earlier face's block owns this cell
-  __shared__ float u[64];
-  __shared__ float Sab[2][16];
-  const long long cell = ((long long)cz * F.ny + cy) * F.nx + cx;
-  u[tid] = to_f<TO>(x[cell * 64 + tid]);
-  __syncthreads();
-  const int l = tid >> 4, j = (tid >> 2) & 3, i = tid & 3;
-  float acc = 0.f;
+    if (on[g]) return;  // group-uniform: an earlier face's group owns this cell
+  const long long c64 = (((long long)cz * F.ny + cy) * F.nx + cx) * 64;
   for (int g = f; g < 6; ++g) {
     if (!on[g]) continue;
     const int d = g >> 1, side = g & 1, end = side ? 3 : 0;
     const float* beta = side ? F.d1 : F.d0;
-    if (tid < 16) {
-      const int t1 = tid >> 2, t2 = tid & 3;
-      float sa = 0.f;
+    // node of this lane's line at position m along d
+    auto node = [&](int m) { return d == 0 ? (t1 * 4 + t2) * 4 + m : (d == 1 ? (t1 * 4 + m) * 4 + t2 : (m * 4 + t1) * 4 + t2); };
+    float sa = 0.f, sb = 0.f;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int node = d == 0 ? (t1 * 4 + t2) * 4 + m : (d == 1 ? (t1 * 4 + m) * 4 + t2 : (m * 4 + t1) * 4 + t2);
-        sa = fmaf(beta[m], u[node], sa);
-      }
-      const int nend = d == 0 ? (t1 * 4 + t2) * 4 + end : (d == 1 ? (t1 * 4 + end) * 4 + t2 : (end * 4 + t1) * 4 + t2);
-      Sab[0][tid] = sa;
-      Sab[1][tid] = u[nend];
+    for (int m = 0; m < 4; ++m) {
+      const float v = to_f<TO>(x[c64 + node(m)]);
+      sa = fmaf(beta[m], v, sa);
+      if (m == end) sb = v;
     }
-    __syncthreads();
-    // this thread's node as (normal, tangent 1, tangent 2) and the tangential mass matrices
-    const int nrm = d == 0 ? i : (d == 1 ? j : l);
-    const int t1 = d == 2 ? j : l, t2 = d == 0 ? j : i;
+    // tangential mass: x-faces M_z (x) M_y, y-faces M_z (x) M_x, z-faces M_y (x) M_x
     const float* M1 = F.M[d == 2 ? 1 : 2];
     const float* M2 = F.M[d == 0 ? 1 : 0];
     float wa = 0.f, wb = 0.f;
 #pragma unroll
-    for (int b1 = 0; b1 < 4; ++b1)
-#pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2) {
-        const float m = M1[t1 * 4 + b1] * M2[t2 * 4 + b2];
-        wa = fmaf(m, Sab[0][b1 * 4 + b2], wa);
-        wb = fmaf(m, Sab[1][b1 * 4 + b2], wb);
-      }
+    for (int q = 0; q < 16; ++q) {
+      const float oa = __shfl_sync(gmask, sa, q, 16), ob = __shfl_sync(gmask, sb, q, 16);
+      const float w = M1[t1 * 4 + (q >> 2)] * M2[t2 * 4 + (q & 3)];
+      wa = fmaf(w, oa, wa);
+      wb = fmaf(w, ob, wb);
+    }
     const float sg = side ? -F.hh[d] : F.hh[d];
-    acc = fmaf(sg, (nrm == end ? wa : 0.f) + beta[nrm] * wb, acc);
-    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const long long gi = c64 + node(m);
+      y[gi] = from_f<TO>(to_f<TO>(y[gi]) + sg * ((m == end ? wa : 0.f) + beta[m] * wb));
+    }
+    __syncwarp(gmask);  // the next face of this cell reads what this one wrote
   }
-  const long long g = cell * 64 + tid;
-  y[g] = from_f<TO>(to_f<TO>(y[g]) + acc);
 }
 
 }  // namespace umma
@@ -573,9 +568,11 @@ static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cuda
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const UmmaFixParams& F = op->umma_fix;
-  const long long fix_blocks = 2 * ((long long)F.ny * F.nz + (long long)F.nx * F.nz + (long long)F.nx * F.ny);
+  const long long slots = 2 * ((long long)F.ny * F.nz + (long long)F.nx * F.nz + (long long)F.nx * F.ny);
+  const long long fix_blocks = (slots + umma::kFixCells - 1) / umma::kFixCells;
   if (fix_blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  umma::umma_fix_kernel<TO><<<(unsigned)fix_blocks, 64, 0, s>>>(static_cast<TO*>(y), static_cast<const TO*>(x), F);
+  umma::umma_fix_kernel<TO><<<(unsigned)fix_blocks, 16 * umma::kFixCells, 0, s>>>(static_cast<TO*>(y),
+                                                                                static_cast<const TO*>(x), F);
   return cudaGetLastError();
 }
 
