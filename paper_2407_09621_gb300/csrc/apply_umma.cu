@@ -6,25 +6,34 @@
 // and one block per face neighbour, e.g. A_{c,c+x} = M_z(x)M_y(x)L^{c,c+1}_x. So
 //   v_c = sum over the seven blocks b of A_b u_{nb_b(c)},
 // a GEMM whose rows are cells: D (cells x 64) = sum_b U_b (cells x 64) A_b^T, each U_b the input
-// tile shifted by the neighbour's cell offset. A tile is a 3D box of BX x BY x BZ = 128 cells of
-// the mesh (the shape that wastes the fewest cells on the mesh's edges), loaded by TMA through a
-// 4D tensor map over (64 values, nx, ny, nz): each of the seven input tiles is the same box shifted
-// by one cell along one axis, one 128-byte row per cell, and cells outside the mesh arrive as
-// zeros. A missing neighbour therefore contributes nothing, and every cell is first computed with
-// the interior diagonal block. A boundary cell differs from that only by its boundary faces: the
-// 1D block of a cell on the low (high) end of direction d is L + dL_0 (L + dL_1) with the rank-2
+// rows of the tile's cells shifted by one cell along one axis. A tile is a plane patch of 8 x 16 x 1
+// cells (128 rows, the UMMA M); TMA loads it through 4D tensor maps over (64 values, nx, ny, nz),
+// one 128-byte row per cell, cells outside the mesh arriving as zeros. A missing neighbour
+// therefore contributes nothing, and every cell is first computed with the interior diagonal
+// block. A boundary cell differs from that only by its boundary faces: the 1D block of a cell on
+// the low (high) end of direction d is L + dL_0 (L + dL_1) with the rank-2
 //   dL_0 = (v0 d0^T + d0 v0^T)/(2h),  dL_1 = -(v1 d1^T + d1 v1^T)/(2h),
 // so a second, small kernel adds (M (x) M (x) dL) u_c for each boundary face of each boundary
 // cell on the FMA pipes (rank 2 along the normal, the mass tensor along the two tangents).
 //
-// One CTA per SM, persistent over tiles, warp-specialized so that loads, products and stores of
-// consecutive tiles overlap:
-//   warp 0      TMA producer: streams the seven input tiles of every output tile through a ring
-//               of 16 KB shared-memory slots;
-//   warp 1      MMA issuer: per slot four tcgen05.mma (M = 128, N = 64, K = 16) into one of two
-//               TMEM accumulators, then tcgen05.commit releases the slot;
-//   warps 2-5   epilogue: tcgen05.ld of the finished accumulator (one cell row per thread),
-//               scale, round to the storage type and store the rows of cells inside the mesh.
+// Loads per tile, instead of seven: a window box of 8 x 18 x 1 cells holds the tile's own rows and
+// those of its y-neighbours at row offsets 8, 0 and 16 (multiples of the 8-row swizzle atom, so each
+// is a plain operand), and two boxes shifted by one cell along x hold the x-neighbours. The z-terms
+// need no load: a CTA walks a z-segment of one tile column, and the own rows of tile z are also the
+// z+ neighbour rows of tile z - 1 and the z- neighbour rows of tile z + 1, so their products go into
+// those tiles' accumulators (four TMEM accumulators rotate: the tile finishing, the current one,
+// the next one, and one being read by the epilogue). A segment [z0, z1) loads the own rows of tiles
+// z0 - 1 and z1 as halos. That is 52 KB per tile from L2 instead of 112 KB, and the ring of 18 KB
+// slots looks about three tiles ahead.
+//
+// One CTA per SM, persistent over work units (a tile column's z-segment), warp-specialized so
+// that loads, products and stores of consecutive tiles overlap:
+//   warp 0      TMA producer: streams the boxes of every tile through the slot ring;
+//   warp 1      MMA issuer: per operand four tcgen05.mma (M = 128, N = 64, K = 16) into the
+//               accumulator it belongs to, then tcgen05.commit releases the slot and hands each
+//               finished accumulator to the epilogue;
+//   warps 2-5   epilogue: tcgen05.ld of a finished accumulator (one cell row per thread), scale,
+//               round to the storage type and store the rows of cells inside the mesh.
 // Algorithm 1 error correction splits each block matrix into a high part and the rounded
 // remainder; both products accumulate into the same FP32 accumulator. The input vector is
 // already in the operand type, so only the matrix needs the split (two products instead of
@@ -52,8 +61,11 @@ namespace tp {
 
 namespace umma {
 
-constexpr int kRows = 128;            // cells per tile (UMMA M)
-constexpr int kTileBytes = kRows * 128;
+constexpr int kRows = 128;            // cells per tile (UMMA M): 8 x 16 x 1
+constexpr int kBX = 8, kBY = 16;
+constexpr int kTileBytes = kRows * 128;            // one tile box
+constexpr int kWinBytes = (kRows + 2 * kBX) * 128; // the window box: the tile with a y-halo row each side
+constexpr int kSlotBytes = kWinBytes;
 constexpr int kMatBytes = 64 * 128;   // one 64 x 64 16-bit block matrix
 constexpr int kThreads = 192;         // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kWaitLimit = 1 << 22;
@@ -64,10 +76,10 @@ template <bool EC>
 __host__ __device__ constexpr int nmat() { return EC ? 14 : 7; }
 // ring slots that fit beside the block matrices in 227 KB of shared memory
 template <bool EC>
-__host__ __device__ constexpr int nslots() { return EC ? 7 : 10; }
+__host__ __device__ constexpr int nslots() { return EC ? 6 : 9; }
 template <bool EC>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kTileBytes + 8 * (2 * nslots<EC>() + 5) + 16;
+  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kSlotBytes + 8 * (2 * nslots<EC>() + 9) + 16;
 }
 
 __device__ __forceinline__ uint32_t s2u(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -164,45 +176,50 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return
                  "=r"(r[base + 28]), "=r"(r[base + 29]), "=r"(r[base + 30]), "=r"(r[base + 31])          \
                : "r"(ta))
 
-// Cell of row r of tile t (x fastest within the box, boxes x fastest over the mesh); false if the
-// cell lies outside the mesh (a partial box on the mesh's far edges).
-__device__ __forceinline__ bool tile_cell(long long t, int r, const Params& P, long long& cell) {
-  const int tx = (int)(t % P.tiles[0]), ty = (int)((t / P.tiles[0]) % P.tiles[1]);
-  const int tz = (int)(t / ((long long)P.tiles[0] * P.tiles[1]));
-  const int cx = tx * P.box[0] + r % P.box[0], cy = ty * P.box[1] + (r / P.box[0]) % P.box[1];
-  const int cz = tz * P.box[2] + r / (P.box[0] * P.box[1]);
-  cell = ((long long)cz * P.ny + cy) * P.nx + cx;
-  return cx < P.nx && cy < P.ny && cz < P.nz;
+// Work unit u: tile column (tx, ty) and its z-segment [z0, z1).
+struct Unit {
+  int x0, y0, z0, z1;
+};
+__device__ __forceinline__ Unit unit_of(long long u, const Params& P) {
+  const long long cols = (long long)P.tiles[0] * P.tiles[1];
+  const long long col = u % cols, sg = u / cols;
+  Unit w;
+  w.x0 = (int)(col % P.tiles[0]) * kBX;
+  w.y0 = (int)(col / P.tiles[0]) * kBY;
+  w.z0 = (int)sg * P.seg;
+  w.z1 = min(w.z0 + P.seg, P.nz);
+  return w;
 }
 
 template <typename TO, bool EC>
 __global__ void __launch_bounds__(kThreads, 1)
-apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, const TO* __restrict__ mats,
-                  const __grid_constant__ Params P, int* __restrict__ err) {
+apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant__ CUtensorMap tmt,
+                  TO* __restrict__ y, const TO* __restrict__ mats, const __grid_constant__ Params P,
+                  int* __restrict__ err) {
   constexpr int NMAT = nmat<EC>(), S = nslots<EC>();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = base;                      // NMAT block matrices, [out n][in k], swizzled
-  unsigned char* sA = base + NMAT * kMatBytes;   // S input-tile slots
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kTileBytes);
-  // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[2] (accumulator complete),
-  // acce[2] (accumulator read), drain
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 5);
+  unsigned char* sA = base + NMAT * kMatBytes;   // S slots of kSlotBytes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kSlotBytes);
+  // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[4] (accumulator complete),
+  // acce[4] (accumulator read), drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 9);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar0 = s2u(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (S + s); };
   auto accf = [&](int a) { return bar0 + 8u * (2 * S + a); };
-  auto acce = [&](int a) { return bar0 + 8u * (2 * S + 2 + a); };
-  const uint32_t drain = bar0 + 8u * (2 * S + 4);
+  auto acce = [&](int a) { return bar0 + 8u * (2 * S + 4 + a); };
+  const uint32_t drain = bar0 + 8u * (2 * S + 8);
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < 4; ++a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(a)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(acce(a)));
     }
@@ -211,7 +228,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
     *abort = 0;
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   // block matrices -> shared, swizzled
@@ -224,37 +241,42 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
-  const long long ntiles = (long long)P.tiles[0] * P.tiles[1] * P.tiles[2];
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      const int offs[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
       int slot = 0;
       uint32_t ph = 0, issued = 0, iph = 0;  // per-slot: issued at least once, parity of the last issue
-      bool ok = true;
-      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int cx = (int)(t % P.tiles[0]) * P.box[0], cy = (int)((t / P.tiles[0]) % P.tiles[1]) * P.box[1];
-        const int cz = (int)(t / ((long long)P.tiles[0] * P.tiles[1])) * P.box[2];
-        for (int b = 0; b < 7; ++b) {
-          if (!(ok = wait_bar(empty(slot), ph ^ 1u, abort, err, 1, P.wait_ns))) break;
-          if (P.test_withhold && blockIdx.x == 0 && t == 0 && b == 0) {
-            // failure-injection tests: this slot never fills, so the waits on it run out
-            if (++slot == S) { slot = 0; ph ^= 1u; }
-            continue;
-          }
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(slot)), "r"(kTileBytes)
-                       : "memory");
-          // the box may start one cell outside the mesh: those cells arrive as zeros
-          asm volatile(
-              "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
-              ::"r"(s2u(sA + slot * kTileBytes)), "l"((uint64_t)&tmx), "r"(0), "r"(cx + offs[b][0]),
-                "r"(cy + offs[b][1]), "r"(cz + offs[b][2]), "r"(full(slot))
-              : "memory");
-          issued |= 1u << slot;
-          iph = (iph & ~(1u << slot)) | (ph << slot);
+      bool ok = true, first = true;
+      // one box into the next slot; boxes may start one cell outside the mesh (zeros arrive)
+      auto load = [&](const CUtensorMap* tm, int bytes, int cx, int cy, int cz) -> bool {
+        if (!wait_bar(empty(slot), ph ^ 1u, abort, err, 1, P.wait_ns)) return false;
+        if (P.test_withhold && blockIdx.x == 0 && first) {
+          // failure-injection tests: this slot never fills, so the waits on it run out
+          first = false;
           if (++slot == S) { slot = 0; ph ^= 1u; }
+          return true;
         }
+        first = false;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(full(slot)), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n"
+            ::"r"(s2u(sA + slot * kSlotBytes)), "l"((uint64_t)tm), "r"(0), "r"(cx), "r"(cy), "r"(cz), "r"(full(slot))
+            : "memory");
+        issued |= 1u << slot;
+        iph = (iph & ~(1u << slot)) | (ph << slot);
+        if (++slot == S) { slot = 0; ph ^= 1u; }
+        return true;
+      };
+      for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+        const Unit w = unit_of(u, P);
+        if (w.z0 > 0) ok = load(&tmt, kTileBytes, w.x0, w.y0, w.z0 - 1);
+        for (int z = w.z0; z < w.z1 && ok; ++z) {
+          ok = load(&tmw, kWinBytes, w.x0, w.y0 - 1, z) && load(&tmt, kTileBytes, w.x0 - 1, w.y0, z) &&
+               load(&tmt, kTileBytes, w.x0 + 1, w.y0, z);
+        }
+        if (ok && w.z1 < P.nz) ok = load(&tmt, kTileBytes, w.x0, w.y0, w.z1);
       }
       // let every copy in flight land before the CTA can leave
       for (int s = 0; s < S; ++s)
@@ -266,37 +288,95 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
       const uint32_t fmt = std::is_same<TO, __nv_bfloat16>::value ? 1u : 0u;
       // D F32, A/B F16 (0) or BF16 (1), both K-major, N = 64, M = 128
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
-      int slot = 0, it = 0;
+      int slot = 0;
       uint32_t ph = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
-        const int a = it & 1;
-        if (!(ok = wait_bar(acce(a), ((it >> 1) & 1) ^ 1u, abort, err, 2, P.wait_ns))) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const uint32_t dt = tmem + 64u * a;
-        for (int b = 0; b < 7; ++b) {
-          if (!(ok = wait_bar(full(slot), ph, abort, err, 3, P.wait_ns))) break;
-          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      long long g = 0;  // running index of this CTA's tiles; accumulator g & 3
+      // D[acc] (+)= rows at `a_addr` times block b^T; `init`: the first product into this accumulator
+      auto mma = [&](long long gt, uint32_t a_addr, int b, bool init) {
+        const uint32_t dt = tmem + 64u * (uint32_t)(gt & 3);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint64_t ad = sw128_desc(s2u(sA + slot * kTileBytes) + ks * 32);
-            const uint64_t bd = sw128_desc(s2u(sB + b * kMatBytes) + ks * 32);
-            const uint32_t acc = (b | ks) != 0;
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ad = sw128_desc(a_addr + ks * 32);
+          const uint64_t bd = sw128_desc(s2u(sB + b * kMatBytes) + ks * 32);
+          const uint32_t acc = (init && ks == 0) ? 0u : 1u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                       ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          if (EC) {
+            const uint64_t bl = sw128_desc(s2u(sB + (7 + b) * kMatBytes) + ks * 32);
             asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            if (EC) {
-              const uint64_t bl = sw128_desc(s2u(sB + (7 + b) * kMatBytes) + ks * 32);
-              asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                           ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc), "r"(1u));
-            }
+                         ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc), "r"(1u));
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(slot))
-                       : "memory");
-          if (++slot == S) { slot = 0; ph ^= 1u; }
+        }
+      };
+      // wait until the epilogue has read the previous tile held by accumulator gt & 3
+      auto acquire = [&](long long gt) -> bool {
+        if (!wait_bar(acce((int)(gt & 3)), (uint32_t)((gt >> 2) & 1) ^ 1u, abort, err, 2, P.wait_ns)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        return true;
+      };
+      auto take = [&]() -> uint32_t {  // wait for the next slot; its shared address
+        if (!wait_bar(full(slot), ph, abort, err, 3, P.wait_ns)) return 0u;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        return s2u(sA + slot * kSlotBytes);
+      };
+      auto release = [&]() {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(slot))
+                     : "memory");
+        if (++slot == S) { slot = 0; ph ^= 1u; }
+      };
+      auto finish = [&](long long gt) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                     ::"r"(accf((int)(gt & 3))) : "memory");
+      };
+      for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+        const Unit w = unit_of(u, P);
+        const long long g0 = g;
+        bool inited = false;  // accumulator of the current tile holds a product already
+        if (w.z0 > 0) {  // halo below: the z- neighbour rows of tile z0
+          uint32_t a;
+          if (!(ok = acquire(g0)) || !(a = take())) { ok = false; break; }
+          mma(g0, a, 5, true);
+          release();
+          inited = true;
+        }
+        for (int z = w.z0; z < w.z1 && ok; ++z) {
+          const long long gz = g0 + (z - w.z0);
+          uint32_t a;
+          if (!(a = take())) { ok = false; break; }
+          // the window: y- rows at offset 0, own rows at 8, y+ rows at 16 (rows of 128 bytes)
+          const uint32_t own = a + 8 * 128;
+          if (z + 1 < w.z1) {  // own rows are the z- neighbour rows of tile z + 1
+            if (!(ok = acquire(gz + 1))) break;
+            mma(gz + 1, own, 5, true);
+          }
+          if (!inited && !(ok = acquire(gz))) break;
+          mma(gz, own, 0, !inited);
+          mma(gz, a, 3, false);
+          mma(gz, a + 16 * 128, 4, false);
+          if (z > w.z0) {  // own rows are the z+ neighbour rows of tile z - 1, its last product
+            mma(gz - 1, own, 6, false);
+            finish(gz - 1);
+          }
+          release();
+          if (!(a = take())) { ok = false; break; }
+          mma(gz, a, 1, false);
+          release();
+          if (!(a = take())) { ok = false; break; }
+          mma(gz, a, 2, false);
+          release();
+          inited = true;  // tile z + 1 was initialized above (or does not exist in this segment)
         }
         if (!ok) break;
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(accf(a))
-                     : "memory");
+        const long long glast = g0 + (w.z1 - w.z0) - 1;
+        if (w.z1 < P.nz) {  // halo above: the z+ neighbour rows of the last tile
+          uint32_t a;
+          if (!(a = take())) { ok = false; break; }
+          mma(glast, a, 6, false);
+          release();
+        }
+        finish(glast);
+        g = glast + 1;
       }
       // every product issued so far has finished before TMEM is released
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(drain)
@@ -307,29 +387,36 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
     // ---------------------------------------------------------------- epilogue
     const int q4 = warp & 3;  // this warp may read TMEM lanes 32*q4 .. 32*q4+31
     const int row = 32 * q4 + lane;
-    int it = 0;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-      const int a = it & 1;
-      // warp-uniform decision: the TMEM loads below are .sync.aligned
-      if (!__all_sync(0xffffffffu, wait_bar(accf(a), (it >> 1) & 1, abort, err, 7, P.wait_ns))) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      uint32_t r[64];
-      const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * a;
-      TP_LD32(r, 0, ta);
-      TP_LD32(r, 32, ta + 32);
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      arrive(acce(a));
-      long long cell;
-      if (tile_cell(t, row, P, cell)) {
-        uint4* dst = reinterpret_cast<uint4*>(y + cell * 64);
+    long long g = 0;
+    bool ok = true;
+    for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
+      const Unit w = unit_of(u, P);
+      for (int z = w.z0; z < w.z1; ++z, ++g) {
+        const int a = (int)(g & 3);
+        // warp-uniform decision: the TMEM loads below are .sync.aligned
+        if (!__all_sync(0xffffffffu, wait_bar(accf(a), (uint32_t)((g >> 2) & 1), abort, err, 7, P.wait_ns))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        uint32_t r[64];
+        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * (uint32_t)a;
+        TP_LD32(r, 0, ta);
+        TP_LD32(r, 32, ta + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        arrive(acce(a));
+        const int cx = w.x0 + (row & (kBX - 1)), cy = w.y0 + row / kBX;
+        if (cx < P.nx && cy < P.ny) {
+          uint4* dst = reinterpret_cast<uint4*>(y + (((long long)z * P.ny + cy) * P.nx + cx) * 64);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint4 o;
-          TO* h = reinterpret_cast<TO*>(&o);
+          for (int c = 0; c < 8; ++c) {
+            uint4 o;
+            TO* h = reinterpret_cast<TO*>(&o);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
-          dst[c] = o;
+            for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
+            dst[c] = o;
+          }
         }
       }
     }
@@ -337,7 +424,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmx, TO* __restrict__ y, c
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256));
   }
 }
 
@@ -474,7 +561,7 @@ static std::vector<double> umma_blocks(const tp_op_s* op) {
   return B;
 }
 
-static void umma_box(int nx, int ny, int nz, int box[3], int tiles[3]);
+static void umma_schedule(int nx, int ny, int nz, int sms, umma::Params& P);
 
 template <typename TO, bool EC>
 static cudaError_t umma_prepare_t(tp_op_s* op) {
@@ -507,7 +594,6 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   P.lo_scale = 1.0f;
   P.wait_ns = 1000000000ull;
   P.test_withhold = 0;
-  umma_box(op->mesh.nx, op->mesh.ny, op->mesh.nz, P.box, P.tiles);
   UmmaFixParams& F = op->umma_fix;
   memset(&F, 0, sizeof(F));
   for (int d = 0; d < 3; ++d) {
@@ -523,25 +609,30 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->device);
   if (err != cudaSuccess) return err;
   op->sm_count = sms > 0 ? sms : 1;
+  umma_schedule(op->mesh.nx, op->mesh.ny, op->mesh.nz, op->sm_count, P);
   return cudaFuncSetAttribute(umma::apply_umma_kernel<TO, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)umma::smem_bytes<EC>());
 }
 
-// Tile shape: the box of 128 cells (powers of two along x, y, z) that pads the mesh the least,
-// the longest x extent among equals (contiguous rows for the copies and the stores).
-static void umma_box(int nx, int ny, int nz, int box[3], int tiles[3]) {
-  long long best = -1;
-  for (int bx = 1; bx <= 128; bx *= 2)
-    for (int by = 1; bx * by <= 128; by *= 2) {
-      const int bz = 128 / (bx * by);
-      const long long tx = (nx + bx - 1) / bx, ty = (ny + by - 1) / by, tz = (nz + bz - 1) / bz;
-      const long long cost = tx * ty * tz;
-      if (best < 0 || cost < best || (cost == best && bx > box[0])) {
-        best = cost;
-        box[0] = bx; box[1] = by; box[2] = bz;
-        tiles[0] = (int)tx; tiles[1] = (int)ty; tiles[2] = (int)tz;
-      }
+// Tiles of 8 x 16 x 1 cells; work units are z-segments of tile columns. The segment length is the
+// one that minimizes the busiest CTA's work: its units times (tiles per unit + the two halo boxes
+// of an inner segment, about a third of a tile's loads each).
+static void umma_schedule(int nx, int ny, int nz, int sms, umma::Params& P) {
+  P.tiles[0] = (nx + umma::kBX - 1) / umma::kBX;
+  P.tiles[1] = (ny + umma::kBY - 1) / umma::kBY;
+  P.tiles[2] = nz;
+  const long long cols = (long long)P.tiles[0] * P.tiles[1];
+  double best = -1.0;
+  for (int L = 1; L <= nz; ++L) {
+    const long long segs = (nz + L - 1) / L, units = cols * segs;
+    const long long per = (units + sms - 1) / sms;
+    const double cost = (double)per * (L + (segs > 1 ? 0.7 : 0.0));
+    if (best < 0.0 || cost < best - 1e-9) {
+      best = cost;
+      P.seg = L;
+      P.units = units;
     }
+  }
 }
 
 template <typename TO, bool EC>
@@ -549,22 +640,26 @@ static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cuda
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   const umma::Params& P = op->umma_params;
-  CUtensorMap tm;
-  // (64 values, nx, ny, nz) with boxes of (64, BX, BY, BZ): one 128-byte row per cell
-  cuuint64_t dims[4] = {64, (cuuint64_t)op->mesh.nx, (cuuint64_t)op->mesh.ny, (cuuint64_t)op->mesh.nz};
-  cuuint64_t strides[3] = {128, 128ull * op->mesh.nx, 128ull * op->mesh.nx * op->mesh.ny};
-  cuuint32_t box[4] = {64, (cuuint32_t)P.box[0], (cuuint32_t)P.box[1], (cuuint32_t)P.box[2]};
-  cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUtensorMapDataType dt =
       std::is_same<TO, __half>::value ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  if (enc(&tm, dt, 4, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  // (64 values, nx, ny, nz), one 128-byte row per cell; boxes of 8 x 18 x 1 cells (the window: a
+  // tile with a y-halo row on each side) and 8 x 16 x 1 cells (a tile)
+  cuuint64_t dims[4] = {64, (cuuint64_t)op->mesh.nx, (cuuint64_t)op->mesh.ny, (cuuint64_t)op->mesh.nz};
+  cuuint64_t strides[3] = {128, 128ull * op->mesh.nx, 128ull * op->mesh.nx * op->mesh.ny};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  cuuint32_t boxw[4] = {64, (cuuint32_t)umma::kBX, (cuuint32_t)(umma::kBY + 2), 1};
+  cuuint32_t boxt[4] = {64, (cuuint32_t)umma::kBX, (cuuint32_t)umma::kBY, 1};
+  CUtensorMap tmw, tmt;
+  if (enc(&tmw, dt, 4, const_cast<void*>(x), dims, strides, boxw, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-      CUDA_SUCCESS)
+          CUDA_SUCCESS ||
+      enc(&tmt, dt, 4, const_cast<void*>(x), dims, strides, boxt, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  const long long tiles = (long long)P.tiles[0] * P.tiles[1] * P.tiles[2];
-  const int grid = (int)(tiles < op->sm_count ? tiles : op->sm_count);
+  const int grid = (int)(P.units < op->sm_count ? P.units : op->sm_count);
   umma::apply_umma_kernel<TO, EC><<<grid, umma::kThreads, umma::smem_bytes<EC>(), s>>>(
-      tm, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P, op->umma_err);
+      tmw, tmt, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P, op->umma_err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const UmmaFixParams& F = op->umma_fix;

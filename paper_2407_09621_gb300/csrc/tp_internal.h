@@ -70,8 +70,9 @@ struct UmmaParams {
   long long ncells;
   float out_scale;  // 1 / (power-of-two scale of the stored block matrices)
   float lo_scale;   // scale of the low-part products (1: they share the accumulator)
-  int box[3];       // cells of one tile along x, y, z (their product is 128, the UMMA M)
-  int tiles[3];     // tiles along x, y, z
+  int tiles[3];     // tiles of 8 x 16 x 1 cells along x, y, z
+  int seg;          // tiles per z-segment of a tile column (one work unit)
+  long long units;  // work units: tile columns x z-segments
   unsigned long long wait_ns;  // limit of every bounded wait on the pipeline barriers (1 s by default)
   int test_withhold;           // failure-injection tests only: CTA 0 skips its first input-tile copy
 };
