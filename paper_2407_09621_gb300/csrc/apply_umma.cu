@@ -14,7 +14,8 @@
 // the low (high) end of direction d is L + dL_0 (L + dL_1) with the rank-2
 //   dL_0 = (v0 d0^T + d0 v0^T)/(2h),  dL_1 = -(v1 d1^T + d1 v1^T)/(2h),
 // so a second, small kernel adds (M (x) M (x) dL) u_c for each boundary face of each boundary
-// cell on the FMA pipes (rank 2 along the normal, the mass tensor along the two tangents).
+// cell on the FMA pipes (rank 2 along the normal, the mass tensor along the two tangents), one
+// thread per boundary cell.
 //
 // Loads per tile, instead of seven: a window box of 8 x 18 x 1 cells holds the tile's own rows and
 // those of its y-neighbours at row offsets 8, 0 and 16 (multiples of the 8-row swizzle atom, so each
@@ -28,12 +29,14 @@
 //
 // One CTA per SM, persistent over work units (a tile column's z-segment), warp-specialized so
 // that loads, products and stores of consecutive tiles overlap:
-//   warp 0      TMA producer: streams the boxes of every tile through the slot ring;
+//   warp 0      TMA producer: streams the boxes of every tile through the slot ring (and asks L2
+//               to prefetch the window boxes a few tiles ahead);
 //   warp 1      MMA issuer: per operand four tcgen05.mma (M = 128, N = 64, K = 16) into the
 //               accumulator it belongs to, then tcgen05.commit releases the slot and hands each
 //               finished accumulator to the epilogue;
-//   warps 2-5   epilogue: tcgen05.ld of a finished accumulator (one cell row per thread), scale,
-//               round to the storage type and store the rows of cells inside the mesh.
+//   warps 2-9   epilogue, two groups of four warps taking alternate tiles: tcgen05.ld of a
+//               finished accumulator (one cell row per thread), scale, round to the storage type
+//               and store the rows of cells inside the mesh.
 // Algorithm 1 error correction splits each block matrix into a high part and the rounded
 // remainder; both products accumulate into the same FP32 accumulator. The input vector is
 // already in the operand type, so only the matrix needs the split (two products instead of
@@ -67,7 +70,8 @@ constexpr int kTileBytes = kRows * 128;            // one tile box
 constexpr int kWinBytes = (kRows + 2 * kBX) * 128; // the window box: the tile with a y-halo row each side
 constexpr int kSlotBytes = kWinBytes;
 constexpr int kMatBytes = 64 * 128;   // one 64 x 64 16-bit block matrix
-constexpr int kThreads = 192;         // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two groups of four)
+constexpr int kPrefetch = 4;          // tiles ahead whose window box the producer prefetches into L2
 constexpr int kWaitLimit = 1 << 22;
 
 using Params = UmmaParams;
@@ -176,6 +180,62 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return
                  "=r"(r[base + 28]), "=r"(r[base + 29]), "=r"(r[base + 30]), "=r"(r[base + 31])          \
                : "r"(ta))
 
+// Boundary-face correction of one cell in FP32: o += s hh (M_t1 (x) M_t2 (x) (e_end beta^T + beta e_end^T)) u
+// for the face of direction D on side SIDE (0: low, beta = d0, end 0, s = +1; 1: high, beta = d1,
+// end 3, s = -1). Node (t1, t2, m) of the line along D at tangential indices (t1, t2): D = 0
+// (t1, t2, m) = (z, y, x), D = 1 (z, x, y), D = 2 (y, x, z); the tangential masses are M_z, M_y
+// (D = 0), M_z, M_x (D = 1), M_y, M_x (D = 2). All indices are compile-time (registers).
+template <int D, int SIDE>
+__device__ __forceinline__ void add_face(float (&o)[64], const float (&u)[64], const Params& P) {
+  constexpr int END = SIDE ? 3 : 0;
+  auto node = [](int t1, int t2, int m) {
+    return D == 0 ? (t1 * 4 + t2) * 4 + m : (D == 1 ? (t1 * 4 + m) * 4 + t2 : (m * 4 + t1) * 4 + t2);
+  };
+  const float* beta = SIDE ? P.fd1 : P.fd0;
+  const float* M1 = P.fM[D == 2 ? 1 : 2];
+  const float* M2 = P.fM[D == 0 ? 1 : 0];
+  float sa[16], sb[16], ta[16], tb[16];
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc = fmaf(beta[m], u[node(a >> 2, a & 3, m)], acc);
+    sa[a] = acc;
+    sb[a] = u[node(a >> 2, a & 3, END)];
+  }
+  // T = S M2^T, then W = M1 T (the tangential mass tensor applied to S)
+#pragma unroll
+  for (int t1 = 0; t1 < 4; ++t1)
+#pragma unroll
+    for (int t2 = 0; t2 < 4; ++t2) {
+      float xa = 0.f, xb = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        xa = fmaf(sa[t1 * 4 + b], M2[t2 * 4 + b], xa);
+        xb = fmaf(sb[t1 * 4 + b], M2[t2 * 4 + b], xb);
+      }
+      ta[t1 * 4 + t2] = xa;
+      tb[t1 * 4 + t2] = xb;
+    }
+  const float sg = SIDE ? -P.fhh[D] : P.fhh[D];
+#pragma unroll
+  for (int t1 = 0; t1 < 4; ++t1)
+#pragma unroll
+    for (int t2 = 0; t2 < 4; ++t2) {
+      float wa = 0.f, wb = 0.f;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        wa = fmaf(M1[t1 * 4 + b], ta[b * 4 + t2], wa);
+        wb = fmaf(M1[t1 * 4 + b], tb[b * 4 + t2], wb);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float add = (m == END ? wa : 0.f) + beta[m] * wb;
+        o[node(t1, t2, m)] = fmaf(sg, add, o[node(t1, t2, m)]);
+      }
+    }
+}
+
 // Work unit u: tile column (tx, ty) and its z-segment [z0, z1).
 struct Unit {
   int x0, y0, z0, z1;
@@ -194,8 +254,8 @@ __device__ __forceinline__ Unit unit_of(long long u, const Params& P) {
 template <typename TO, bool EC>
 __global__ void __launch_bounds__(kThreads, 1)
 apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant__ CUtensorMap tmt,
-                  TO* __restrict__ y, const TO* __restrict__ mats, const __grid_constant__ Params P,
-                  int* __restrict__ err) {
+                  const TO* __restrict__ x, TO* __restrict__ y, const TO* __restrict__ mats,
+                  const __grid_constant__ Params P, int* __restrict__ err) {
   constexpr int NMAT = nmat<EC>(), S = nslots<EC>();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -271,8 +331,15 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
       };
       for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
         const Unit w = unit_of(u, P);
+        // first touches of the column come from DRAM: ask L2 for the first window boxes early
+        for (int z = w.z0; z < w.z1 && z < w.z0 + kPrefetch; ++z)
+          asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global [%0, {%1, %2, %3, %4}];\n"
+                       ::"l"((uint64_t)&tmw), "r"(0), "r"(w.x0), "r"(w.y0 - 1), "r"(z) : "memory");
         if (w.z0 > 0) ok = load(&tmt, kTileBytes, w.x0, w.y0, w.z0 - 1);
         for (int z = w.z0; z < w.z1 && ok; ++z) {
+          if (z + kPrefetch < w.z1)
+            asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global [%0, {%1, %2, %3, %4}];\n"
+                         ::"l"((uint64_t)&tmw), "r"(0), "r"(w.x0), "r"(w.y0 - 1), "r"(z + kPrefetch) : "memory");
           ok = load(&tmw, kWinBytes, w.x0, w.y0 - 1, z) && load(&tmt, kTileBytes, w.x0 - 1, w.y0, z) &&
                load(&tmt, kTileBytes, w.x0 + 1, w.y0, z);
         }
@@ -386,12 +453,14 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q4 = warp & 3;  // this warp may read TMEM lanes 32*q4 .. 32*q4+31
+    const int grp = (warp - 2) >> 2;  // group 0 takes the even tiles, group 1 the odd ones
     const int row = 32 * q4 + lane;
     long long g = 0;
     bool ok = true;
     for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
       const Unit w = unit_of(u, P);
       for (int z = w.z0; z < w.z1; ++z, ++g) {
+        if ((int)(g & 1) != grp) continue;
         const int a = (int)(g & 3);
         // warp-uniform decision: the TMEM loads below are .sync.aligned
         if (!__all_sync(0xffffffffu, wait_bar(accf(a), (uint32_t)((g >> 2) & 1), abort, err, 7, P.wait_ns))) {
@@ -411,11 +480,11 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
           uint4* dst = reinterpret_cast<uint4*>(y + (((long long)z * P.ny + cy) * P.nx + cx) * 64);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            uint4 o;
-            TO* h = reinterpret_cast<TO*>(&o);
+            uint4 ov;
+            TO* h = reinterpret_cast<TO*>(&ov);
 #pragma unroll
             for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
-            dst[c] = o;
+            dst[c] = ov;
           }
         }
       }
@@ -428,74 +497,61 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   }
 }
 
-// Boundary-face corrections (FP32 arithmetic). The cells of the six boundary faces are enumerated
-// face by face (x-, x+, y-, y+, z-, z+), one 16-lane group per slot; a cell on several faces is
-// handled by the group of the first of them, which adds the corrections of all its faces one after
-// the other. For direction d lane a = (t1, t2) owns the cell's line along d at the tangential
-// indices (t1, t2), with side 0 (low) / 1 (high) of the face:
-//   S_a = beta . u(t1, t2, :),  S_b = u(t1, t2, end)        (beta = d0, end 0 / beta = d1, end 3)
-//   W = (M_t1 (x) M_t2) S  over the 16 lines (shuffles),
-//   y(t1, t2, m) += s hh (e_end[m] W_a + beta[m] W_b),  s = +1 / -1.
-constexpr int kFixCells = 8;  // 16-lane groups per block of 128 threads
-
+// Boundary-face corrections, one thread per boundary cell, after the apply: the cells of the six
+// boundary faces are enumerated face by face (x-, x+, y-, y+, z-, z+); a cell on several faces is
+// handled by the thread of the first of them, which adds the corrections of all its faces (FP32)
+// to the stored row and rounds it again.
 template <typename TO>
-__global__ void __launch_bounds__(16 * kFixCells) umma_fix_kernel(TO* __restrict__ y, const TO* __restrict__ x,
-                                                                  const __grid_constant__ UmmaFixParams F) {
-  const long long fx = (long long)F.ny * F.nz, fy = (long long)F.nx * F.nz, fz = (long long)F.nx * F.ny;
-  long long b = (long long)blockIdx.x * kFixCells + (threadIdx.x >> 4);
-  if (b >= 2 * (fx + fy + fz)) return;  // group-uniform
-  const int lane = threadIdx.x & 15, t1 = lane >> 2, t2 = lane & 3;
-  const unsigned gmask = 0xffffu << (threadIdx.x & 16);  // the lanes of this group
+__global__ void __launch_bounds__(128) umma_fix_kernel(const TO* __restrict__ x, TO* __restrict__ y,
+                                                       const __grid_constant__ Params P) {
+  const long long fx = (long long)P.ny * P.nz, fy = (long long)P.nx * P.nz, fz = (long long)P.nx * P.ny;
+  long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= 2 * (fx + fy + fz)) return;
   int f, cx, cy, cz;
   if (b < 2 * fx) {
     f = (int)(b / fx);
     const long long i = b % fx;
-    cx = f ? F.nx - 1 : 0; cy = (int)(i % F.ny); cz = (int)(i / F.ny);
+    cx = f ? P.nx - 1 : 0; cy = (int)(i % P.ny); cz = (int)(i / P.ny);
   } else if ((b -= 2 * fx) < 2 * fy) {
     f = 2 + (int)(b / fy);
     const long long i = b % fy;
-    cy = f == 3 ? F.ny - 1 : 0; cx = (int)(i % F.nx); cz = (int)(i / F.nx);
+    cy = f == 3 ? P.ny - 1 : 0; cx = (int)(i % P.nx); cz = (int)(i / P.nx);
   } else {
     b -= 2 * fy;
     f = 4 + (int)(b / fz);
     const long long i = b % fz;
-    cz = f == 5 ? F.nz - 1 : 0; cx = (int)(i % F.nx); cy = (int)(i / F.nx);
+    cz = f == 5 ? P.nz - 1 : 0; cx = (int)(i % P.nx); cy = (int)(i / P.nx);
   }
-  const bool on[6] = {cx == 0, cx == F.nx - 1, cy == 0, cy == F.ny - 1, cz == 0, cz == F.nz - 1};
+  const bool on[6] = {cx == 0, cx == P.nx - 1, cy == 0, cy == P.ny - 1, cz == 0, cz == P.nz - 1};
   for (int g = 0; g < f; ++g)
-    if (on[g]) return;  // group-uniform: an earlier face's group owns this cell
-  const long long c64 = (((long long)cz * F.ny + cy) * F.nx + cx) * 64;
-  for (int g = f; g < 6; ++g) {
-    if (!on[g]) continue;
-    const int d = g >> 1, side = g & 1, end = side ? 3 : 0;
-    const float* beta = side ? F.d1 : F.d0;
-    // node of this lane's line at position m along d
-    auto node = [&](int m) { return d == 0 ? (t1 * 4 + t2) * 4 + m : (d == 1 ? (t1 * 4 + m) * 4 + t2 : (m * 4 + t1) * 4 + t2); };
-    float sa = 0.f, sb = 0.f;
+    if (on[g]) return;  // the thread of an earlier face owns this cell
+  const long long cell = ((long long)cz * P.ny + cy) * P.nx + cx;
+  float u[64], o[64];
+  const uint4* src = reinterpret_cast<const uint4*>(x + cell * 64);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const float v = to_f<TO>(x[c64 + node(m)]);
-      sa = fmaf(beta[m], v, sa);
-      if (m == end) sb = v;
-    }
-    // tangential mass: x-faces M_z (x) M_y, y-faces M_z (x) M_x, z-faces M_y (x) M_x
-    const float* M1 = F.M[d == 2 ? 1 : 2];
-    const float* M2 = F.M[d == 0 ? 1 : 0];
-    float wa = 0.f, wb = 0.f;
+  for (int c = 0; c < 8; ++c) {
+    const uint4 v = __ldg(src + c);
+    const TO* h = reinterpret_cast<const TO*>(&v);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const float oa = __shfl_sync(gmask, sa, q, 16), ob = __shfl_sync(gmask, sb, q, 16);
-      const float w = M1[t1 * 4 + (q >> 2)] * M2[t2 * 4 + (q & 3)];
-      wa = fmaf(w, oa, wa);
-      wb = fmaf(w, ob, wb);
+    for (int q = 0; q < 8; ++q) {
+      u[c * 8 + q] = to_f<TO>(h[q]);
+      o[c * 8 + q] = 0.f;
     }
-    const float sg = side ? -F.hh[d] : F.hh[d];
+  }
+  if (on[0]) add_face<0, 0>(o, u, P);
+  if (on[1]) add_face<0, 1>(o, u, P);
+  if (on[2]) add_face<1, 0>(o, u, P);
+  if (on[3]) add_face<1, 1>(o, u, P);
+  if (on[4]) add_face<2, 0>(o, u, P);
+  if (on[5]) add_face<2, 1>(o, u, P);
+  uint4* dst = reinterpret_cast<uint4*>(y + cell * 64);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const long long gi = c64 + node(m);
-      y[gi] = from_f<TO>(to_f<TO>(y[gi]) + sg * ((m == end ? wa : 0.f) + beta[m] * wb));
-    }
-    __syncwarp(gmask);  // the next face of this cell reads what this one wrote
+  for (int c = 0; c < 8; ++c) {
+    uint4 v = dst[c];
+    TO* h = reinterpret_cast<TO*>(&v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(to_f<TO>(h[q]) + o[c * 8 + q]);
+    dst[c] = v;
   }
 }
 
@@ -594,17 +650,14 @@ static cudaError_t umma_prepare_t(tp_op_s* op) {
   P.lo_scale = 1.0f;
   P.wait_ns = 1000000000ull;
   P.test_withhold = 0;
-  UmmaFixParams& F = op->umma_fix;
-  memset(&F, 0, sizeof(F));
   for (int d = 0; d < 3; ++d) {
-    for (int e = 0; e < 16; ++e) F.M[d][e] = (float)op->dir[d].M[e];
-    F.hh[d] = (float)(0.5 / op->dir[d].h);
+    for (int e = 0; e < 16; ++e) P.fM[d][e] = (float)op->dir[d].M[e];
+    P.fhh[d] = (float)(0.5 / op->dir[d].h);
   }
   for (int m = 0; m < 4; ++m) {
-    F.d0[m] = (float)op->ref.d0[m];
-    F.d1[m] = (float)op->ref.d1[m];
+    P.fd0[m] = (float)op->ref.d0[m];
+    P.fd1[m] = (float)op->ref.d1[m];
   }
-  F.nx = op->mesh.nx; F.ny = op->mesh.ny; F.nz = op->mesh.nz;
   int sms = 0;
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->device);
   if (err != cudaSuccess) return err;
@@ -659,15 +712,14 @@ static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cuda
     return cudaErrorInvalidValue;
   const int grid = (int)(P.units < op->sm_count ? P.units : op->sm_count);
   umma::apply_umma_kernel<TO, EC><<<grid, umma::kThreads, umma::smem_bytes<EC>(), s>>>(
-      tmw, tmt, static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P, op->umma_err);
+      tmw, tmt, static_cast<const TO*>(x), static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P,
+      op->umma_err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const UmmaFixParams& F = op->umma_fix;
-  const long long slots = 2 * ((long long)F.ny * F.nz + (long long)F.nx * F.nz + (long long)F.nx * F.ny);
-  const long long fix_blocks = (slots + umma::kFixCells - 1) / umma::kFixCells;
-  if (fix_blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  umma::umma_fix_kernel<TO><<<(unsigned)fix_blocks, 16 * umma::kFixCells, 0, s>>>(static_cast<TO*>(y),
-                                                                                static_cast<const TO*>(x), F);
+  const long long slots = 2 * ((long long)P.ny * P.nz + (long long)P.nx * P.nz + (long long)P.nx * P.ny);
+  const long long blocks = (slots + 127) / 128;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  umma::umma_fix_kernel<TO><<<(unsigned)blocks, 128, 0, s>>>(static_cast<const TO*>(x), static_cast<TO*>(y), P);
   return cudaGetLastError();
 }
 

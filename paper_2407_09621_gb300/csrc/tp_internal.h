@@ -75,15 +75,11 @@ struct UmmaParams {
   long long units;  // work units: tile columns x z-segments
   unsigned long long wait_ns;  // limit of every bounded wait on the pipeline barriers (1 s by default)
   int test_withhold;           // failure-injection tests only: CTA 0 skips its first input-tile copy
-};
-
-// Boundary-face corrections of the tcgen05 apply (apply_umma.cu), FP32: per direction d the mass
-// matrix M_d (n = 4, row-major), the basis derivatives at the ends, and 1/(2 h_d).
-struct UmmaFixParams {
-  float M[3][16];
-  float d0[4], d1[4];
-  float hh[3];
-  int nx, ny, nz;
+  // boundary-face corrections, FP32: per direction d the mass matrix M_d (n = 4, row-major), the basis
+  // derivatives at the ends, and 1/(2 h_d)
+  float fM[3][16];
+  float fd0[4], fd1[4];
+  float fhh[3];
 };
 
 void set_error(const char* fmt, ...);
@@ -115,7 +111,6 @@ struct tp_op_s {
   int* umma_err = nullptr;      // device error code of its bounded waits (0 = none)
   void* pw_mats = nullptr;      // patch-wise kernel: its 3 x 4 pairs of 1D patch factors (device)
   tp::UmmaParams umma_params;
-  tp::UmmaFixParams umma_fix;
   const void* hconst(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64 : (const void*)&c32; }
   const void* hconst_high(size_t tc_bytes) const { return tc_bytes == 8 ? (const void*)&c64h : (const void*)&c32h; }
   // host-buffer path (tp_apply_host): library-owned staging, and the streams and events of its
