@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--k", type=int, default=None, help="degree (default 3)")
     p.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp16", "bf16"])
     p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
+    p.add_argument("--patch", action="store_true", help="kernel-only: use the patch-wise kernel (vertex patches)")
     p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
     p.add_argument("--no-tune", action="store_true", help="keep the default apply tile shape (no autotuner)")
     p.add_argument("--vcycle-only", action="store_true",
@@ -609,8 +610,8 @@ def run_ours(args):
         print(json.dumps({"sweep_only": True, "degree_sweep": degree_sweep(torch.cuda.current_stream())}),
               flush=True)
         return
-    op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=2 if args.tensor else 0, ec=1 if args.ec else 0,
-                   autotune=0 if args.no_tune else 1)
+    op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=3 if args.patch else (2 if args.tensor else 0),
+                   ec=1 if args.ec else 0, autotune=0 if args.no_tune else 1)
     ndofs = op.ndofs
     if args.kernel_only:
         x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)
