@@ -509,7 +509,8 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
     if half:
         # FP16/BF16-storage V-cycles: tcgen05 level applies at k = 3, CUDA-core otherwise
         kh = TC if k == 3 else CC
-        runs += [("bf16_vcycle", _lib.TP_BF16, kh, CH), ("fp16_vcycle", _lib.TP_FP16, kh, CH)]
+        runs += [("bf16_vcycle", _lib.TP_BF16, kh, CH), ("fp16_vcycle", _lib.TP_FP16, kh, CH),
+                 ("bf16_vertex_patch", _lib.TP_BF16, kh, VP), ("fp16_vertex_patch", _lib.TP_FP16, kh, VP)]
     for name, prec, kern, smoother in runs:
         mg = _lib.tp_mg_create(op, precision=prec, kernel=kern, smoother=smoother)
         solver = _lib.tp_fgmres_create(op, mg, 30)

@@ -217,8 +217,8 @@ tp_status tp_op_check(tp_op op);
  *    colour r = b - A_l x, then x_P += A_P^{-1} r_P on each of its patches,
  *    solved exactly by fast diagonalization of the patch's Kronecker-sum
  *    matrix. One sweep per smoothing step, colours ascending before and
- *    descending after the coarse correction (tp_mg_smooth: ascending). FP64
- *    and FP32 multigrid precision only;
+ *    descending after the coarse correction (tp_mg_smooth: ascending); the
+ *    patch solves compute in FP64 for FP64 vectors and in FP32 otherwise;
  *  - restriction I_down = P^T, prolongation I_up = P, the exact embedding of
  *    the coarse DG space into the fine one;
  *  - coarse solve A_0^{-1}: exact, in FP64, by fast diagonalization.
@@ -268,8 +268,7 @@ typedef struct {
  * level by power iteration on the GPU (synchronizes the device).
  * The vertex-patch smoother estimates no lmax (lmax and ratio are unused).
  * Errors: TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA, TP_ERR_NONFINITE,
- * TP_ERR_UNSUPPORTED (finest degree above 7; vertex-patch smoother with
- * FP16/BF16 vectors). */
+ * TP_ERR_UNSUPPORTED (finest degree above 7; kernel TP_KERNEL_PATCH). */
 tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts);
 tp_status tp_mg_get_info(tp_mg mg, tp_mg_info_t* info);
 /* Level operator (owned by the hierarchy; valid until tp_mg_destroy). */

@@ -713,10 +713,6 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
     set_error("tp_mg_create: the level operators take the CUDA-core or tensor kernels, not the patch-wise one");
     return TP_ERR_UNSUPPORTED;
   }
-  if (o.smoother == TP_SMOOTHER_VERTEX_PATCH && o.precision != TP_FP64 && o.precision != TP_FP32) {
-    set_error("tp_mg_create: the vertex-patch smoother takes FP64 or FP32 multigrid vectors");
-    return TP_ERR_UNSUPPORTED;
-  }
   if (o.degree < 1 || o.degree > 16 || !(o.ratio > 1.0) || !(o.safety > 0) || o.coarse_cells < 1 ||
       (o.precision != TP_FP64 && o.precision != TP_FP32 && o.precision != TP_FP16 && o.precision != TP_BF16) ||
       o.power_iters < 1 || o.lmax < 0) {

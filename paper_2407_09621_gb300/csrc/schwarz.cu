@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "apply_common.cuh"
 #include "tp_internal.h"
 
 namespace tp {
@@ -78,9 +79,11 @@ constexpr size_t vp_smem_bytes() {
 
 // P^2 / 2 threads per patch; in every phase a thread owns two lines of the contracted direction,
 // lines p0 and p0 + P/2 of the outer index, so that each basis row it loads serves two lines.
-template <typename T, int N>
+// TS: storage type of x and r; T: arithmetic type (FP32 for FP16/BF16 storage) of the tables and
+// of every operation.
+template <typename TS, typename T, int N>
 __global__ void __launch_bounds__(2 * N * N)
-vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
+vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
                 VPDims D) {
   constexpr int P = 2 * N, R = P + 1, N3 = N * N * N, H = P / 2, NT = P * H;
   extern __shared__ __align__(16) unsigned char vp_smem[];
@@ -123,7 +126,7 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
   {
     T v[2 * P];  // all loads in flight before the shared stores
 #pragma unroll
-    for (int j = 0; j < 2 * P; ++j) v[j] = __ldg(r + gaddr(tid + j * NT));
+    for (int j = 0; j < 2 * P; ++j) v[j] = load_as<TS, T>(r + gaddr(tid + j * NT));
 #pragma unroll
     for (int j = 0; j < 2 * P; ++j) bufA[saddr(tid + j * NT)] = v[j];
   }
@@ -216,13 +219,13 @@ vp_patch_kernel(T* __restrict__ x, const T* __restrict__ r, const T* __restrict_
   {
     T v[2 * P];
 #pragma unroll
-    for (int j = 0; j < 2 * P; ++j) v[j] = x[gaddr(tid + j * NT)];
+    for (int j = 0; j < 2 * P; ++j) v[j] = static_cast<T>(x[gaddr(tid + j * NT)]);
 #pragma unroll
-    for (int j = 0; j < 2 * P; ++j) x[gaddr(tid + j * NT)] = v[j] + bufA[saddr(tid + j * NT)];
+    for (int j = 0; j < 2 * P; ++j) store_as<TS, T>(x + gaddr(tid + j * NT), v[j] + bufA[saddr(tid + j * NT)]);
   }
 }
 
-template <typename T, int N>
+template <typename TS, typename T, int N>
 cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
                           cudaStream_t s) {
   const int par[3] = {colour & 1, (colour >> 1) & 1, (colour >> 2) & 1};
@@ -230,42 +233,42 @@ cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, c
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
-  vp_patch_kernel<T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
-      static_cast<T*>(x), static_cast<const T*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D);
+  vp_patch_kernel<TS, T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
+      static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D);
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename TS, typename T, int N>
 cudaError_t prepare_colour() {
-  return cudaFuncSetAttribute(vp_patch_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(vp_patch_kernel<TS, T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)vp_smem_bytes<T, N>());
 }
 
-template <typename T>
+template <typename TS, typename T>
 cudaError_t prepare_t(int n) {
   switch (n) {
-    case 2: return prepare_colour<T, 2>();
-    case 3: return prepare_colour<T, 3>();
-    case 4: return prepare_colour<T, 4>();
-    case 5: return prepare_colour<T, 5>();
-    case 6: return prepare_colour<T, 6>();
-    case 7: return prepare_colour<T, 7>();
-    case 8: return prepare_colour<T, 8>();
+    case 2: return prepare_colour<TS, T, 2>();
+    case 3: return prepare_colour<TS, T, 3>();
+    case 4: return prepare_colour<TS, T, 4>();
+    case 5: return prepare_colour<TS, T, 5>();
+    case 6: return prepare_colour<TS, T, 6>();
+    case 7: return prepare_colour<TS, T, 7>();
+    case 8: return prepare_colour<TS, T, 8>();
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename TS, typename T>
 cudaError_t launch_colour_t(int n, int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
                             cudaStream_t s) {
   switch (n) {
-    case 2: return launch_colour<T, 2>(colour, nc, x, r, S, L, s);
-    case 3: return launch_colour<T, 3>(colour, nc, x, r, S, L, s);
-    case 4: return launch_colour<T, 4>(colour, nc, x, r, S, L, s);
-    case 5: return launch_colour<T, 5>(colour, nc, x, r, S, L, s);
-    case 6: return launch_colour<T, 6>(colour, nc, x, r, S, L, s);
-    case 7: return launch_colour<T, 7>(colour, nc, x, r, S, L, s);
-    case 8: return launch_colour<T, 8>(colour, nc, x, r, S, L, s);
+    case 2: return launch_colour<TS, T, 2>(colour, nc, x, r, S, L, s);
+    case 3: return launch_colour<TS, T, 3>(colour, nc, x, r, S, L, s);
+    case 4: return launch_colour<TS, T, 4>(colour, nc, x, r, S, L, s);
+    case 5: return launch_colour<TS, T, 5>(colour, nc, x, r, S, L, s);
+    case 6: return launch_colour<TS, T, 6>(colour, nc, x, r, S, L, s);
+    case 7: return launch_colour<TS, T, 7>(colour, nc, x, r, S, L, s);
+    case 8: return launch_colour<TS, T, 8>(colour, nc, x, r, S, L, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -277,15 +280,21 @@ bool vp_colour_nonempty(const int nc[3], int c) {
   return vp_count(c & 1, nc[0]) > 0 && vp_count((c >> 1) & 1, nc[1]) > 0 && vp_count((c >> 2) & 1, nc[2]) > 0;
 }
 
-// x_P += A_P^{-1} r_P for every patch of colour c (FP64 or FP32 vectors; every nc >= 2).
+// x_P += A_P^{-1} r_P for every patch of colour c (FP64 or FP32 vectors, or FP16/BF16 storage with
+// FP32 arithmetic; every nc >= 2).
 cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, void* x, const void* r, const void* S,
                       const void* L, cudaStream_t s) {
-  if (prec == TP_FP64) return launch_colour_t<double>(n, colour, nc, x, r, S, L, s);
-  if (prec == TP_FP32) return launch_colour_t<float>(n, colour, nc, x, r, S, L, s);
+  switch (prec) {
+    case TP_FP64: return launch_colour_t<double, double>(n, colour, nc, x, r, S, L, s);
+    case TP_FP32: return launch_colour_t<float, float>(n, colour, nc, x, r, S, L, s);
+    case TP_FP16: return launch_colour_t<__half, float>(n, colour, nc, x, r, S, L, s);
+    case TP_BF16: return launch_colour_t<__nv_bfloat16, float>(n, colour, nc, x, r, S, L, s);
+  }
   return cudaErrorInvalidValue;
 }
 
-// Eigenbases of the 1D patch factors of one level, uploaded in the vectors' precision:
+// Eigenbases of the 1D patch factors of one level, uploaded in the arithmetic precision (FP64 for
+// FP64 vectors, FP32 otherwise):
 // S[(d*4 + t)][X * kMaxP + a] = component X of eigenvector a, L[(d*4 + t)][a] = its eigenvalue,
 // for direction d and boundary type t. A mesh of min(nc, 4) cells with the level's h has every
 // type of the level at its vertices 1 .. min(nc, 4) - 1.
@@ -326,7 +335,11 @@ tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void*
     else reinterpret_cast<float*>(hL.data())[i] = (float)lam[i];
   }
   *S_out = *L_out = nullptr;
-  tp_status st = cuda_status(prec == TP_FP64 ? prepare_t<double>(n) : prepare_t<float>(n), "vertex-patch kernel set-up");
+  const cudaError_t pe = prec == TP_FP64   ? prepare_t<double, double>(n)
+                        : prec == TP_FP32 ? prepare_t<float, float>(n)
+                        : prec == TP_FP16 ? prepare_t<__half, float>(n)
+                                          : prepare_t<__nv_bfloat16, float>(n);
+  tp_status st = cuda_status(pe, "vertex-patch kernel set-up");
   if (st == TP_OK) st = cuda_status(cudaMalloc(S_out, hS.size()), "vertex-patch tables");
   if (st == TP_OK) st = cuda_status(cudaMalloc(L_out, hL.size()), "vertex-patch tables");
   if (st == TP_OK) st = cuda_status(cudaMemcpy(*S_out, hS.data(), hS.size(), cudaMemcpyHostToDevice), "cudaMemcpy");
