@@ -26,7 +26,9 @@
 // thread owns one line of its cell along the direction being contracted, so
 // all threads of a warp apply the same 1D coefficients at the same time: the
 // 1D data is a __grid_constant__ kernel parameter and the coefficients are
-// constant-bank operands of the FMAs. Phases: (A) x- and y-lines of
+// constant-bank operands of the FMAs. The x-neighbour rows of the x-faces come from the block's own
+// shared cell tensors where the neighbour is one of the block's cells (cells of a block are
+// consecutive along x). Phases: (A) x- and y-lines of
 // w_x = G_x u + x faces and w_y = G_y u + y faces; (B) z-lines: w = w_x + w_y
 // + G_z u + z faces, then M_z w in registers; (C) y-lines: M_y; (D) x-lines:
 // M_x and the store; given a vector b the store is the residual b - A x instead (the smoother's
@@ -152,6 +154,34 @@ __device__ __forceinline__ void sts_row(float* p, const float (&v)[N]) {
     reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
+// One x-row (N contiguous values) of a cell tensor in shared memory, as 16-byte loads in the
+// float layout with unpadded rows (VX), else value by value.
+template <typename TC, int N, bool VX>
+__device__ __forceinline__ void x_row_shared(TC (&v)[N], const TC* p) {
+  if constexpr (VX) {
+    lds_row<N>(v, p);
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) v[m] = p[m];
+  }
+}
+
+// One x-row of a cell in global memory: 16-byte loads for FP32 vectors with n a multiple of 4
+// (VG: the row starts 16-byte aligned), else value by value.
+template <typename TS, typename TC, int N, bool VG>
+__device__ __forceinline__ void x_row_global(TC (&v)[N], const TS* p) {
+  if constexpr (VG) {
+#pragma unroll
+    for (int k = 0; k < N / 4; ++k) {
+      const float4 t = __ldg(reinterpret_cast<const float4*>(p) + k);
+      v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < N; ++m) v[m] = load_as<TS, TC>(p + m);
+  }
+}
+
 template <typename TS, typename TC, int N, int V, bool RES>
 __global__ void __launch_bounds__(N * N * cc_cells_per_block<N, V>())
 apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restrict__ b,
@@ -215,9 +245,25 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
     }
     contract_d<TC, N>(w, P, false, 0, u);
     if (valid) {
-      const TS* lo = cx > 0 ? xc - N3 + p * N2 + q * N : nullptr;
-      const TS* hi = cx < nx - 1 ? xc + N3 + p * N2 + q * N : nullptr;
-      add_faces<TS, TC, N>(w, u, lo, hi, 1, P, 0);
+      // the x-neighbours' rows: from this block's shared cell tensors where the neighbour cell is
+      // one of the block's (all but the block's first and last cell), else from global memory
+      TC wl[N], wh[N];
+      const bool hl = cx > 0, hh = cx < nx - 1;
+      if (hl) {
+        if (cs > 0) {
+          x_row_shared<TC, N, VX>(wl, base + (cs - 1) * B + ix(p, q, 0));
+        } else {
+          x_row_global<TS, TC, N, VG>(wl, xc - N3 + p * N2 + q * N);
+        }
+      }
+      if (hh) {
+        if (cs + 1 < CPB && cell + 1 < c_end) {
+          x_row_shared<TC, N, VX>(wh, base + (cs + 1) * B + ix(p, q, 0));
+        } else {
+          x_row_global<TS, TC, N, VG>(wh, xc + N3 + p * N2 + q * N);
+        }
+      }
+      add_faces_lines<TC, N>(w, u, wl, hl, wh, hh, P, 0);
     }
     if constexpr (VX) {
       sts_row<N>(sX + ix(p, q, 0), w);

@@ -70,4 +70,38 @@ __device__ __forceinline__ void add_faces(TC (&acc)[N], const TC (&u)[N], const 
   }
 }
 
+// The rank-2 face terms of direction d for a line whose neighbour lines are already in registers:
+// wl / wh the low / high neighbour's line (used only when has_lo / has_hi; a missing neighbour is
+// a boundary face and takes the own-line form, as in add_faces).
+template <typename TC, int N, typename PC>
+__device__ __forceinline__ void add_faces_lines(TC (&acc)[N], const TC (&u)[N], const TC (&wl)[N], bool has_lo,
+                                                const TC (&wh)[N], bool has_hi, const PC& P, int d) {
+  if (has_hi) {
+    TC sd = P.d0[0] * wh[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d0[m], wh[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][0][i], wh[0], fma(P.E[d][1][i], sd, acc[i]));
+  } else {
+    TC sd = P.d1[0] * u[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d1[m], u[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][4][i], u[N - 1], fma(P.E[d][5][i], sd, acc[i]));
+  }
+  if (has_lo) {
+    TC sd = P.d1[0] * wl[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d1[m], wl[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][2][i], wl[N - 1], fma(P.E[d][3][i], sd, acc[i]));
+  } else {
+    TC sd = P.d0[0] * u[0];
+#pragma unroll
+    for (int m = 1; m < N; ++m) sd = fma(P.d0[m], u[m], sd);
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = fma(P.E[d][6][i], u[0], fma(P.E[d][7][i], sd, acc[i]));
+  }
+}
+
 }  // namespace tp
