@@ -9,7 +9,13 @@
 // four columns are zero and are dropped). Each thread keeps its B fragments (the 1D matrices)
 // in registers for the whole kernel; A fragments are read from the cell tensor in shared
 // memory, which holds u, w and one temporary per cell. One warp per cell, no block-wide
-// barriers.
+// barriers. The shared cell tensors are padded against bank conflicts (the concern of Sec. 4.1,
+// met here by padding rather than an XOR permutation): element (l, j, i) sits at l*PL + j*RP + i
+// with RP = 4, PL = 20 for n = 4 and RP = 12, PL = 100 for n = 8. A half-warp's A fragment touches
+// 4 lines x 4 nodes; with these pitches (2 RP and 2 PL are 8 or 24 modulo the 32 banks) its 16
+// doubles fall in 16 distinct bank pairs for lines along x, y and z. For n = 4 every fragment load
+// and store is then conflict-free (the unpadded layout: 4-way along z); for n = 8 the fragment
+// stores of even and odd nodes stay 2-way (unpadded: up to 4-way), half the wavefronts in all.
 //
 // On this part DMMA and DFMA issue to the same FP64 pipe (DMMA measured at 1.05 TFLOP/s, DFMA
 // at 1.19-1.25), so this kernel is the tensor-core comparator of the FP64 apply, not its
@@ -24,16 +30,23 @@ namespace dmma {
 template <int N, int V>
 __host__ __device__ constexpr int cells_per_block() { return (N == 8 ? 4 : 8) * (V == 0 ? 1 : (V == 1 ? 2 : 4)) / 2; }
 
-template <int N, int V>
-__host__ __device__ constexpr size_t smem_bytes() { return sizeof(double) * 3 * N * N * N * cells_per_block<N, V>(); }
+// pitches of the padded shared cell tensor: row (RP) and plane (PL); its size in doubles
+template <int N> __host__ __device__ constexpr int rp() { return N == 8 ? 12 : N; }
+template <int N> __host__ __device__ constexpr int pl() { return N == 8 ? 100 : N * N + 4; }
+template <int N> __host__ __device__ constexpr int cell_pad() { return N * pl<N>(); }
 
-// Offset of node m of line r along direction D in a cell tensor with index (l*N + j)*N + i:
-// D = 0 (x): r = l*N + j; D = 1 (y): r = l*N + i; D = 2 (z): r = j*N + i.
-template <int N, int D>
+template <int N, int V>
+__host__ __device__ constexpr size_t smem_bytes() { return sizeof(double) * 3 * cell_pad<N>() * cells_per_block<N, V>(); }
+
+// Offset of node m of line r along direction D, in the padded shared layout (PAD) or the
+// canonical global layout (l*N + j)*N + i: D = 0 (x): r = l*N + j; D = 1 (y): r = l*N + i;
+// D = 2 (z): r = j*N + i.
+template <int N, int D, bool PAD>
 __device__ __forceinline__ int off(int r, int m) {
-  if (D == 0) return r * N + m;
-  if (D == 1) return (r / N) * N * N + m * N + (r % N);
-  return m * N * N + r;
+  constexpr int R = PAD ? rp<N>() : N, L = PAD ? pl<N>() : N * N;
+  if (D == 0) return (r / N) * L + (r % N) * R + m;
+  if (D == 1) return (r / N) * L + m * R + (r % N);
+  return m * L + (r / N) * R + (r % N);
 }
 
 __device__ __forceinline__ void mma_f64(double& d0, double& d1, double a, double b) {
@@ -44,7 +57,8 @@ __device__ __forceinline__ void mma_f64(double& d0, double& d1, double a, double
 
 // dst[line][i] (+)= sum_m src[line][m] A[i][m] along direction D for all N^2 lines of one cell.
 // bf[ks] is this lane's B fragment A[lane/4][4 ks + lane%4] (0 for rows >= N).
-template <int N, int D, bool ACC>
+// src: a padded shared cell tensor; dst: padded shared (GDST false) or the cell in global memory.
+template <int N, int D, bool ACC, bool GDST = false>
 __device__ __forceinline__ void contract_dmma(double* dst, const double* src, const double (&bf)[N / 4], int lane) {
   constexpr int G = N * N / 8;
   const int rr = lane >> 2, cc = lane & 3, i0 = 2 * cc;
@@ -53,14 +67,14 @@ __device__ __forceinline__ void contract_dmma(double* dst, const double* src, co
     const int r = g * 8 + rr;
     double c0 = 0.0, c1 = 0.0;
     if (ACC && i0 < N) {
-      c0 = dst[off<N, D>(r, i0)];
-      c1 = dst[off<N, D>(r, i0 + 1)];
+      c0 = dst[off<N, D, !GDST>(r, i0)];
+      c1 = dst[off<N, D, !GDST>(r, i0 + 1)];
     }
 #pragma unroll
-    for (int ks = 0; ks < N / 4; ++ks) mma_f64(c0, c1, src[off<N, D>(r, ks * 4 + cc)], bf[ks]);
+    for (int ks = 0; ks < N / 4; ++ks) mma_f64(c0, c1, src[off<N, D, true>(r, ks * 4 + cc)], bf[ks]);
     if (i0 < N) {
-      dst[off<N, D>(r, i0)] = c0;
-      dst[off<N, D>(r, i0 + 1)] = c1;
+      dst[off<N, D, !GDST>(r, i0)] = c0;
+      dst[off<N, D, !GDST>(r, i0 + 1)] = c1;
     }
   }
 }
@@ -74,13 +88,13 @@ __device__ __forceinline__ void faces_dmma(double* sW, const double* sU, const d
     double u[N], acc[N];
 #pragma unroll
     for (int m = 0; m < N; ++m) {
-      u[m] = sU[off<N, D>(r, m)];
+      u[m] = sU[off<N, D, true>(r, m)];
       acc[m] = 0.0;
     }
-    const double* own = xc + off<N, D>(r, 0);
+    const double* own = xc + off<N, D, false>(r, 0);
     add_faces<double, double, N>(acc, u, has_lo ? own - nb : nullptr, has_hi ? own + nb : nullptr, step, P, D);
 #pragma unroll
-    for (int m = 0; m < N; ++m) sW[off<N, D>(r, m)] += acc[m];
+    for (int m = 0; m < N; ++m) sW[off<N, D, true>(r, m)] += acc[m];
   }
 }
 
@@ -91,9 +105,10 @@ apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __
   constexpr int CPB = cells_per_block<N, V>(), N3 = N * N * N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* sU = reinterpret_cast<double*>(smem_raw) + warp * 3 * N3;
-  double* sW = sU + N3;
-  double* sT = sW + N3;
+  constexpr int C = cell_pad<N>();
+  double* sU = reinterpret_cast<double*>(smem_raw) + warp * 3 * C;
+  double* sW = sU + C;
+  double* sT = sW + C;
   const long long cell = c_begin + (long long)blockIdx.x * CPB + warp;  // cells [c_begin, c_end)
   if (cell >= c_end) return;  // whole warp; the kernel has no block-wide barrier
   const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((long long)nx * ny));
@@ -111,7 +126,7 @@ apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __
         bM[d][ks] = io < N ? P.M[d][io * kMaxN + ks * 4 + mk] : 0.0;
       }
   }
-  for (int e = lane; e < N3; e += 32) sU[e] = __ldg(xc + e);
+  for (int e = lane; e < N3; e += 32) sU[(e / (N * N)) * pl<N>() + ((e / N) % N) * rp<N>() + e % N] = __ldg(xc + e);
   __syncwarp();
 
   // w = G_x u + G_y u + G_z u on the tensor cores
@@ -133,7 +148,7 @@ apply_dmma_kernel(const double* __restrict__ x, double* __restrict__ y, const __
   __syncwarp();
   contract_dmma<N, 1, false>(sW, sT, bM[1], lane);
   __syncwarp();
-  contract_dmma<N, 0, false>(y + cell * N3, sW, bM[0], lane);
+  contract_dmma<N, 0, false, true>(y + cell * N3, sW, bM[0], lane);
 }
 
 template <int N, int V>
