@@ -64,12 +64,18 @@ __host__ __device__ constexpr int cc_cells_per_block() {
 template <typename TC, int N> __host__ __device__ constexpr int cc_pitch() {
   return (N > kMaxN || sizeof(TC) == 4) ? N + 1 : N;
 }
-template <int N> __host__ __device__ constexpr int cc_buffers() { return N > kMaxN ? 3 : 4; }
+// FP64 arithmetic accumulates the y-lines into the x-line buffer (one more barrier, one buffer and
+// one FP64 addition per DoF fewer: the FP64 pipe bounds that kernel); other types keep a separate
+// y-line buffer (their kernels are bound by shared-memory instructions, which the merge would add).
+template <typename TC> __host__ __device__ constexpr bool cc_merge_xy() { return sizeof(TC) == 8; }
+template <typename TC, int N> __host__ __device__ constexpr int cc_buffers() {
+  return (N > kMaxN ? 3 : 4) - (cc_merge_xy<TC>() ? 1 : 0);
+}
 template <typename TC, int N> using CcConst = OpConst<TC, (N > kMaxN ? kMaxNHigh : kMaxN)>;
 
 template <typename TC, int N, int V>
 __host__ __device__ constexpr size_t cc_smem_bytes() {
-  return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<N>() * N * N * cc_pitch<TC, N>();
+  return sizeof(TC) * cc_cells_per_block<N, V>() * cc_buffers<TC, N>() * N * N * cc_pitch<TC, N>();
 }
 
 // out = A in for a centrosymmetric A through its even-odd halves (AE, AO of OpConst), H = n/2
@@ -200,10 +206,11 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
   const int cs = tid / N2, t = tid % N2, p = t / N, q = t % N;
+  constexpr bool MXY = cc_merge_xy<TC>();
   TC* sU = base + cs * B;                   // u
-  TC* sX = base + (CPB + cs) * B;           // w_x, later M_y M_z w
-  TC* sY = base + (2 * CPB + cs) * B;       // w_y
-  TC* sZ = cc_buffers<N>() == 4 ? base + (3 * CPB + cs) * B : sU;  // M_z w
+  TC* sX = base + (CPB + cs) * B;           // w_x (with MXY: w_x + w_y), later M_y M_z w
+  TC* sY = MXY ? sX : base + (2 * CPB + cs) * B;  // w_y
+  TC* sZ = N > kMaxN ? sU : base + ((MXY ? 2 : 3) * CPB + cs) * B;  // M_z w
   auto ix = [](int l, int j, int i) { return l * PL + j * RP + i; };
 
   const long long cell = c_begin + (long long)blockIdx.x * CPB + cs;  // cells [c_begin, c_end) of the mesh
@@ -271,6 +278,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
 #pragma unroll
       for (int i = 0; i < N; ++i) sX[ix(p, q, i)] = w[i];
     }
+    if constexpr (MXY) __syncthreads();  // the y-lines add into the x-lines' buffer
 #pragma unroll
     for (int m = 0; m < N; ++m) u[m] = sU[ix(p, m, q)];
     contract_d<TC, N>(w, P, false, 1, u);
@@ -279,8 +287,13 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       const TS* hi = cy < ny - 1 ? xc + sy + p * N2 + q : nullptr;
       add_faces<TS, TC, N>(w, u, lo, hi, N, P, 1);
     }
+    if constexpr (MXY) {
 #pragma unroll
-    for (int j = 0; j < N; ++j) sY[ix(p, j, q)] = w[j];
+      for (int j = 0; j < N; ++j) sX[ix(p, j, q)] += w[j];
+    } else {
+#pragma unroll
+      for (int j = 0; j < N; ++j) sY[ix(p, j, q)] = w[j];
+    }
   }
   __syncthreads();
 
@@ -295,8 +308,13 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       const TS* hi = cz < nz - 1 ? xc + sz + t : nullptr;
       add_faces<TS, TC, N>(w, u, lo, hi, N2, P, 2);
     }
+    if constexpr (MXY) {
 #pragma unroll
-    for (int l = 0; l < N; ++l) w[l] += sX[ix(l, p, q)] + sY[ix(l, p, q)];
+      for (int l = 0; l < N; ++l) w[l] += sX[ix(l, p, q)];
+    } else {
+#pragma unroll
+      for (int l = 0; l < N; ++l) w[l] += sX[ix(l, p, q)] + sY[ix(l, p, q)];
+    }
     contract_d<TC, N>(v, P, true, 2, w);
 #pragma unroll
     for (int l = 0; l < N; ++l) sZ[ix(l, p, q)] = v[l];
