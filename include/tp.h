@@ -77,7 +77,8 @@ typedef struct {
   int autotune; /* 1: at creation, time the tile shapes of the apply kernel (CUDA-core and DMMA:
                    cells per thread block, the default halved, kept or doubled) on this device on a
                    proxy of the mesh (same nx, ny, about 128 MB per vector) and keep the fastest.
-                   Results do not depend on the tile shape. 0 (default): the default shape */
+                   Results do not depend on the tile shape. 0 (default): the default shape, halved
+                   for meshes with fewer cells than two default blocks per SM */
 } tp_op_opts;
 
 /* Tensor kernel (TP_KERNEL_TENSOR). With FP64 vectors (k = 3 and k = 7 only) the six 1D

@@ -460,6 +460,14 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   else
     st = cuda_status(op->opts.kernel == TP_KERNEL_TENSOR ? prepare_tensor(op) : prepare_apply_cc(op),
                      "apply kernel set-up");
+  if (st == TP_OK && op->opts.kernel == TP_KERNEL_CUDA_CORE && op->n <= kMaxN) {
+    // small meshes (fewer cells than two default thread blocks per SM) take the half-size tile: twice
+    // the blocks to spread over the SMs; the results do not depend on the tile shape
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->device) == cudaSuccess && sms > 0 &&
+        op->ncells < 2LL * sms * cc_tile_cells(op->n, 1))
+      op->tile_variant = 0;
+  }
   if (st == TP_OK && o.autotune) st = autotune_apply(op);
   if (st != TP_OK) {
     tp_op_destroy(op);

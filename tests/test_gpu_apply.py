@@ -280,7 +280,9 @@ def test_autotuned_apply_identical_to_default(k, prec, kernel):
     base = (128 // (k + 1) ** 2) or 1
     if kernel == TENSOR:
         base = 4 if k == 7 else 8
-    assert tiles[0] == base and tiles[1] in (max(base // 2, 1), base, 2 * base)
+    elif m.ncells < 2 * torch.cuda.get_device_properties(0).multi_processor_count * base:
+        base = max(base // 2, 1)  # small meshes default to the half-size CUDA-core tile
+    assert tiles[0] == base and tiles[1] in (max(base // 2, 1), base, 2 * base, 4 * base)
     assert torch.equal(outs[0], outs[1])
     assert rel_l2(outs[1].double().numpy(), BlockOperator(m, k).apply(x64)) < TOL[prec]
 
