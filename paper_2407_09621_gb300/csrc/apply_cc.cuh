@@ -145,27 +145,28 @@ __device__ __forceinline__ void contract_d(TC (&out)[N], const CcConst<TC, N>& P
 }
 
 // Shared-memory row helpers of the vector layout (rows of N floats, 16-byte aligned)
+// (16-byte chunk k of the row stored at chunk position k ^ sw: the swizzled layout below)
 template <int N>
-__device__ __forceinline__ void lds_row(float (&v)[N], const float* p) {
+__device__ __forceinline__ void lds_row(float (&v)[N], const float* p, int sw = 0) {
 #pragma unroll
   for (int k = 0; k < N / 4; ++k) {
-    const float4 t = reinterpret_cast<const float4*>(p)[k];
+    const float4 t = reinterpret_cast<const float4*>(p)[k ^ sw];
     v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
   }
 }
 template <int N>
-__device__ __forceinline__ void sts_row(float* p, const float (&v)[N]) {
+__device__ __forceinline__ void sts_row(float* p, const float (&v)[N], int sw = 0) {
 #pragma unroll
   for (int k = 0; k < N / 4; ++k)
-    reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    reinterpret_cast<float4*>(p)[k ^ sw] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
 }
 
 // One x-row (N contiguous values) of a cell tensor in shared memory, as 16-byte loads in the
 // float layout with unpadded rows (VX), else value by value.
 template <typename TC, int N, bool VX>
-__device__ __forceinline__ void x_row_shared(TC (&v)[N], const TC* p) {
+__device__ __forceinline__ void x_row_shared(TC (&v)[N], const TC* p, int sw) {
   if constexpr (VX) {
-    lds_row<N>(v, p);
+    lds_row<N>(v, p, sw);
   } else {
 #pragma unroll
     for (int m = 0; m < N; ++m) v[m] = p[m];
@@ -200,8 +201,16 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   // conflicts; otherwise rows are padded to cc_pitch.
   constexpr bool VX = sizeof(TC) == 4 && (N == 4 || N == 8 || N == 16);
   constexpr bool VG = VX && sizeof(TS) == 4;  // the global x-rows move as float4 as well
-  constexpr int RP = VX ? N : cc_pitch<TC, N>(), PL = VX ? N * (N + 1) : N * RP;
-  constexpr int B = N * PL;  // size of a shared cell tensor
+  // n = 8 with FP32 arithmetic (SW): the row (l, j) is stored at row position r = j ^ l of plane l,
+  // its two 16-byte chunks swapped when r >= 4, so that the x-rows (16-byte accesses), the y-lines
+  // and the z-lines (scalar accesses) of the half cell a warp holds all fall in distinct banks (the
+  // padded layout leaves the x-rows 2-way). For n = 4 the same permutation (with the cells 16 banks
+  // apart) also removes the x-row conflicts, but measured slower (the extra index arithmetic of the
+  // y- and z-lines costs more than the conflicts), so n = 4 keeps the padded planes.
+  constexpr bool SW = VX && N == 8;
+  constexpr int RP = VX ? N : cc_pitch<TC, N>(), PL = SW ? N * N : (VX ? N * (N + 1) : N * RP);
+  // pitch of the shared cell tensors (the allocation of cc_smem_bytes)
+  constexpr int B = N * N * cc_pitch<TC, N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TC* base = reinterpret_cast<TC*>(smem_raw);
   const int tid = threadIdx.x;
@@ -211,7 +220,17 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   TC* sX = base + (CPB + cs) * B;           // w_x (with MXY: w_x + w_y), later M_y M_z w
   TC* sY = MXY ? sX : base + (2 * CPB + cs) * B;  // w_y
   TC* sZ = N > kMaxN ? sU : base + ((MXY ? 2 : 3) * CPB + cs) * B;  // M_z w
-  auto ix = [](int l, int j, int i) { return l * PL + j * RP + i; };
+  auto ix = [](int l, int j, int i) {
+    if constexpr (SW) {
+      const int r = (j ^ l) & (N - 1);
+      return l * PL + r * RP + ((((i >> 2) ^ ((r >> 2) & (N / 4 - 1)))) << 2) + (i & 3);
+    } else {
+      return l * PL + j * RP + i;
+    }
+  };
+  // start of the stored row (l, j) and its chunk permutation
+  auto rowp = [](int l, int j) { return SW ? l * PL + ((j ^ l) & (N - 1)) * RP : l * PL + j * RP; };
+  auto rsw = [](int l, int j) { return SW ? ((((j ^ l) & (N - 1)) >> 2) & (N / 4 - 1)) : 0; };
 
   const long long cell = c_begin + (long long)blockIdx.x * CPB + cs;  // cells [c_begin, c_end) of the mesh
   const bool valid = cell < c_end;
@@ -234,7 +253,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
 #pragma unroll
       for (int i = 0; i < N; ++i) r[i] = TC(0);
     }
-    sts_row<N>(sU + ix(p, q, 0), r);
+    sts_row<N>(sU + rowp(p, q), r, rsw(p, q));
   } else {
 #pragma unroll
     for (int l = 0; l < N; ++l) sU[ix(l, p, q)] = valid ? load_as<TS, TC>(xc + l * N2 + t) : TC(0);
@@ -245,7 +264,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   {
     TC u[N], w[N];
     if constexpr (VX) {
-      lds_row<N>(u, sU + ix(p, q, 0));
+      lds_row<N>(u, sU + rowp(p, q), rsw(p, q));
     } else {
 #pragma unroll
       for (int m = 0; m < N; ++m) u[m] = sU[ix(p, q, m)];
@@ -258,14 +277,14 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       const bool hl = cx > 0, hh = cx < nx - 1;
       if (hl) {
         if (cs > 0) {
-          x_row_shared<TC, N, VX>(wl, base + (cs - 1) * B + ix(p, q, 0));
+          x_row_shared<TC, N, VX>(wl, base + (cs - 1) * B + rowp(p, q), rsw(p, q));
         } else {
           x_row_global<TS, TC, N, VG>(wl, xc - N3 + p * N2 + q * N);
         }
       }
       if (hh) {
         if (cs + 1 < CPB && cell + 1 < c_end) {
-          x_row_shared<TC, N, VX>(wh, base + (cs + 1) * B + ix(p, q, 0));
+          x_row_shared<TC, N, VX>(wh, base + (cs + 1) * B + rowp(p, q), rsw(p, q));
         } else {
           x_row_global<TS, TC, N, VG>(wh, xc + N3 + p * N2 + q * N);
         }
@@ -273,7 +292,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
       add_faces_lines<TC, N>(w, u, wl, hl, wh, hh, P, 0);
     }
     if constexpr (VX) {
-      sts_row<N>(sX + ix(p, q, 0), w);
+      sts_row<N>(sX + rowp(p, q), w, rsw(p, q));
     } else {
 #pragma unroll
       for (int i = 0; i < N; ++i) sX[ix(p, q, i)] = w[i];
@@ -336,7 +355,7 @@ apply_cc_kernel(const TS* __restrict__ x, TS* __restrict__ y, const TS* __restri
   if (valid) {
     TC w[N], v[N];
     if constexpr (VX) {
-      lds_row<N>(w, sX + ix(p, q, 0));
+      lds_row<N>(w, sX + rowp(p, q), rsw(p, q));
     } else {
 #pragma unroll
       for (int m = 0; m < N; ++m) w[m] = sX[ix(p, q, m)];
