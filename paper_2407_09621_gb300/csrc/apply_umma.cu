@@ -22,21 +22,32 @@
 // is a plain operand), and two boxes shifted by one cell along x hold the x-neighbours. The z-terms
 // need no load: a CTA walks a z-segment of one tile column, and the own rows of tile z are also the
 // z+ neighbour rows of tile z - 1 and the z- neighbour rows of tile z + 1, so their products go into
-// those tiles' accumulators (four TMEM accumulators rotate: the tile finishing, the current one,
-// the next one, and one being read by the epilogue). A segment [z0, z1) loads the own rows of tiles
-// z0 - 1 and z1 as halos. That is 52 KB per tile from L2 instead of 112 KB, and the ring of 18 KB
-// slots looks about three tiles ahead.
+// those tiles' accumulators. A segment [z0, z1) loads the own rows of tiles z0 - 1 and z1 as halos.
+// That is 52 KB per tile from L2 instead of 112 KB, and the ring of 18 KB slots looks about three
+// tiles ahead.
+//
+// Issue rate, measured on this part: one thread issues a tcgen05.mma (M = 128, K = 16) only every
+// ~112 cycles, whatever N (64 .. 192) and wherever A sits (shared memory or TMEM), while the
+// tensor pipe finishes an N = 64 product in ~36 cycles when four warps issue. With seven 64 x 64
+// blocks (28 products) per tile a single issuer sets the pace, so two warps issue into separate
+// TMEM accumulators that the epilogue adds, and the own rows take one product for three blocks:
+// the z+, own and z- blocks sit side by side in shared memory and the accumulators of tiles
+// z - 1, z and z + 1 in adjacent TMEM columns (N = 192; split in two where the rotation of four
+// accumulators wraps).
 //
 // One CTA per SM, persistent over work units (a tile column's z-segment), warp-specialized so
 // that loads, products and stores of consecutive tiles overlap:
 //   warp 0      TMA producer: streams the boxes of every tile through the slot ring (and asks L2
 //               to prefetch the window boxes a few tiles ahead);
-//   warp 1      MMA issuer: per operand four tcgen05.mma (M = 128, N = 64, K = 16) into the
-//               accumulator it belongs to, then tcgen05.commit releases the slot and hands each
-//               finished accumulator to the epilogue;
-//   warps 2-9   epilogue, two groups of four warps taking alternate tiles: tcgen05.ld of a
-//               finished accumulator (one cell row per thread), scale, round to the storage type
-//               and store the rows of cells inside the mesh.
+//   warp 1      MMA issuer A: the own rows (z+, own and z- blocks) and the y- rows, into
+//               accumulator set A (TMEM columns 0-255), four tcgen05.mma per operand (K = 16 each);
+//   warp 10     MMA issuer B: the y+ rows and the two x-neighbour boxes, into set B (256-511);
+//               each issuer's tcgen05.commit releases the slots it read, and a tile's accumulators
+//               go to the epilogue when both issuers have committed them;
+//   warps 2-9   epilogue, two groups of four warps taking alternate tiles: tcgen05.ld of both
+//               accumulators of a finished tile (one cell row per thread), add them, zero set A's
+//               (its products all accumulate; set B's first product overwrites), scale, round to
+//               the storage type and store the rows of cells inside the mesh.
 // Algorithm 1 error correction splits each block matrix into a high part and the rounded
 // remainder; both products accumulate into the same FP32 accumulator. The input vector is
 // already in the operand type, so only the matrix needs the split (two products instead of
@@ -70,20 +81,25 @@ constexpr int kTileBytes = kRows * 128;            // one tile box
 constexpr int kWinBytes = (kRows + 2 * kBX) * 128; // the window box: the tile with a y-halo row each side
 constexpr int kSlotBytes = kWinBytes;
 constexpr int kMatBytes = 64 * 128;   // one 64 x 64 16-bit block matrix
-constexpr int kThreads = 320;         // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two groups of four)
+constexpr int kThreads = 352;         // warp 0 TMA, warps 1 and 10 MMA, warps 2-9 epilogue (two groups of four)
 constexpr int kPrefetch = 4;          // tiles ahead whose window box the producer prefetches into L2
+constexpr int kAcc = 4;               // TMEM accumulators of 64 columns per issuer (all 512 columns)
 constexpr int kWaitLimit = 1 << 22;
 
 using Params = UmmaParams;
 
 template <bool EC>
 __host__ __device__ constexpr int nmat() { return EC ? 14 : 7; }
-// ring slots that fit beside the block matrices in 227 KB of shared memory
+// ring slots that fit beside the block matrices in 227 KB of shared memory (at most 32: per-slot bits)
 template <bool EC>
-__host__ __device__ constexpr int nslots() { return EC ? 6 : 9; }
+__host__ __device__ constexpr int nslots() {
+  return (232448 - 2048 - nmat<EC>() * kMatBytes) / kSlotBytes < 32 ? (232448 - 2048 - nmat<EC>() * kMatBytes) / kSlotBytes
+                                                                     : 32;
+}
 template <bool EC>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kSlotBytes + 8 * (2 * nslots<EC>() + 9) + 16;
+  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kSlotBytes + 8 * (2 * nslots<EC>() + 2 * kAcc + 1) +
+         16;
 }
 
 __device__ __forceinline__ uint32_t s2u(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -180,6 +196,16 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return
                  "=r"(r[base + 28]), "=r"(r[base + 29]), "=r"(r[base + 30]), "=r"(r[base + 31])          \
                : "r"(ta))
 
+// 32 columns of zeros into this warp's 32 TMEM lanes
+#define TP_ST32Z(ta)                                                                                       \
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1," \
+               "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(ta), "r"(0u)                      \
+               : "memory")
+
+// Shared-memory position of block matrix b (own, x-, x+, y-, y+, z-, z+): the z+, own and z- blocks
+// sit side by side (in that order), so one product with N = 192 applies all three to the own rows.
+__device__ __forceinline__ int mat_pos(int b) { return b == 6 ? 0 : (b == 0 ? 1 : (b == 5 ? 2 : b + 2)); }
+
 // Boundary-face correction of one cell in FP32: o += s hh (M_t1 (x) M_t2 (x) (e_end beta^T + beta e_end^T)) u
 // for the face of direction D on side SIDE (0: low, beta = d0, end 0, s = +1; 1: high, beta = d1,
 // end 3, s = -1). Node (t1, t2, m) of the line along D at tangential indices (t1, t2): D = 0
@@ -262,45 +288,57 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   unsigned char* sB = base;                      // NMAT block matrices, [out n][in k], swizzled
   unsigned char* sA = base + NMAT * kMatBytes;   // S slots of kSlotBytes
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kSlotBytes);
-  // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[4] (accumulator complete),
-  // acce[4] (accumulator read), drain
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 9);
+  // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[kAcc] (accumulator complete),
+  // acce[kAcc] (accumulator read and zeroed), drain
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * kAcc + 1);
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t bar0 = s2u(bars);
   auto full = [&](int s) { return bar0 + 8u * s; };
   auto empty = [&](int s) { return bar0 + 8u * (S + s); };
   auto accf = [&](int a) { return bar0 + 8u * (2 * S + a); };
-  auto acce = [&](int a) { return bar0 + 8u * (2 * S + 4 + a); };
-  const uint32_t drain = bar0 + 8u * (2 * S + 8);
+  auto acce = [&](int a) { return bar0 + 8u * (2 * S + kAcc + a); };
+  const uint32_t drain = bar0 + 8u * (2 * S + 2 * kAcc);
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(full(s)));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(empty(s)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;\n" ::"r"(empty(s)));  // both issuers
     }
-    for (int a = 0; a < 4; ++a) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(accf(a)));
+    for (int a = 0; a < kAcc; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;\n" ::"r"(accf(a)));  // both issuers
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(acce(a)));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(drain));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;\n" ::"r"(drain));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     *abort = 0;
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(s2u(tslot)), "r"(128 * kAcc));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
-  // block matrices -> shared, swizzled
+  // block matrices -> shared, swizzled, at their positions (the error-correction remainders as a
+  // second set of seven)
   for (int e = tid; e < NMAT * 64 * 8; e += kThreads) {
     const int m = e >> 9, n = (e >> 3) & 63, c = e & 7;
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(mats + ((size_t)m * 64 + n) * 64) + c);
-    *reinterpret_cast<uint4*>(sB + m * kMatBytes + sw_off(n, c)) = v;
+    *reinterpret_cast<uint4*>(sB + (7 * (m / 7) + mat_pos(m % 7)) * kMatBytes + sw_off(n, c)) = v;
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
+  // every product of issuer A accumulates, so its accumulators start at zero (and the epilogue
+  // zeroes each one again after reading it)
+  if (warp >= 2 && warp < 10) {
+    const uint32_t t0 = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(((warp - 2) >> 2) * 32 * kAcc);
+#pragma unroll
+    for (int c = 0; c < kAcc; ++c) TP_ST32Z(t0 + 32u * c);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 
   if (warp == 0) {
     // ---------------------------------------------------------------- TMA producer
@@ -349,36 +387,53 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
       for (int s = 0; s < S; ++s)
         if (issued >> s & 1u) drain_bar(full(s), (iph >> s) & 1u, err, 5);
     }
-  } else if (warp == 1) {
-    // ---------------------------------------------------------------- MMA issuer
+  } else if (warp == 1 || warp == 10) {
+    // ---------------------------------------------------------------- MMA issuers
+    // One thread issues a tcgen05.mma only every ~110 cycles on this part, so two warps issue:
+    // A (warp 1) the own rows (z+, own and z- blocks in one product) and the y- rows into TMEM
+    // columns [0, 64 kAcc); B (warp 10) the y+ rows and the two x-neighbour boxes into columns
+    // [64 kAcc, 128 kAcc). The epilogue adds the two accumulators of a tile. Both walk the whole
+    // slot ring in order: each waits for every slot to fill and releases every slot (a slot is
+    // refilled after both released it), passing over the slots it does not read.
     if (lane == 0) {
+      const bool RA = warp == 1;
       const uint32_t fmt = std::is_same<TO, __nv_bfloat16>::value ? 1u : 0u;
-      // D F32, A/B F16 (0) or BF16 (1), both K-major, N = 64, M = 128
-      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+      // D F32, A/B F16 (0) or BF16 (1), both K-major, M = 128; N = 64 per block in the product
+      const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 4) << 24);
+      const uint32_t tset = tmem + (RA ? 0u : 64u * kAcc);
       int slot = 0;
       uint32_t ph = 0;
       bool ok = true;
-      long long g = 0;  // running index of this CTA's tiles; accumulator g & 3
-      // D[acc] (+)= rows at `a_addr` times block b^T; `init`: the first product into this accumulator
-      auto mma = [&](long long gt, uint32_t a_addr, int b, bool init) {
-        const uint32_t dt = tmem + 64u * (uint32_t)(gt & 3);
+      long long g = 0;  // running index of this CTA's tiles; accumulator g % kAcc
+      // accumulators of tiles gt .. gt + nb - 1 (+)= rows at `a_addr` times the nb blocks from shared
+      // position `pos` on (transposed); a run of accumulators that wraps past the last one of the
+      // set is split in two products; `init`: the first product into a (single) accumulator
+      auto mma = [&](long long gt, uint32_t a_addr, int pos, int nb, bool init) {
+        while (nb > 0) {
+          const int a0 = (int)(gt % kAcc), c = min(nb, kAcc - a0);
+          const uint32_t dt = tset + 64u * (uint32_t)a0;
+          const uint32_t idesc = idesc0 | ((64u * (uint32_t)c >> 3) << 17);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ad = sw128_desc(a_addr + ks * 32);
-          const uint64_t bd = sw128_desc(s2u(sB + b * kMatBytes) + ks * 32);
-          const uint32_t acc = (init && ks == 0) ? 0u : 1u;
-          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                       ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          if (EC) {
-            const uint64_t bl = sw128_desc(s2u(sB + (7 + b) * kMatBytes) + ks * 32);
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint64_t ad = sw128_desc(a_addr + ks * 32);
+            const uint64_t bd = sw128_desc(s2u(sB + pos * kMatBytes) + ks * 32);
+            const uint32_t acc = (init && ks == 0) ? 0u : 1u;
             asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc), "r"(1u));
+                         ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            if (EC) {
+              const uint64_t bl = sw128_desc(s2u(sB + (7 + pos) * kMatBytes) + ks * 32);
+              asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n"
+                           ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc));
+            }
           }
+          gt += c;
+          pos += c;
+          nb -= c;
         }
       };
-      // wait until the epilogue has read the previous tile held by accumulator gt & 3
+      // wait until the epilogue has read the previous tile held by accumulator gt % kAcc
       auto acquire = [&](long long gt) -> bool {
-        if (!wait_bar(acce((int)(gt & 3)), (uint32_t)((gt >> 2) & 1) ^ 1u, abort, err, 2, P.wait_ns)) return false;
+        if (!wait_bar(acce((int)(gt % kAcc)), (uint32_t)((gt / kAcc) & 1) ^ 1u, abort, err, 2, P.wait_ns)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         return true;
       };
@@ -387,62 +442,80 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         return s2u(sA + slot * kSlotBytes);
       };
-      auto release = [&]() {
+      auto release = [&]() {  // once the products issued so far are done
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(empty(slot))
                      : "memory");
         if (++slot == S) { slot = 0; ph ^= 1u; }
       };
+      auto pass = [&]() -> bool {  // a slot this issuer does not read: release it once it is full
+        if (!wait_bar(full(slot), ph, abort, err, 3, P.wait_ns)) return false;
+        arrive(empty(slot));
+        if (++slot == S) { slot = 0; ph ^= 1u; }
+        return true;
+      };
       auto finish = [&](long long gt) {
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                     ::"r"(accf((int)(gt & 3))) : "memory");
+                     ::"r"(accf((int)(gt % kAcc))) : "memory");
       };
       for (long long u = blockIdx.x; u < P.units && ok; u += gridDim.x) {
         const Unit w = unit_of(u, P);
         const long long g0 = g;
-        bool inited = false;  // accumulator of the current tile holds a product already
+        bool held = false;  // A: the accumulator of the current tile is acquired already
         if (w.z0 > 0) {  // halo below: the z- neighbour rows of tile z0
-          uint32_t a;
-          if (!(ok = acquire(g0)) || !(a = take())) { ok = false; break; }
-          mma(g0, a, 5, true);
-          release();
-          inited = true;
+          if (RA) {
+            uint32_t a;
+            if (!(ok = acquire(g0)) || !(a = take())) { ok = false; break; }
+            mma(g0, a, mat_pos(5), 1, false);
+            release();
+            held = true;
+          } else if (!(ok = pass())) {
+            break;
+          }
         }
         for (int z = w.z0; z < w.z1 && ok; ++z) {
           const long long gz = g0 + (z - w.z0);
           uint32_t a;
           if (!(a = take())) { ok = false; break; }
-          // the window: y- rows at offset 0, own rows at 8, y+ rows at 16 (rows of 128 bytes)
-          const uint32_t own = a + 8 * 128;
-          if (z + 1 < w.z1) {  // own rows are the z- neighbour rows of tile z + 1
-            if (!(ok = acquire(gz + 1))) break;
-            mma(gz + 1, own, 5, true);
+          // the window: y- rows at offset 0, own rows at kBX, y+ rows at 2 kBX (rows of 128 bytes)
+          if (RA) {
+            if (!held && !(ok = acquire(gz))) break;
+            if (z + 1 < w.z1 && !(ok = acquire(gz + 1))) break;
+            // the own rows are also the z+ neighbour rows of tile z - 1 (its last product from A)
+            // and the z- neighbour rows of tile z + 1: one product applies the z+, own and z- blocks
+            // to them, over the tiles of this segment among z - 1, z, z + 1
+            const int lo = z > w.z0 ? -1 : 0, hi = z + 1 < w.z1 ? 1 : 0;
+            mma(gz + lo, a + kBX * 128, 1 + lo, hi - lo + 1, false);
+            if (lo < 0) finish(gz - 1);
+            mma(gz, a, mat_pos(3), 1, false);
+            release();
+            if (!(ok = pass() && pass())) break;  // the x-neighbour boxes
+            held = true;  // tile z + 1 was acquired above (or does not exist in this segment)
+          } else {
+            if (!(ok = acquire(gz))) break;
+            mma(gz, a + 2 * kBX * 128, mat_pos(4), 1, true);
+            release();
+            if (!(a = take())) { ok = false; break; }
+            mma(gz, a, mat_pos(1), 1, false);
+            release();
+            if (!(a = take())) { ok = false; break; }
+            mma(gz, a, mat_pos(2), 1, false);
+            release();
+            finish(gz);
           }
-          if (!inited && !(ok = acquire(gz))) break;
-          mma(gz, own, 0, !inited);
-          mma(gz, a, 3, false);
-          mma(gz, a + 16 * 128, 4, false);
-          if (z > w.z0) {  // own rows are the z+ neighbour rows of tile z - 1, its last product
-            mma(gz - 1, own, 6, false);
-            finish(gz - 1);
-          }
-          release();
-          if (!(a = take())) { ok = false; break; }
-          mma(gz, a, 1, false);
-          release();
-          if (!(a = take())) { ok = false; break; }
-          mma(gz, a, 2, false);
-          release();
-          inited = true;  // tile z + 1 was initialized above (or does not exist in this segment)
         }
         if (!ok) break;
         const long long glast = g0 + (w.z1 - w.z0) - 1;
         if (w.z1 < P.nz) {  // halo above: the z+ neighbour rows of the last tile
-          uint32_t a;
-          if (!(a = take())) { ok = false; break; }
-          mma(glast, a, 6, false);
-          release();
+          if (RA) {
+            uint32_t a;
+            if (!(a = take())) { ok = false; break; }
+            mma(glast, a, mat_pos(6), 1, false);
+            release();
+          } else if (!(ok = pass())) {
+            break;
+          }
         }
-        finish(glast);
+        if (RA) finish(glast);
         g = glast + 1;
       }
       // every product issued so far has finished before TMEM is released
@@ -461,18 +534,26 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
       const Unit w = unit_of(u, P);
       for (int z = w.z0; z < w.z1; ++z, ++g) {
         if ((int)(g & 1) != grp) continue;
-        const int a = (int)(g & 3);
+        const int a = (int)(g % kAcc);
         // warp-uniform decision: the TMEM loads below are .sync.aligned
-        if (!__all_sync(0xffffffffu, wait_bar(accf(a), (uint32_t)((g >> 2) & 1), abort, err, 7, P.wait_ns))) {
+        if (!__all_sync(0xffffffffu, wait_bar(accf(a), (uint32_t)((g / kAcc) & 1), abort, err, 7, P.wait_ns))) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        uint32_t r[64];
-        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * (uint32_t)a;
-        TP_LD32(r, 0, ta);
-        TP_LD32(r, 32, ta + 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        uint32_t r[64], rb[32];
+        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * (uint32_t)a, tb = ta + 64u * kAcc;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // the two issuers' accumulators, 32 columns at a time
+          TP_LD32(r, 32 * h, ta + 32 * h);
+          TP_LD32(rb, 0, tb + 32 * h);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 32; ++q) r[32 * h + q] = __float_as_uint(__uint_as_float(r[32 * h + q]) + __uint_as_float(rb[q]));
+        }
+        TP_ST32Z(ta);
+        TP_ST32Z(ta + 32);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         arrive(acce(a));
         const int cx = w.x0 + (row & (kBX - 1)), cy = w.y0 + row / kBX;
@@ -493,7 +574,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(256));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128 * kAcc));
   }
 }
 
