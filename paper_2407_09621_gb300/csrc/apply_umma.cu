@@ -90,16 +90,22 @@ using Params = UmmaParams;
 
 template <bool EC>
 __host__ __device__ constexpr int nmat() { return EC ? 14 : 7; }
+// Output staging: without error correction each epilogue warp writes its 32 rows (4 KB, 8 x 4
+// cells) into shared memory and stores them with one TMA box; with it, the products bound the
+// kernel and the ring needs the room, so rows are stored from registers.
+template <bool EC>
+__host__ __device__ constexpr int stage_bytes() { return EC ? 0 : 8 * 4096; }
 // ring slots that fit beside the block matrices in 227 KB of shared memory (at most 32: per-slot bits)
 template <bool EC>
 __host__ __device__ constexpr int nslots() {
-  return (232448 - 2048 - nmat<EC>() * kMatBytes) / kSlotBytes < 32 ? (232448 - 2048 - nmat<EC>() * kMatBytes) / kSlotBytes
-                                                                     : 32;
+  return (232448 - 2048 - nmat<EC>() * kMatBytes - stage_bytes<EC>()) / kSlotBytes < 32
+             ? (232448 - 2048 - nmat<EC>() * kMatBytes - stage_bytes<EC>()) / kSlotBytes
+             : 32;
 }
 template <bool EC>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kSlotBytes + 8 * (2 * nslots<EC>() + 2 * kAcc + 1) +
-         16;
+  return 1024 + (size_t)nmat<EC>() * kMatBytes + (size_t)nslots<EC>() * kSlotBytes + stage_bytes<EC>() +
+         8 * (2 * nslots<EC>() + 2 * kAcc + 1) + 16;
 }
 
 __device__ __forceinline__ uint32_t s2u(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -280,14 +286,15 @@ __device__ __forceinline__ Unit unit_of(long long u, const Params& P) {
 template <typename TO, bool EC>
 __global__ void __launch_bounds__(kThreads, 1)
 apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant__ CUtensorMap tmt,
-                  const TO* __restrict__ x, TO* __restrict__ y, const TO* __restrict__ mats,
+                  const __grid_constant__ CUtensorMap tmy, const TO* __restrict__ x, TO* __restrict__ y, const TO* __restrict__ mats,
                   const __grid_constant__ Params P, int* __restrict__ err) {
   constexpr int NMAT = nmat<EC>(), S = nslots<EC>();
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sB = base;                      // NMAT block matrices, [out n][in k], swizzled
   unsigned char* sA = base + NMAT * kMatBytes;   // S slots of kSlotBytes
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kSlotBytes);
+  unsigned char* sY = sA + S * kSlotBytes;       // output staging, 4 KB per epilogue warp
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sY + stage_bytes<EC>());
   // full[S] (TMA landed), empty[S] (MMAs done with the slot), accf[kAcc] (accumulator complete),
   // acce[kAcc] (accumulator read and zeroed), drain
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * S + 2 * kAcc + 1);
@@ -556,20 +563,49 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         arrive(acce(a));
-        const int cx = w.x0 + (row & (kBX - 1)), cy = w.y0 + row / kBX;
-        if (cx < P.nx && cy < P.ny) {
-          uint4* dst = reinterpret_cast<uint4*>(y + (((long long)z * P.ny + cy) * P.nx + cx) * 64);
+        if (stage_bytes<EC>() > 0) {
+          // this warp's 32 rows are the 8 x 4 cells at (w.x0, w.y0 + 4 q4, z): swizzled into its
+          // staging buffer (conflict-free), then one TMA store; cells outside the mesh are clipped
+          const uint32_t sb = s2u(sY + (warp - 2) * 4096);
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");  // buffer read out
+          __syncwarp();
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             uint4 ov;
             TO* h = reinterpret_cast<TO*>(&ov);
 #pragma unroll
             for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
-            dst[c] = ov;
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};\n" ::"r"(sb + (uint32_t)sw_off(lane, c)), "r"(ov.x),
+                         "r"(ov.y), "r"(ov.z), "r"(ov.w)
+                         : "memory");
+          }
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          __syncwarp();
+          if (lane == 0 && w.y0 + 4 * q4 < P.ny) {
+            asm volatile(
+                "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n"
+                ::"l"((uint64_t)&tmy), "r"(0), "r"(w.x0), "r"(w.y0 + 4 * q4), "r"(z), "r"(sb)
+                : "memory");
+            asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+          }
+        } else {
+          const int cx = w.x0 + (row & (kBX - 1)), cy = w.y0 + row / kBX;
+          if (cx < P.nx && cy < P.ny) {
+            uint4* dst = reinterpret_cast<uint4*>(y + (((long long)z * P.ny + cy) * P.nx + cx) * 64);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              uint4 ov;
+              TO* h = reinterpret_cast<TO*>(&ov);
+#pragma unroll
+              for (int q = 0; q < 8; ++q) h[q] = from_f<TO>(__uint_as_float(r[c * 8 + q]) * P.out_scale);
+              dst[c] = ov;
+            }
           }
         }
       }
     }
+    // the staged stores have landed before the kernel ends (the boundary kernel reads them next)
+    if (stage_bytes<EC>() > 0 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
   __syncthreads();
   if (warp == 1) {
@@ -783,17 +819,20 @@ static cudaError_t umma_launch_t(const tp_op_s* op, void* y, const void* x, cuda
   cuuint32_t estr[4] = {1, 1, 1, 1};
   cuuint32_t boxw[4] = {64, (cuuint32_t)umma::kBX, (cuuint32_t)(umma::kBY + 2), 1};
   cuuint32_t boxt[4] = {64, (cuuint32_t)umma::kBX, (cuuint32_t)umma::kBY, 1};
-  CUtensorMap tmw, tmt;
+  cuuint32_t boxy[4] = {64, (cuuint32_t)umma::kBX, 4, 1};  // one epilogue warp's 32 output rows
+  CUtensorMap tmw, tmt, tmy;
   if (enc(&tmw, dt, 4, const_cast<void*>(x), dims, strides, boxw, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
           CUDA_SUCCESS ||
       enc(&tmt, dt, 4, const_cast<void*>(x), dims, strides, boxt, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-          CUDA_SUCCESS)
+          CUDA_SUCCESS ||
+      enc(&tmy, dt, 4, y, dims, strides, boxy, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   const int grid = (int)(P.units < op->sm_count ? P.units : op->sm_count);
   umma::apply_umma_kernel<TO, EC><<<grid, umma::kThreads, umma::smem_bytes<EC>(), s>>>(
-      tmw, tmt, static_cast<const TO*>(x), static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P,
+      tmw, tmt, tmy, static_cast<const TO*>(x), static_cast<TO*>(y), static_cast<const TO*>(op->umma_mats), P,
       op->umma_err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
