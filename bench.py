@@ -78,6 +78,8 @@ def parse():
                    help="print only the apply throughput for degrees 1..15 (FP64 and FP32) and exit")
     p.add_argument("--solve-only", action="store_true",
                    help="only the Sec. 7.2 Poisson solves at --k/--cells (for profiler captures)")
+    p.add_argument("--umma-issue", action="store_true",
+                   help="print only the tcgen05.mma issue-rate table (libtp_bench.so) and exit")
     return p.parse_args()
 
 
@@ -146,11 +148,15 @@ class Clocks:
 
 
 def bench_lib():
-    """libtp_bench.so (include/tp_bench.h): the FMA-pipe peak probe, measurement support only."""
+    """libtp_bench.so (include/tp_bench.h): the FMA-pipe peak and tcgen05 issue-rate probes, measurement
+    support only."""
     import ctypes
     lib = ctypes.CDLL(os.path.join(ROOT, "paper_2407_09621_gb300", "libtp_bench.so"))
     lib.tp_bench_fma_peak.restype = ctypes.c_int
     lib.tp_bench_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.tp_bench_umma_issue.restype = ctypes.c_int
+    lib.tp_bench_umma_issue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
     lib.tp_bench_last_error.restype = ctypes.c_char_p
     return lib
 
@@ -164,6 +170,24 @@ def fma_peak(precision, stream):
     if st != 0:
         raise RuntimeError(f"tp_bench_fma_peak: {lib.tp_bench_last_error().decode()}")
     return out.value
+
+
+def umma_issue_table(stream):
+    """SM cycles per tcgen05.mma (M = 128, K = 16) by N, issuing warps and the place of A: the rates that
+    shape the tensor-core apply (one issuing thread is the limit there, not the tensor pipe)."""
+    import ctypes
+    lib = bench_lib()
+    rows = []
+    for a_in_tmem in (0, 1):
+        for n, iss in ((64, 1), (128, 1), (192, 1), (256, 1), (64, 2), (192, 2), (64, 4)):
+            clk, tf = ctypes.c_double(), ctypes.c_double()
+            st = lib.tp_bench_umma_issue(n, iss, a_in_tmem, ctypes.byref(clk), ctypes.byref(tf),
+                                         ctypes.c_void_p(stream.cuda_stream))
+            if st != 0:
+                raise RuntimeError(f"tp_bench_umma_issue: {lib.tp_bench_last_error().decode()}")
+            rows.append({"a": "tmem" if a_in_tmem else "smem", "n": n, "issuers": iss,
+                         "cycles_per_mma": round(clk.value, 1), "tflops": round(tf.value, 1)})
+    return rows
 
 
 # the device-code sources of each kernel whose ncu counters a profile summary records
@@ -633,6 +657,9 @@ def run_ours(args):
     if args.vcycle_only:
         print(json.dumps({"vcycle_only": True, **vcycle_bench(kdeg, nc, args.prec, args.smoother, args.steps,
                                                                args.warmup)}), flush=True)
+        return
+    if args.umma_issue:
+        print(json.dumps({"umma_issue": umma_issue_table(torch.cuda.current_stream())}), flush=True)
         return
     if args.sweep_only:
         print(json.dumps({"sweep_only": True, "degree_sweep": degree_sweep(torch.cuda.current_stream())}),

@@ -17,7 +17,7 @@ def test_header_functions_are_exported():
 
 
 def test_bench_support_library_is_separate():
-    """The FMA-peak probe (include/tp_bench.h) lives in libtp_bench.so, not in the method's library."""
+    """The measurement probes (include/tp_bench.h) live in libtp_bench.so, not in the method's library."""
     import os
     hdr = os.path.join(_lib.INCLUDE, "tp_bench.h")
     names = _lib.header_functions([hdr])
@@ -31,6 +31,17 @@ def test_bench_support_library_is_separate():
     bench.tp_bench_last_error.restype = ctypes.c_char_p
     assert bench.tp_bench_fma_peak(0, None, None) == _lib.TP_ERR_INVALID_ARG
     assert b"NULL" in bench.tp_bench_last_error()
+    assert not hasattr(_lib.lib, "tp_bench_umma_issue")
+    bench.tp_bench_umma_issue.restype = ctypes.c_int
+    bench.tp_bench_umma_issue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]
+    out = (ctypes.c_double * 2)()
+    p0, p1 = ctypes.byref(out, 0), ctypes.byref(out, 8)
+    assert bench.tp_bench_umma_issue(64, 1, 0, None, p1, None) == _lib.TP_ERR_INVALID_ARG
+    # rejected before any device work: N outside {64, 128, 192, 256}, 3 issuers, too many TMEM columns
+    for n, iss, tm in ((96, 1, 0), (64, 3, 0), (256, 4, 0), (256, 2, 1)):
+        assert bench.tp_bench_umma_issue(n, iss, tm, p0, p1, None) == _lib.TP_ERR_INVALID_ARG
+        assert b"issuers" in bench.tp_bench_last_error()
 
 
 def test_mesh_validation():
