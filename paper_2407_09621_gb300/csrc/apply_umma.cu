@@ -39,9 +39,11 @@
 // that loads, products and stores of consecutive tiles overlap:
 //   warp 0      TMA producer: streams the boxes of every tile through the slot ring (and asks L2
 //               to prefetch the window boxes a few tiles ahead);
-//   warp 1      MMA issuer A: the own rows (z+, own and z- blocks) and the y- rows, into
-//               accumulator set A (TMEM columns 0-255), four tcgen05.mma per operand (K = 16 each);
-//   warp 10     MMA issuer B: the y+ rows and the two x-neighbour boxes, into set B (256-511);
+//   warp 1      MMA issuer A: the own rows (z+, own and z- blocks) and, without error correction,
+//               the y- rows, into accumulator set A (TMEM columns 0-255), four tcgen05.mma per
+//               operand (K = 16 each);
+//   warp 10     MMA issuer B: the y+ rows and the two x-neighbour boxes (with error correction
+//               also the y- rows), into set B (256-511);
 //               each issuer's tcgen05.commit releases the slots it read, and a tile's accumulators
 //               go to the epilogue when both issuers have committed them;
 //   warps 2-9   epilogue, two groups of four warps taking alternate tiles: tcgen05.ld of both
@@ -49,7 +51,10 @@
 //               (its products all accumulate; set B's first product overwrites), scale, round to
 //               the storage type and store the rows of cells inside the mesh.
 // Algorithm 1 error correction splits each block matrix into a high part and the rounded
-// remainder; both products accumulate into the same FP32 accumulator. The input vector is
+// remainder. For the own rows both products accumulate into the same FP32 accumulator; for each
+// shifted operand the high part and the remainder sit side by side in shared memory and one
+// N = 128 product (as costly to issue as one N = 64 product, and reading the operand once) writes
+// two adjacent accumulators that the epilogue adds. The input vector is
 // already in the operand type, so only the matrix needs the split (two products instead of
 // three), and because the matrices are normalized by a power of two (largest entry in
 // [32, 64)) the remainder needs no 2^s scaling: remainders below the FP16 normal range lose at
@@ -208,9 +213,16 @@ __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return
                "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};\n" ::"r"(ta), "r"(0u)                      \
                : "memory")
 
-// Shared-memory position of block matrix b (own, x-, x+, y-, y+, z-, z+): the z+, own and z- blocks
-// sit side by side (in that order), so one product with N = 192 applies all three to the own rows.
-__device__ __forceinline__ int mat_pos(int b) { return b == 6 ? 0 : (b == 0 ? 1 : (b == 5 ? 2 : b + 2)); }
+// Shared-memory position of block matrix b (own, x-, x+, y-, y+, z-, z+; lo = 1: its Algorithm 1
+// remainder). The z+, own and z- blocks sit side by side (in that order), so one product with
+// N = 192 applies all three to the own rows; their remainders follow them. With error correction
+// each of the four shifted blocks is followed by its remainder, so one product with N = 128 applies
+// both, into two adjacent accumulators that the epilogue adds.
+template <bool EC>
+__device__ __forceinline__ int mat_pos(int b, int lo) {
+  if (b == 6 || b == 0 || b == 5) return (b == 6 ? 0 : (b == 0 ? 1 : 2)) + (EC && lo ? 3 : 0);
+  return EC ? 6 + 2 * (b - 1) + lo : b + 2;
+}
 
 // Boundary-face correction of one cell in FP32: o += s hh (M_t1 (x) M_t2 (x) (e_end beta^T + beta e_end^T)) u
 // for the face of direction D on side SIDE (0: low, beta = d0, end 0, s = +1; 1: high, beta = d1,
@@ -329,7 +341,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   for (int e = tid; e < NMAT * 64 * 8; e += kThreads) {
     const int m = e >> 9, n = (e >> 3) & 63, c = e & 7;
     const uint4 v = __ldg(reinterpret_cast<const uint4*>(mats + ((size_t)m * 64 + n) * 64) + c);
-    *reinterpret_cast<uint4*>(sB + (7 * (m / 7) + mat_pos(m % 7)) * kMatBytes + sw_off(n, c)) = v;
+    *reinterpret_cast<uint4*>(sB + mat_pos<EC>(m % 7, m / 7) * kMatBytes + sw_off(n, c)) = v;
   }
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   __syncthreads();
@@ -397,11 +409,14 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
   } else if (warp == 1 || warp == 10) {
     // ---------------------------------------------------------------- MMA issuers
     // One thread issues a tcgen05.mma only every ~110 cycles on this part, so two warps issue:
-    // A (warp 1) the own rows (z+, own and z- blocks in one product) and the y- rows into TMEM
-    // columns [0, 64 kAcc); B (warp 10) the y+ rows and the two x-neighbour boxes into columns
-    // [64 kAcc, 128 kAcc). The epilogue adds the two accumulators of a tile. Both walk the whole
-    // slot ring in order: each waits for every slot to fill and releases every slot (a slot is
-    // refilled after both released it), passing over the slots it does not read.
+    // A (warp 1) the own rows (z+, own and z- blocks in one product) into TMEM columns
+    // [0, 64 kAcc), and without error correction also the y- rows; B (warp 10) the other shifted
+    // operands into columns [64 kAcc, 128 kAcc): the y+ rows and the two x-neighbour boxes, and with
+    // error correction also the y- rows, each as one N = 128 product (high part and remainder into
+    // two adjacent accumulators, two tiles' worth rotating) instead of two N = 64 products. The
+    // epilogue adds a tile's accumulators. Both issuers walk the whole slot ring in order: each
+    // waits for every slot to fill and releases every slot (a slot is refilled after both released
+    // it), passing over the slots it does not read.
     if (lane == 0) {
       const bool RA = warp == 1;
       const uint32_t fmt = std::is_same<TO, __nv_bfloat16>::value ? 1u : 0u;
@@ -412,10 +427,10 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
       uint32_t ph = 0;
       bool ok = true;
       long long g = 0;  // running index of this CTA's tiles; accumulator g % kAcc
-      // accumulators of tiles gt .. gt + nb - 1 (+)= rows at `a_addr` times the nb blocks from shared
-      // position `pos` on (transposed); a run of accumulators that wraps past the last one of the
-      // set is split in two products; `init`: the first product into a (single) accumulator
-      auto mma = [&](long long gt, uint32_t a_addr, int pos, int nb, bool init) {
+      // A: accumulators of tiles gt .. gt + nb - 1 (+)= rows at `a_addr` times the nb blocks from
+      // shared position `pos` on (transposed), and with error correction their remainders (from
+      // pos + 3); a run of accumulators that wraps past the last one of the set is split in two
+      auto mma = [&](long long gt, uint32_t a_addr, int pos, int nb) {
         while (nb > 0) {
           const int a0 = (int)(gt % kAcc), c = min(nb, kAcc - a0);
           const uint32_t dt = tset + 64u * (uint32_t)a0;
@@ -424,11 +439,10 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
           for (int ks = 0; ks < 4; ++ks) {
             const uint64_t ad = sw128_desc(a_addr + ks * 32);
             const uint64_t bd = sw128_desc(s2u(sB + pos * kMatBytes) + ks * 32);
-            const uint32_t acc = (init && ks == 0) ? 0u : 1u;
-            asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                         ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n"
+                         ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc));
             if (EC) {
-              const uint64_t bl = sw128_desc(s2u(sB + (7 + pos) * kMatBytes) + ks * 32);
+              const uint64_t bl = sw128_desc(s2u(sB + (pos + 3) * kMatBytes) + ks * 32);
               asm volatile("tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n"
                            ::"r"(dt), "l"(ad), "l"(bl), "r"(idesc));
             }
@@ -436,6 +450,22 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
           gt += c;
           pos += c;
           nb -= c;
+        }
+      };
+      // B: the accumulator of tile gt (+)= rows at `a_addr` times shifted block b (with error
+      // correction: its high part and remainder, N = 128, into two adjacent accumulators);
+      // `init`: the first product of the tile
+      auto mmaB = [&](long long gt, uint32_t a_addr, int b, bool init) {
+        const uint32_t dt = EC ? tset + 128u * (uint32_t)(gt & 1) : tset + 64u * (uint32_t)(gt % kAcc);
+        const uint32_t idesc = idesc0 | (((EC ? 128u : 64u) >> 3) << 17);
+        const uint32_t bb = s2u(sB + mat_pos<EC>(b, 0) * kMatBytes);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ad = sw128_desc(a_addr + ks * 32);
+          const uint64_t bd = sw128_desc(bb + ks * 32);
+          const uint32_t acc = (init && ks == 0) ? 0u : 1u;
+          asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                       ::"r"(dt), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
         }
       };
       // wait until the epilogue has read the previous tile held by accumulator gt % kAcc
@@ -472,7 +502,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
           if (RA) {
             uint32_t a;
             if (!(ok = acquire(g0)) || !(a = take())) { ok = false; break; }
-            mma(g0, a, mat_pos(5), 1, false);
+            mma(g0, a, mat_pos<EC>(5, 0), 1);
             release();
             held = true;
           } else if (!(ok = pass())) {
@@ -491,21 +521,24 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
             // and the z- neighbour rows of tile z + 1: one product applies the z+, own and z- blocks
             // to them, over the tiles of this segment among z - 1, z, z + 1
             const int lo = z > w.z0 ? -1 : 0, hi = z + 1 < w.z1 ? 1 : 0;
-            mma(gz + lo, a + kBX * 128, 1 + lo, hi - lo + 1, false);
+            mma(gz + lo, a + kBX * 128, 1 + lo, hi - lo + 1);
             if (lo < 0) finish(gz - 1);
-            mma(gz, a, mat_pos(3), 1, false);
+            if (!EC) mma(gz, a, mat_pos<EC>(3, 0), 1);
             release();
             if (!(ok = pass() && pass())) break;  // the x-neighbour boxes
             held = true;  // tile z + 1 was acquired above (or does not exist in this segment)
           } else {
-            if (!(ok = acquire(gz))) break;
-            mma(gz, a + 2 * kBX * 128, mat_pos(4), 1, true);
+            // set B rotates kAcc accumulators of 64 columns, or with error correction two pairs of
+            // 64: wait for the epilogue to have read tile gz - kAcc (gz - 2)
+            if (!(ok = acquire(EC ? gz + kAcc - 2 : gz))) break;
+            if (EC) mmaB(gz, a, 3, true);
+            mmaB(gz, a + 2 * kBX * 128, 4, !EC);
             release();
             if (!(a = take())) { ok = false; break; }
-            mma(gz, a, mat_pos(1), 1, false);
+            mmaB(gz, a, 1, false);
             release();
             if (!(a = take())) { ok = false; break; }
-            mma(gz, a, mat_pos(2), 1, false);
+            mmaB(gz, a, 2, false);
             release();
             finish(gz);
           }
@@ -516,7 +549,7 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
           if (RA) {
             uint32_t a;
             if (!(a = take())) { ok = false; break; }
-            mma(glast, a, mat_pos(6), 1, false);
+            mma(glast, a, mat_pos<EC>(6, 0), 1);
             release();
           } else if (!(ok = pass())) {
             break;
@@ -549,14 +582,24 @@ apply_umma_kernel(const __grid_constant__ CUtensorMap tmw, const __grid_constant
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         uint32_t r[64], rb[32];
-        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * (uint32_t)a, tb = ta + 64u * kAcc;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q4) << 16) + 64u * (uint32_t)a;
+        // set B: the tile's accumulator, or with error correction its high-part and remainder pair
+        const uint32_t tb = EC ? tmem + ((uint32_t)(32 * q4) << 16) + 64u * kAcc + 128u * (uint32_t)(g & 1)
+                               : ta + 64u * kAcc;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // the two issuers' accumulators, 32 columns at a time
+        for (int h = 0; h < 2; ++h) {  // the issuers' accumulators, 32 columns at a time
           TP_LD32(r, 32 * h, ta + 32 * h);
           TP_LD32(rb, 0, tb + 32 * h);
           asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
           for (int q = 0; q < 32; ++q) r[32 * h + q] = __float_as_uint(__uint_as_float(r[32 * h + q]) + __uint_as_float(rb[q]));
+          if (EC) {
+            TP_LD32(rb, 0, tb + 64 + 32 * h);
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+              r[32 * h + q] = __float_as_uint(__uint_as_float(r[32 * h + q]) + __uint_as_float(rb[q]));
+          }
         }
         TP_ST32Z(ta);
         TP_ST32Z(ta + 32);
