@@ -5,6 +5,14 @@
 
 namespace tp {
 
+// n = 2 with FP32 arithmetic: one thread per cell (apply_cpt.cu)
+cudaError_t launch_apply_cpt_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                   cudaStream_t s, const void* b);
+
+// The CUDA-core apply of this operator runs the cell-per-thread kernel (one tile shape, 128 cells
+// per block) instead of the line-per-thread one.
+bool cc_cell_per_thread(const tp_op_s* op) { return op->n == 2 && op->prec != TP_FP64; }
+
 // n > 8, FP64 and FP32 vectors (apply_cc_high.cu)
 cudaError_t prepare_apply_cc_high(const tp_op_s* op);
 cudaError_t launch_apply_cc_high(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
@@ -64,6 +72,7 @@ int cc_tile_cells(int n, int v) {
 cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
                                   cudaStream_t s, const void* b) {
   if (op->n > kMaxN) return launch_apply_cc_high(op, y, x, c0, c1, s, b);
+  if (cc_cell_per_thread(op)) return launch_apply_cpt_range(op, y, x, c0, c1, s, b);
   switch (op->prec) {
     case TP_FP64: return launch_cc_t<double, double>(op, y, x, c0, c1, s, b);
     case TP_FP32: return launch_cc_t<float, float>(op, y, x, c0, c1, s, b);

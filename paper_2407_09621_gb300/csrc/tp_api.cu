@@ -59,6 +59,7 @@ cudaError_t launch_residual(const tp_op_s* op, void* r, const void* b, const voi
 }
 
 int cc_tile_cells(int n, int v);
+bool cc_cell_per_thread(const tp_op_s* op);
 int dmma_tile_cells(int n, int v);
 size_t elem_bytes(tp_precision p);
 
@@ -73,6 +74,7 @@ static tp_status autotune_apply(tp_op_s* op) {
   if (op->opts.kernel == TP_KERNEL_TENSOR && !dm) return TP_OK;  // tcgen05 / mma.sync: fixed tiles
   if (op->opts.kernel == TP_KERNEL_PATCH) return TP_OK;           // one patch per thread block
   if (op->n > kMaxN) return TP_OK;                                 // n > 8: one tile shape
+  if (op->opts.kernel == TP_KERNEL_CUDA_CORE && cc_cell_per_thread(op)) return TP_OK;  // one shape
   const long long eb = (long long)elem_bytes(op->prec);
   const long long n3 = (long long)op->n * op->n * op->n;
   const long long slab = (long long)op->mesh.nx * op->mesh.ny;
@@ -496,7 +498,9 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   info->approximate = op->prec == TP_FP32 && op->opts.kernel == TP_KERNEL_TENSOR &&
                       !(op->opts.tc_type == TP_FP16 && op->opts.ec == 1);
   info->tile_cells = op->opts.kernel == TP_KERNEL_PATCH ? 8
-                     : info->tensor_path == 0 ? cc_tile_cells(op->n, op->tile_variant)
+                     : info->tensor_path == 0 ? (op->opts.kernel == TP_KERNEL_CUDA_CORE && cc_cell_per_thread(op)
+                                                     ? 128
+                                                     : cc_tile_cells(op->n, op->tile_variant))
                      : info->tensor_path == 3 ? dmma_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 2 ? 128 : 0;
   return TP_OK;

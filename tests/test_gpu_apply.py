@@ -83,6 +83,27 @@ def test_low_precision_against_fp64_oracle(prec, k, kernel):
     assert rel_l2(y, BlockOperator(m, k).apply(x)) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("dims", [(17, 9, 13), (1, 1, 1), (2, 1, 7), (130, 2, 1)])
+def test_cell_per_thread_kernel_k1(prec, dims):
+    """At k = 1 the CUDA-core apply with FP32 arithmetic runs one thread per cell (128 cells per
+    block): meshes over several blocks with a ragged last block, and one-cell and one-cell-thick
+    meshes where most faces are boundary faces, against the oracle."""
+    from paper_2407_09621_gb300 import DGLaplace
+    m = Mesh(*dims)
+    x64 = uniform_vector(m.ncells * 8, seed=91)
+    op = DGLaplace(*dims, 1, prec, kernel=1)
+    try:
+        assert op.info["tile_cells"] == 128
+        x = to_device(x64, prec)
+        y = torch.empty_like(x)
+        op.apply(y, x)
+        torch.cuda.synchronize()
+        assert rel_l2(y.double().cpu().numpy(), BlockOperator(m, 1).apply(x64)) < TOL[prec]
+    finally:
+        op.close()
+
+
 @pytest.mark.parametrize("k,prec,family,path", [(3, "fp16", 2, 2), (3, "bf16", 2, 2), (3, "fp64", 1, 0),
                                                 (3, "fp32", 1, 0), (2, "fp16", 1, 0), (7, "bf16", 1, 0),
                                                 (7, "fp64", 1, 0), (12, "fp32", 1, 0)])
@@ -289,6 +310,7 @@ def test_autotuned_apply_identical_to_default(k, prec, kernel):
 
 @pytest.mark.parametrize("k,prec,kernel,dims,pinned", [
     (3, "fp64", 0, (6, 5, 8), True), (3, "fp64", 0, (7, 3, 11), False), (2, "fp32", 0, (5, 6, 19), True),
+    (1, "fp32", 0, (9, 5, 17), True), (1, "bf16", 0, (4, 7, 10), False),
     (7, "fp64", TENSOR, (3, 4, 9), True), (3, "fp16", TENSOR, (9, 4, 10), True), (3, "bf16", 0, (4, 4, 8), True)])
 def test_pipelined_host_apply_matches_device(k, prec, kernel, dims, pinned):
     """tp_apply_host cuts meshes with at least eight z-layers into z-slab chunks whose copies and
