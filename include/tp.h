@@ -79,6 +79,15 @@ typedef struct {
                    proxy of the mesh (same nx, ny, about 128 MB per vector) and keep the fastest.
                    Results do not depend on the tile shape. 0 (default): the default shape, halved
                    for meshes with fewer cells than two default blocks per SM */
+  int dword;    /* FP64 vectors on the CUDA-core kernel (k <= 7): 1 = double-word FP32 arithmetic:
+                   every FP64 value is split on load into an unevaluated sum of two FP32 numbers
+                   (about 48 significand bits) and the contractions and face terms run as
+                   error-free FP32 transformations on the FMA pipe, the result joined back to FP64
+                   on store. On GB300, whose FP64 pipe delivers ~1.25 TFLOP/s against ~75 for FP32,
+                   this is ~3x the FP64 kernel's rate; the relative error per apply is ~1e-14
+                   (FP64 arithmetic: ~1e-15), inside the 1e-12 FP64 tolerance. Inputs of magnitude
+                   below 2^-126 are taken as 0. 0 (default): FP64 arithmetic on the DFMA pipe.
+                   No tile autotuning with 1 (one tile shape) */
 } tp_op_opts;
 
 /* Tensor kernel (TP_KERNEL_TENSOR). With FP64 vectors (k = 3 and k = 7 only) the six 1D
@@ -122,6 +131,7 @@ typedef struct {
                              vertex patch) or per tile (tcgen05) of the apply launch; 0 for mma.sync */
   int approximate;        /* 1: FP32 vectors on a tensor path that does not reach FP32 accuracy
                              (see the tensor kernel note above); 0 otherwise */
+  int dword;              /* 1: FP64 vectors in double-word FP32 arithmetic (tp_op_opts.dword) */
 } tp_op_info_t;
 
 /* Uniform Cartesian mesh of [0,lx]x[0,ly]x[0,lz] with nx*ny*nz cells
@@ -320,7 +330,9 @@ typedef struct {
 } tp_solve_info;
 
 /* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's
- * mesh (NULL: no preconditioner). Allocates (restart+1)+restart+1 FP64
+ * mesh (NULL: no preconditioner). With a double-word operator (tp_op_opts.dword)
+ * the Arnoldi products A z_j use double-word arithmetic, while the initial
+ * residual and the true residual at the end are evaluated in FP64 arithmetic. Allocates (restart+1)+restart+1 FP64
  * vectors of A's size plus two vectors of mg's precision. Errors:
  * TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA. */
 tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart);

@@ -40,14 +40,15 @@ lib = ctypes.CDLL(LIB_PATH)
 
 class tp_op_opts(ctypes.Structure):
     _fields_ = [("penalty", ctypes.c_int), ("kernel", ctypes.c_int), ("ec", ctypes.c_int),
-                ("tc_type", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("tc_type", ctypes.c_int), ("autotune", ctypes.c_int), ("dword", ctypes.c_int)]
 
 
 class tp_op_info_t(ctypes.Structure):
     _fields_ = [("ncells", ctypes.c_longlong), ("ndofs", ctypes.c_longlong), ("k", ctypes.c_int),
                 ("n", ctypes.c_int), ("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("elem_bytes", ctypes.c_size_t), ("flops_per_dof", ctypes.c_double),
-                ("tensor_path", ctypes.c_int), ("tile_cells", ctypes.c_int), ("approximate", ctypes.c_int)]
+                ("tensor_path", ctypes.c_int), ("tile_cells", ctypes.c_int), ("approximate", ctypes.c_int),
+                ("dword", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p
@@ -98,9 +99,9 @@ def tp_mesh_destroy(mesh):
 
 
 def tp_dg_laplace_create(mesh, k, precision, penalty=TP_PENALTY_CONFIG, kernel=TP_KERNEL_AUTO, ec=0,
-                         tc_type=TP_FP16, autotune=0):
+                         tc_type=TP_FP16, autotune=0, dword=0):
     h = _vp()
-    opts = tp_op_opts(penalty, kernel, ec, tc_type, autotune)
+    opts = tp_op_opts(penalty, kernel, ec, tc_type, autotune, dword)
     _check(lib.tp_dg_laplace_create(ctypes.byref(h), mesh, k, precision, ctypes.byref(opts)))
     return h
 

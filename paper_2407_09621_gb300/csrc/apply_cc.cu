@@ -13,6 +13,10 @@ cudaError_t launch_apply_cpt_range(const tp_op_s* op, void* y, const void* x, lo
 // per block) instead of the line-per-thread one.
 bool cc_cell_per_thread(const tp_op_s* op) { return op->n == 2 && op->prec != TP_FP64; }
 
+// FP64 vectors in double-word FP32 arithmetic (apply_dd.cu)
+cudaError_t launch_apply_dd_range(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
+                                  cudaStream_t s, const void* b);
+
 // n > 8, FP64 and FP32 vectors (apply_cc_high.cu)
 cudaError_t prepare_apply_cc_high(const tp_op_s* op);
 cudaError_t launch_apply_cc_high(const tp_op_s* op, void* y, const void* x, long long c0, long long c1,
@@ -74,7 +78,9 @@ cudaError_t launch_apply_cc_range(const tp_op_s* op, void* y, const void* x, lon
   if (op->n > kMaxN) return launch_apply_cc_high(op, y, x, c0, c1, s, b);
   if (cc_cell_per_thread(op)) return launch_apply_cpt_range(op, y, x, c0, c1, s, b);
   switch (op->prec) {
-    case TP_FP64: return launch_cc_t<double, double>(op, y, x, c0, c1, s, b);
+    case TP_FP64:
+      return op->opts.dword ? launch_apply_dd_range(op, y, x, c0, c1, s, b)
+                            : launch_cc_t<double, double>(op, y, x, c0, c1, s, b);
     case TP_FP32: return launch_cc_t<float, float>(op, y, x, c0, c1, s, b);
     case TP_FP16: return launch_cc_t<__half, float>(op, y, x, c0, c1, s, b);
     case TP_BF16: return launch_cc_t<__nv_bfloat16, float>(op, y, x, c0, c1, s, b);

@@ -179,10 +179,18 @@ cudaError_t norm_to_host(Ctx& c, const double* w, double* out) {
   return e;
 }
 
-// out = b - A x (one pass where the operator's kernel stores the residual form itself)
+// out = b - A x (one pass where the operator's kernel stores the residual form itself), in FP64
+// arithmetic: a double-word operator (tp_op_opts.dword) serves the Arnoldi products only
 cudaError_t residual64(Ctx& c, double* out, const double* b, const double* x) {
-  if (c.s->A->opts.kernel == TP_KERNEL_CUDA_CORE) return launch_residual(c.s->A, out, b, x, c.st);
-  cudaError_t e = launch_apply(c.s->A, c.s->w, x, c.st);
+  const tp_op_s* A = c.s->A;
+  tp_op_s native;
+  if (A->opts.dword) {
+    native = *A;  // shares the constants and owns nothing
+    native.opts.dword = 0;
+    A = &native;
+  }
+  if (A->opts.kernel == TP_KERNEL_CUDA_CORE) return launch_residual(A, out, b, x, c.st);
+  cudaError_t e = launch_apply(A, c.s->w, x, c.st);
   const double coef[2] = {1.0, -1.0};
   const double* v[2] = {b, c.s->w};
   if (e == cudaSuccess) e = multi_axpy<double>(c.s->n, out, 0.0, v, coef, 2, c.st);

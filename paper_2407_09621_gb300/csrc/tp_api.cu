@@ -75,6 +75,7 @@ static tp_status autotune_apply(tp_op_s* op) {
   if (op->opts.kernel == TP_KERNEL_PATCH) return TP_OK;           // one patch per thread block
   if (op->n > kMaxN) return TP_OK;                                 // n > 8: one tile shape
   if (op->opts.kernel == TP_KERNEL_CUDA_CORE && cc_cell_per_thread(op)) return TP_OK;  // one shape
+  if (op->opts.dword) return TP_OK;                                // double-word: one tile shape
   const long long eb = (long long)elem_bytes(op->prec);
   const long long n3 = (long long)op->n * op->n * op->n;
   const long long slab = (long long)op->mesh.nx * op->mesh.ny;
@@ -370,7 +371,7 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
     set_error("tp_dg_laplace_create: unknown precision %d", (int)p);
     return TP_ERR_INVALID_ARG;
   }
-  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16, 0};
+  tp_op_opts o{TP_PENALTY_CONFIG, TP_KERNEL_AUTO, 0, TP_FP16, 0, 0};
   if (opts) o = *opts;
   if (o.penalty != TP_PENALTY_CONFIG && o.penalty != TP_PENALTY_PAPER) {
     set_error("tp_dg_laplace_create: unknown penalty mode %d", o.penalty);
@@ -387,6 +388,15 @@ tp_status tp_dg_laplace_create(tp_op* out, tp_mesh m, int k, tp_precision p, con
   if (o.ec < 0 || o.ec > 3) {
     set_error("tp_dg_laplace_create: ec must be 0 (off), 1 (both operands), 2 (matrix) or 3 (vector)");
     return TP_ERR_INVALID_ARG;
+  }
+  if (o.dword != 0 && o.dword != 1) {
+    set_error("tp_dg_laplace_create: dword must be 0 (FP64 arithmetic) or 1 (double-word FP32 arithmetic)");
+    return TP_ERR_INVALID_ARG;
+  }
+  if (o.dword && (p != TP_FP64 || (o.kernel != TP_KERNEL_AUTO && o.kernel != TP_KERNEL_CUDA_CORE) || k + 1 > kMaxN)) {
+    set_error("tp_dg_laplace_create: double-word arithmetic is for FP64 vectors on the CUDA-core kernel, k <= %d",
+              kMaxN - 1);
+    return TP_ERR_UNSUPPORTED;
   }
   const long long ncells = (long long)m->nx * m->ny * m->nz;
   if (o.kernel == TP_KERNEL_AUTO) {
@@ -497,10 +507,11 @@ tp_status tp_op_get_info(tp_op op, tp_op_info_t* info) {
   // operands and both operands refined (Algorithm 1, ec = 1)
   info->approximate = op->prec == TP_FP32 && op->opts.kernel == TP_KERNEL_TENSOR &&
                       !(op->opts.tc_type == TP_FP16 && op->opts.ec == 1);
+  info->dword = op->opts.dword;
   info->tile_cells = op->opts.kernel == TP_KERNEL_PATCH ? 8
                      : info->tensor_path == 0 ? (op->opts.kernel == TP_KERNEL_CUDA_CORE && cc_cell_per_thread(op)
                                                      ? 128
-                                                     : cc_tile_cells(op->n, op->tile_variant))
+                                                     : cc_tile_cells(op->n, op->opts.dword ? 1 : op->tile_variant))
                      : info->tensor_path == 3 ? dmma_tile_cells(op->n, op->tile_variant)
                      : info->tensor_path == 2 ? 128 : 0;
   return TP_OK;

@@ -19,12 +19,14 @@ class DGLaplace:
     """SIPG Laplace operator of degree k on an nx*ny*nz box mesh (owns its handles)."""
 
     def __init__(self, nx, ny, nz, k, precision="fp64", penalty=_lib.TP_PENALTY_CONFIG,
-                 kernel=_lib.TP_KERNEL_AUTO, ec=0, lengths=(1.0, 1.0, 1.0), tc_type=_lib.TP_FP16, autotune=0):
+                 kernel=_lib.TP_KERNEL_AUTO, ec=0, lengths=(1.0, 1.0, 1.0), tc_type=_lib.TP_FP16, autotune=0,
+                 dword=0):
         self.op = self.mesh = None
         self.prec, self.dtype = PRECISIONS[precision]
         self.mesh = _lib.tp_mesh_create(nx, ny, nz, *lengths)
         try:
-            self.op = _lib.tp_dg_laplace_create(self.mesh, k, self.prec, penalty, kernel, ec, tc_type, autotune)
+            self.op = _lib.tp_dg_laplace_create(self.mesh, k, self.prec, penalty, kernel, ec, tc_type, autotune,
+                                                dword)
         except Exception:
             mesh, self.mesh = self.mesh, None
             _lib.tp_mesh_destroy(mesh)

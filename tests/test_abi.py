@@ -88,6 +88,16 @@ def test_operator_argument_validation():
         with pytest.raises(_lib.TPError) as e:
             _lib.tp_dg_laplace_create(m, 3, _lib.TP_FP64, penalty=5)
         assert e.value.status == _lib.TP_ERR_INVALID_ARG
+        # double-word arithmetic: FP64 vectors on the CUDA-core kernel, k <= 7 (checked before any CUDA call)
+        for k, p, kern in ((3, _lib.TP_FP32, 0), (3, _lib.TP_FP16, 1), (3, _lib.TP_FP64, 2), (3, _lib.TP_FP64, 3),
+                           (8, _lib.TP_FP64, 1)):
+            with pytest.raises(_lib.TPError) as e:
+                _lib.tp_dg_laplace_create(m, k, p, kernel=kern, dword=1)
+            assert e.value.status == _lib.TP_ERR_UNSUPPORTED
+            assert "double-word" in _lib.tp_last_error()
+        with pytest.raises(_lib.TPError) as e:
+            _lib.tp_dg_laplace_create(m, 3, _lib.TP_FP64, dword=2)
+        assert e.value.status == _lib.TP_ERR_INVALID_ARG
     finally:
         _lib.tp_mesh_destroy(m)
     assert _lib.lib.tp_apply(None, None, None, None) == _lib.TP_ERR_INVALID_ARG

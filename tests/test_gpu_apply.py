@@ -104,6 +104,53 @@ def test_cell_per_thread_kernel_k1(prec, dims):
         op.close()
 
 
+@pytest.mark.parametrize("k", range(1, 8))
+@pytest.mark.parametrize("dims", [(13, 9, 11), (1, 1, 1), (3, 1, 7)])
+def test_double_word_fp64_apply_matches_oracle(k, dims):
+    """FP64 vectors in double-word FP32 arithmetic (tp_op_opts.dword): within the FP64 tolerance
+    of the oracle on meshes over several blocks and on one-cell and one-cell-thick meshes, and
+    within 1e-13 of the FP64 kernel."""
+    from paper_2407_09621_gb300 import DGLaplace
+    m = Mesh(*dims)
+    x64 = uniform_vector(m.ncells * (k + 1) ** 3, seed=95 + k)
+    x = torch.from_numpy(x64).cuda()
+    ys = []
+    for dword in (0, 1):
+        op = DGLaplace(*dims, k, "fp64", kernel=1, dword=dword)
+        try:
+            assert op.info["dword"] == dword and op.info["kernel"] == 1
+            y = torch.empty_like(x)
+            op.apply(y, x)
+            torch.cuda.synchronize()
+            ys.append(y.cpu().numpy())
+        finally:
+            op.close()
+    assert rel_l2(ys[1], BlockOperator(m, k).apply(x64)) < TOL["fp64"]
+    assert rel_l2(ys[1], ys[0]) < 1e-13
+
+
+def test_double_word_host_apply_matches_device():
+    """tp_apply_host on a double-word operator runs the same kernel over z-slab chunks: equal to
+    tp_apply bit for bit."""
+    from paper_2407_09621_gb300 import DGLaplace
+    dims, k = (6, 5, 17), 3
+    m = Mesh(*dims)
+    x64 = uniform_vector(m.ncells * 64, seed=97)
+    op = DGLaplace(*dims, k, "fp64", dword=1)
+    try:
+        xd = torch.from_numpy(x64).cuda()
+        yd = torch.empty_like(xd)
+        op.apply(yd, xd)
+        xh = xd.cpu().pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        op.apply_host(yh, xh)
+        torch.cuda.synchronize()
+        assert torch.equal(yh, yd.cpu())
+        assert rel_l2(yh.numpy(), BlockOperator(m, k).apply(x64)) < TOL["fp64"]
+    finally:
+        op.close()
+
+
 @pytest.mark.parametrize("k,prec,family,path", [(3, "fp16", 2, 2), (3, "bf16", 2, 2), (3, "fp64", 1, 0),
                                                 (3, "fp32", 1, 0), (2, "fp16", 1, 0), (7, "bf16", 1, 0),
                                                 (7, "fp64", 1, 0), (12, "fp32", 1, 0)])

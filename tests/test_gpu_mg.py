@@ -137,10 +137,10 @@ def test_lmax_estimate_bounds_the_spectrum(k):
         g.close()
 
 
-def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4, kernel=1, smoother=0):
+def _solve(nc, k, mg_prec, rtol=1e-10, maxit=200, lmax=0.0, coarse_cells=4, kernel=1, smoother=0, dword=0):
     from paper_2407_09621_gb300 import _lib
     mesh = _lib.tp_mesh_create(nc, nc, nc)
-    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64)
+    op = _lib.tp_dg_laplace_create(mesh, k, _lib.TP_FP64, dword=dword)
     mg = (_lib.tp_mg_create(op, lmax=lmax, coarse_cells=coarse_cells, precision=PREC[mg_prec], kernel=kernel,
                             smoother=smoother)
           if mg_prec else None)
@@ -173,6 +173,20 @@ def test_fgmres_solution_matches_exact_discrete_solution(mg_prec, k, nc):
     A = BlockOperator(Mesh(nc, nc, nc), k)
     _, its, _ = fgmres(A.apply, mg, rhs_sine(k, nc, nc, nc), rtol=1e-10)
     assert abs(info["iterations"] - its) <= 2
+
+
+@pytest.mark.parametrize("k,nc,smoother", [(3, 16, 0), (2, 16, 1), (7, 8, 1)])
+def test_fgmres_double_word_arnoldi_products(k, nc, smoother):
+    """With a double-word operator (tp_op_opts.dword) the Arnoldi products run in double-word FP32
+    arithmetic and the residuals in FP64: the solve takes the FP64 operator's iteration count
+    (within one), its true residual meets the tolerance and it reaches the exact discrete solution."""
+    lmax = 2.9 if k > 1 else 4.9
+    x_n, info_n = _solve(nc, k, "fp32", lmax=lmax, coarse_cells=2, smoother=smoother)
+    x_d, info_d = _solve(nc, k, "fp32", lmax=lmax, coarse_cells=2, smoother=smoother, dword=1)
+    assert info_d["converged"] == 1 and info_d["true_rel_residual"] < 2e-10
+    assert abs(info_d["iterations"] - info_n["iterations"]) <= 1
+    u = FastDiag(k, nc, nc, nc).solve(rhs_sine(k, nc, nc, nc))
+    assert rel_l2(x_d, u) < 1e-8 and rel_l2(x_d, x_n) < 1e-8
 
 
 @pytest.mark.parametrize("kernel", [1, 2])
