@@ -608,13 +608,16 @@ def solve_bench(k, nc, rtol=1e-10, half=True):
     out["speedup_mixed_vs_fp64_vertex_patch"] = (out["fp64_vertex_patch"]["seconds"] /
                                                  out["mixed_fp32_vertex_patch"]["seconds"])
     fastest_fp64 = min(out["fp64_vcycle"]["seconds"], out["fp64_vertex_patch"]["seconds"])
-    # best mixed solve with FP64 Arnoldi products; the double-word variant is reported beside it
+    # best mixed solve with FP64 Arnoldi products. The double-word variant is reported beside it with
+    # its own L2-rule flag: its products carry ~2^-48 relative to the summed terms, so its Arnoldi
+    # estimate and the FP64 true residual part near 1e-10 and it need not meet the rule
     mixed = [n for n, p, _, _ in runs if p != _lib.TP_FP64 and out[n]["l2_within_rule"] and not n.endswith("_dword")]
     best = min(mixed or ["mixed_fp32_vcycle"], key=lambda n: out[n]["seconds"])
     out["best_mixed"] = {"run": best, "seconds": out[best]["seconds"],
                          "speedup_vs_fastest_fp64": fastest_fp64 / out[best]["seconds"]}
     dw = out["mixed_fp32_vertex_patch_dword"]
     out["mixed_dword"] = {"seconds": dw["seconds"], "l2_within_rule": dw["l2_within_rule"],
+                          "true_rel_residual": dw["true_rel_residual"],
                           "speedup_vs_fastest_fp64": fastest_fp64 / dw["seconds"]}
     _lib.tp_op_destroy(op_dw)
     _lib.tp_op_destroy(op)
@@ -667,9 +670,7 @@ def solve_summary(solves):
             "mixed_iters": s[best["run"]]["iterations"], "fp64_s": round(fp64, 4),
             "speedup": round(best["speedup_vs_fastest_fp64"], 2),
             "l2_mixed": s[best["run"]]["l2_error"], "l2_fp64": s["fp64_vcycle"]["l2_error"],
-            "l2_within_rule": bool(s[best["run"]]["l2_within_rule"]),
-            "dword_arnoldi_s": round(s["mixed_dword"]["seconds"], 4),
-            "dword_arnoldi_speedup": round(s["mixed_dword"]["speedup_vs_fastest_fp64"], 2)}
+            "l2_within_rule": bool(s[best["run"]]["l2_within_rule"])}
     return out
 
 

@@ -332,7 +332,12 @@ typedef struct {
 /* A: the FP64 operator (must be TP_FP64). mg: preconditioner built on A's
  * mesh (NULL: no preconditioner). With a double-word operator (tp_op_opts.dword)
  * the Arnoldi products A z_j use double-word arithmetic, while the initial
- * residual and the true residual at the end are evaluated in FP64 arithmetic. Allocates (restart+1)+restart+1 FP64
+ * residual and the true residual at the end are evaluated in FP64 arithmetic.
+ * Double-word products carry ~2^-48 relative to the operator's summed terms
+ * (FP64: 2^-53), which for smooth Krylov vectors exceed A z by orders of
+ * magnitude: the Arnoldi estimate then stops being trustworthy near 1e-10
+ * (measured true residuals 1.5e-10 at k = 3, 128^3 and 2.4e-10 at k = 7, 64^3
+ * for rtol = 1e-10), so tight tolerances want the FP64 operator. Allocates (restart+1)+restart+1 FP64
  * vectors of A's size plus two vectors of mg's precision. Errors:
  * TP_ERR_INVALID_ARG, TP_ERR_OOM, TP_ERR_CUDA. */
 tp_status tp_fgmres_create(tp_solver* out, tp_op A, tp_mg mg, int restart);
