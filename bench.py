@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--tensor", action="store_true", help="kernel-only: use the tensor-core kernel")
     p.add_argument("--patch", action="store_true", help="kernel-only: use the patch-wise kernel (vertex patches)")
     p.add_argument("--ec", action="store_true", help="kernel-only: tensor kernel with error correction")
+    p.add_argument("--dword", action="store_true",
+                   help="kernel-only: FP64 vectors in double-word FP32 arithmetic (tp_op_opts.dword)")
     p.add_argument("--no-tune", action="store_true", help="keep the default apply tile shape (no autotuner)")
     p.add_argument("--vcycle-only", action="store_true",
                    help="print only the time of one V-cycle (--k, --cells, --prec, --smoother) and exit")
@@ -701,7 +703,8 @@ def run_ours(args):
               flush=True)
         return
     op = DGLaplace(nc, nc, nc, kdeg, args.prec, kernel=3 if args.patch else (2 if args.tensor else 0),
-                   ec=1 if args.ec else 0, autotune=0 if args.no_tune else 1)
+                   ec=1 if args.ec else 0, autotune=0 if (args.no_tune or args.dword) else 1,
+                   dword=1 if args.dword else 0)
     ndofs = op.ndofs
     if args.kernel_only:
         x = torch.from_numpy(uniform_vector(ndofs, seed=rank)).to("cuda", op.dtype)
@@ -709,7 +712,8 @@ def run_ours(args):
         per, total_ms = time_applies(op, y, x, args.steps, args.warmup, torch.cuda.current_stream())
         op.check()
         print(json.dumps({"kernel_only": True, "k": kdeg, "cells": nc, "prec": args.prec, "dofs": ndofs,
-                          "tensor_path": op.info["tensor_path"], "ec": int(args.ec), "tile_cells": op.info["tile_cells"],
+                          "tensor_path": op.info["tensor_path"], "ec": int(args.ec), "dword": op.info["dword"],
+                          "tile_cells": op.info["tile_cells"],
                           "ms_per_apply": statistics.mean(per), "gdofs": ndofs / statistics.mean(per) / 1e6}))
         op.close()
         return
