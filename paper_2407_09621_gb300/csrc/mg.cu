@@ -32,8 +32,9 @@ size_t elem_bytes(tp_precision p);
 // vertex-patch smoother (schwarz.cu)
 bool vp_colour_nonempty(const int nc[3], int c);
 cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, void* x, const void* r, const void* S,
-                      const void* L, cudaStream_t s);
-tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out);
+                      const void* L, const void* C, cudaStream_t s);
+tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out,
+                    std::vector<unsigned char>* C_out);
 
 // Division of n < 2^31 by an invariant d >= 1 with one multiply-high (Granlund and Montgomery,
 // "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d) and
@@ -356,6 +357,7 @@ struct tp_mg_level {
   void *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
   double lmax = 0.0;
   void *vpS = nullptr, *vpL = nullptr;  // vertex-patch smoother: 1D patch eigenbases and eigenvalues
+  std::vector<unsigned char> vpC;       // and the interior ones as the patch kernel's parameter
   tp::JacobiParams<double> j64;
   tp::JacobiParams<float> j32;
 };
@@ -549,7 +551,7 @@ static cudaError_t smooth_vertex_patch(const tp_mg_s* mg, int l, void* x, const 
       r = L.r;
     }
     zero = false;
-    if (e == cudaSuccess) e = vp_colour(mg->prec, mg->n, L.nc, c, x, r, L.vpS, L.vpL, s);
+    if (e == cudaSuccess) e = vp_colour(mg->prec, mg->n, L.nc, c, x, r, L.vpS, L.vpL, L.vpC.data(), s);
   }
   return e;
 }
@@ -827,7 +829,7 @@ tp_status tp_mg_create(tp_mg* out, tp_op finest, const tp_mg_opts* opts) {
   // vertex-patch eigenbases of every smoothed level (each has >= 2 cells per direction: it is at
   // least twice the coarsest level)
   for (int l = 1; l < nl && st == TP_OK && o.smoother == TP_SMOOTHER_VERTEX_PATCH; ++l)
-    st = vp_tables(mg->lv[l].op, mg->lv[l].nc, mg->prec, &mg->lv[l].vpS, &mg->lv[l].vpL);
+    st = vp_tables(mg->lv[l].op, mg->lv[l].nc, mg->prec, &mg->lv[l].vpS, &mg->lv[l].vpL, &mg->lv[l].vpC);
   // smoother eigenvalue bounds
   for (int l = 1; l < nl && st == TP_OK && o.smoother == TP_SMOOTHER_CHEBYSHEV; ++l) {
     if (o.lmax > 0) {

@@ -70,6 +70,28 @@ __device__ __forceinline__ void dot_row2(const T* __restrict__ row, const T (&a)
   }
 }
 
+// The bases and eigenvalues of interior patches (boundary type 0 in every direction: on fine levels
+// nearly every patch), passed as a kernel parameter: their entries become constant-bank operands of
+// the FMAs, so an interior patch loads no table into shared memory and reads no basis row from it.
+// S[d][X * P + a] = component X of eigenvector a of direction d, lam[d][a] its eigenvalue.
+template <typename T, int P>
+struct VPInterior {
+  T S[3][P * P];
+  T lam[3][P];
+};
+
+// sum_m c[m * STRIDE] in[m] for two lines, c a row or column of a basis in the kernel parameter
+template <typename T, int P, int STRIDE>
+__device__ __forceinline__ void dotc2(const T* c, const T (&a)[P], const T (&b)[P], T& sa, T& sb) {
+  sa = T(0);
+  sb = T(0);
+#pragma unroll
+  for (int m = 0; m < P; ++m) {
+    sa = fma(c[m * STRIDE], a[m], sa);
+    sb = fma(c[m * STRIDE], b[m], sb);
+  }
+}
+
 // dynamic shared memory of the patch kernel: two padded patch tensors, six P x P bases (S^T and S
 // per direction), 3P eigenvalues
 template <typename T, int N>
@@ -84,7 +106,7 @@ constexpr size_t vp_smem_bytes() {
 template <typename TS, typename T, int N>
 __global__ void __launch_bounds__(2 * N * N)
 vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
-                VPDims D) {
+                VPDims D, const __grid_constant__ VPInterior<T, 2 * N> C) {
   constexpr int P = 2 * N, R = P + 1, N3 = N * N * N, H = P / 2, NT = P * H;
   extern __shared__ __align__(16) unsigned char vp_smem[];
   T* bufA = reinterpret_cast<T*>(vp_smem);
@@ -95,9 +117,10 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
   const int tid = threadIdx.x, p0 = tid / P, p1 = p0 + H, q = tid % P;
   const int vx = D.first[0] + 2 * (int)blockIdx.x, vy = D.first[1] + 2 * (int)blockIdx.y;
   const int vz = D.first[2] + 2 * (int)blockIdx.z;
-  {
-    const int t[3] = {(vx == 1 ? 1 : 0) + (vx == D.nx - 1 ? 2 : 0), (vy == 1 ? 1 : 0) + (vy == D.ny - 1 ? 2 : 0),
-                      (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
+  const int t[3] = {(vx == 1 ? 1 : 0) + (vx == D.nx - 1 ? 2 : 0), (vy == 1 ? 1 : 0) + (vy == D.ny - 1 ? 2 : 0),
+                    (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
+  const bool interior = (t[0] | t[1] | t[2]) == 0;  // block-uniform
+  if (!interior) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
 #pragma unroll
@@ -131,90 +154,166 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
     for (int j = 0; j < 2 * P; ++j) bufA[saddr(tid + j * NT)] = v[j];
   }
   __syncthreads();
-  // Two lines of the patch tensor in registers, contracted per output node o with a basis row:
-  // sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of sB);
-  // each output goes straight to shared memory.
-  T i0[P], i1[P], s0, s1;
-  // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
+  if (interior) {
+    // the same six phases with the bases and eigenvalues from the kernel parameter
+    T i0[P], i1[P], s0, s1;
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    i0[m] = bufA[(p0 * P + q) * R + m];
-    i1[m] = bufA[(p1 * P + q) * R + m];
-  }
-#pragma unroll 2
-  for (int a = 0; a < P; ++a) {
-    dot_row2<T, P>(sF[0] + a * P, i0, i1, s0, s1);
-    bufB[(p0 * P + q) * R + a] = s0;
-    bufB[(p1 * P + q) * R + a] = s1;
-  }
-  __syncthreads();
-  // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
-#pragma unroll
-  for (int m = 0; m < P; ++m) {
-    i0[m] = bufB[(p0 * P + m) * R + q];
-    i1[m] = bufB[(p1 * P + m) * R + q];
-  }
-#pragma unroll 2
-  for (int b = 0; b < P; ++b) {
-    dot_row2<T, P>(sF[1] + b * P, i0, i1, s0, s1);
-    bufA[(p0 * P + b) * R + q] = s0;
-    bufA[(p1 * P + b) * R + q] = s1;
-  }
-  __syncthreads();
-  // z-lines (b = p, a = q): S_z^T and the eigenvalue scaling into bufB, then S_z back into bufA.
-  // A thread reads and writes only its own z-lines here, so no barrier is needed in between.
-#pragma unroll
-  for (int m = 0; m < P; ++m) {
-    i0[m] = bufA[(m * P + p0) * R + q];
-    i1[m] = bufA[(m * P + p1) * R + q];
-  }
-  {
-    const T l0 = sL[0][q] + sL[1][p0], l1 = sL[0][q] + sL[1][p1];
-#pragma unroll 2
-    for (int c = 0; c < P; ++c) {
-      dot_row2<T, P>(sF[2] + c * P, i0, i1, s0, s1);
-      bufB[(c * P + p0) * R + q] = s0 / (l0 + sL[2][c]);
-      bufB[(c * P + p1) * R + q] = s1 / (l1 + sL[2][c]);
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufA[(p0 * P + q) * R + m];
+      i1[m] = bufA[(p1 * P + q) * R + m];
     }
-  }
 #pragma unroll
-  for (int c = 0; c < P; ++c) {
-    i0[c] = bufB[(c * P + p0) * R + q];
-    i1[c] = bufB[(c * P + p1) * R + q];
-  }
-#pragma unroll 2
-  for (int Z = 0; Z < P; ++Z) {
-    dot_row2<T, P>(sB[2] + Z * P, i0, i1, s0, s1);
-    bufA[(Z * P + p0) * R + q] = s0;
-    bufA[(Z * P + p1) * R + q] = s1;
-  }
-  __syncthreads();
-  // S_y along y-lines (Z = p, a = q): bufA -> bufB
+    for (int a = 0; a < P; ++a) {
+      dotc2<T, P, P>(C.S[0] + a, i0, i1, s0, s1);  // (S_x^T)[a][m] = S_x[m][a]
+      bufB[(p0 * P + q) * R + a] = s0;
+      bufB[(p1 * P + q) * R + a] = s1;
+    }
+    __syncthreads();
 #pragma unroll
-  for (int b = 0; b < P; ++b) {
-    i0[b] = bufA[(p0 * P + b) * R + q];
-    i1[b] = bufA[(p1 * P + b) * R + q];
-  }
-#pragma unroll 2
-  for (int Y = 0; Y < P; ++Y) {
-    dot_row2<T, P>(sB[1] + Y * P, i0, i1, s0, s1);
-    bufB[(p0 * P + Y) * R + q] = s0;
-    bufB[(p1 * P + Y) * R + q] = s1;
-  }
-  __syncthreads();
-  // S_x along x-lines (Z = p, Y = q): bufB -> bufA
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufB[(p0 * P + m) * R + q];
+      i1[m] = bufB[(p1 * P + m) * R + q];
+    }
 #pragma unroll
-  for (int a = 0; a < P; ++a) {
-    i0[a] = bufB[(p0 * P + q) * R + a];
-    i1[a] = bufB[(p1 * P + q) * R + a];
+    for (int b = 0; b < P; ++b) {
+      dotc2<T, P, P>(C.S[1] + b, i0, i1, s0, s1);
+      bufA[(p0 * P + b) * R + q] = s0;
+      bufA[(p1 * P + b) * R + q] = s1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufA[(m * P + p0) * R + q];
+      i1[m] = bufA[(m * P + p1) * R + q];
+    }
+    {
+      // S_z^T and the scaling; the z-lines stay in registers for S_z (a thread owns them)
+      const T l0 = C.lam[0][q] + C.lam[1][p0], l1 = C.lam[0][q] + C.lam[1][p1];
+      T t0[P], t1[P];
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        dotc2<T, P, P>(C.S[2] + c, i0, i1, s0, s1);
+        t0[c] = s0 / (l0 + C.lam[2][c]);
+        t1[c] = s1 / (l1 + C.lam[2][c]);
+      }
+#pragma unroll
+      for (int Z = 0; Z < P; ++Z) {
+        dotc2<T, P, 1>(C.S[2] + Z * P, t0, t1, s0, s1);
+        bufA[(Z * P + p0) * R + q] = s0;
+        bufA[(Z * P + p1) * R + q] = s1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      i0[b] = bufA[(p0 * P + b) * R + q];
+      i1[b] = bufA[(p1 * P + b) * R + q];
+    }
+#pragma unroll
+    for (int Y = 0; Y < P; ++Y) {
+      dotc2<T, P, 1>(C.S[1] + Y * P, i0, i1, s0, s1);
+      bufB[(p0 * P + Y) * R + q] = s0;
+      bufB[(p1 * P + Y) * R + q] = s1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      i0[a] = bufB[(p0 * P + q) * R + a];
+      i1[a] = bufB[(p1 * P + q) * R + a];
+    }
+#pragma unroll
+    for (int X = 0; X < P; ++X) {
+      dotc2<T, P, 1>(C.S[0] + X * P, i0, i1, s0, s1);
+      bufA[(p0 * P + q) * R + X] = s0;
+      bufA[(p1 * P + q) * R + X] = s1;
+    }
+    __syncthreads();
+  } else {
+    // Two lines of the patch tensor in registers, contracted per output node o with a basis row:
+    // sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of sB);
+    // each output goes straight to shared memory.
+    T i0[P], i1[P], s0, s1;
+    // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
+  #pragma unroll
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufA[(p0 * P + q) * R + m];
+      i1[m] = bufA[(p1 * P + q) * R + m];
+    }
+  #pragma unroll 2
+    for (int a = 0; a < P; ++a) {
+      dot_row2<T, P>(sF[0] + a * P, i0, i1, s0, s1);
+      bufB[(p0 * P + q) * R + a] = s0;
+      bufB[(p1 * P + q) * R + a] = s1;
+    }
+    __syncthreads();
+    // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
+  #pragma unroll
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufB[(p0 * P + m) * R + q];
+      i1[m] = bufB[(p1 * P + m) * R + q];
+    }
+  #pragma unroll 2
+    for (int b = 0; b < P; ++b) {
+      dot_row2<T, P>(sF[1] + b * P, i0, i1, s0, s1);
+      bufA[(p0 * P + b) * R + q] = s0;
+      bufA[(p1 * P + b) * R + q] = s1;
+    }
+    __syncthreads();
+    // z-lines (b = p, a = q): S_z^T and the eigenvalue scaling into bufB, then S_z back into bufA.
+    // A thread reads and writes only its own z-lines here, so no barrier is needed in between.
+  #pragma unroll
+    for (int m = 0; m < P; ++m) {
+      i0[m] = bufA[(m * P + p0) * R + q];
+      i1[m] = bufA[(m * P + p1) * R + q];
+    }
+    {
+      const T l0 = sL[0][q] + sL[1][p0], l1 = sL[0][q] + sL[1][p1];
+  #pragma unroll 2
+      for (int c = 0; c < P; ++c) {
+        dot_row2<T, P>(sF[2] + c * P, i0, i1, s0, s1);
+        bufB[(c * P + p0) * R + q] = s0 / (l0 + sL[2][c]);
+        bufB[(c * P + p1) * R + q] = s1 / (l1 + sL[2][c]);
+      }
+    }
+  #pragma unroll
+    for (int c = 0; c < P; ++c) {
+      i0[c] = bufB[(c * P + p0) * R + q];
+      i1[c] = bufB[(c * P + p1) * R + q];
+    }
+  #pragma unroll 2
+    for (int Z = 0; Z < P; ++Z) {
+      dot_row2<T, P>(sB[2] + Z * P, i0, i1, s0, s1);
+      bufA[(Z * P + p0) * R + q] = s0;
+      bufA[(Z * P + p1) * R + q] = s1;
+    }
+    __syncthreads();
+    // S_y along y-lines (Z = p, a = q): bufA -> bufB
+  #pragma unroll
+    for (int b = 0; b < P; ++b) {
+      i0[b] = bufA[(p0 * P + b) * R + q];
+      i1[b] = bufA[(p1 * P + b) * R + q];
+    }
+  #pragma unroll 2
+    for (int Y = 0; Y < P; ++Y) {
+      dot_row2<T, P>(sB[1] + Y * P, i0, i1, s0, s1);
+      bufB[(p0 * P + Y) * R + q] = s0;
+      bufB[(p1 * P + Y) * R + q] = s1;
+    }
+    __syncthreads();
+    // S_x along x-lines (Z = p, Y = q): bufB -> bufA
+  #pragma unroll
+    for (int a = 0; a < P; ++a) {
+      i0[a] = bufB[(p0 * P + q) * R + a];
+      i1[a] = bufB[(p1 * P + q) * R + a];
+    }
+  #pragma unroll 2
+    for (int X = 0; X < P; ++X) {
+      dot_row2<T, P>(sB[0] + X * P, i0, i1, s0, s1);
+      bufA[(p0 * P + q) * R + X] = s0;
+      bufA[(p1 * P + q) * R + X] = s1;
+    }
+    __syncthreads();
   }
-#pragma unroll 2
-  for (int X = 0; X < P; ++X) {
-    dot_row2<T, P>(sB[0] + X * P, i0, i1, s0, s1);
-    bufA[(p0 * P + q) * R + X] = s0;
-    bufA[(p1 * P + q) * R + X] = s1;
-  }
-  __syncthreads();
   // x_P += the correction, cell by cell like the gather
   {
     T v[2 * P];
@@ -227,14 +326,15 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
 
 template <typename TS, typename T, int N>
 cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
-                          cudaStream_t s) {
+                          const void* Cint, cudaStream_t s) {
   const int par[3] = {colour & 1, (colour >> 1) & 1, (colour >> 2) & 1};
   const dim3 grid(vp_count(par[0], nc[0]), vp_count(par[1], nc[1]), vp_count(par[2], nc[2]));
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
   vp_patch_kernel<TS, T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
-      static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D);
+      static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D,
+      *static_cast<const VPInterior<T, 2 * N>*>(Cint));
   return cudaGetLastError();
 }
 
@@ -260,15 +360,15 @@ cudaError_t prepare_t(int n) {
 
 template <typename TS, typename T>
 cudaError_t launch_colour_t(int n, int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
-                            cudaStream_t s) {
+                            const void* C, cudaStream_t s) {
   switch (n) {
-    case 2: return launch_colour<TS, T, 2>(colour, nc, x, r, S, L, s);
-    case 3: return launch_colour<TS, T, 3>(colour, nc, x, r, S, L, s);
-    case 4: return launch_colour<TS, T, 4>(colour, nc, x, r, S, L, s);
-    case 5: return launch_colour<TS, T, 5>(colour, nc, x, r, S, L, s);
-    case 6: return launch_colour<TS, T, 6>(colour, nc, x, r, S, L, s);
-    case 7: return launch_colour<TS, T, 7>(colour, nc, x, r, S, L, s);
-    case 8: return launch_colour<TS, T, 8>(colour, nc, x, r, S, L, s);
+    case 2: return launch_colour<TS, T, 2>(colour, nc, x, r, S, L, C, s);
+    case 3: return launch_colour<TS, T, 3>(colour, nc, x, r, S, L, C, s);
+    case 4: return launch_colour<TS, T, 4>(colour, nc, x, r, S, L, C, s);
+    case 5: return launch_colour<TS, T, 5>(colour, nc, x, r, S, L, C, s);
+    case 6: return launch_colour<TS, T, 6>(colour, nc, x, r, S, L, C, s);
+    case 7: return launch_colour<TS, T, 7>(colour, nc, x, r, S, L, C, s);
+    case 8: return launch_colour<TS, T, 8>(colour, nc, x, r, S, L, C, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -283,22 +383,55 @@ bool vp_colour_nonempty(const int nc[3], int c) {
 // x_P += A_P^{-1} r_P for every patch of colour c (FP64 or FP32 vectors, or FP16/BF16 storage with
 // FP32 arithmetic; every nc >= 2).
 cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, void* x, const void* r, const void* S,
-                      const void* L, cudaStream_t s) {
+                      const void* L, const void* C, cudaStream_t s) {
   switch (prec) {
-    case TP_FP64: return launch_colour_t<double, double>(n, colour, nc, x, r, S, L, s);
-    case TP_FP32: return launch_colour_t<float, float>(n, colour, nc, x, r, S, L, s);
-    case TP_FP16: return launch_colour_t<__half, float>(n, colour, nc, x, r, S, L, s);
-    case TP_BF16: return launch_colour_t<__nv_bfloat16, float>(n, colour, nc, x, r, S, L, s);
+    case TP_FP64: return launch_colour_t<double, double>(n, colour, nc, x, r, S, L, C, s);
+    case TP_FP32: return launch_colour_t<float, float>(n, colour, nc, x, r, S, L, C, s);
+    case TP_FP16: return launch_colour_t<__half, float>(n, colour, nc, x, r, S, L, C, s);
+    case TP_BF16: return launch_colour_t<__nv_bfloat16, float>(n, colour, nc, x, r, S, L, C, s);
   }
   return cudaErrorInvalidValue;
 }
+
+namespace {
+
+// the type-0 (interior) bases and eigenvalues of a level as the kernel parameter's bytes
+template <typename T, int P>
+void fill_interior(std::vector<unsigned char>& out, const std::vector<double>& S, const std::vector<double>& lam) {
+  VPInterior<T, P> c{};
+  for (int d = 0; d < 3; ++d) {
+    for (int X = 0; X < P; ++X)
+      for (int a = 0; a < P; ++a) c.S[d][X * P + a] = (T)S[(size_t)(d * 4) * kMaxP * kMaxP + X * kMaxP + a];
+    for (int a = 0; a < P; ++a) c.lam[d][a] = (T)lam[(size_t)(d * 4) * kMaxP + a];
+  }
+  out.assign(reinterpret_cast<const unsigned char*>(&c), reinterpret_cast<const unsigned char*>(&c) + sizeof(c));
+}
+
+template <typename T>
+void fill_interior_t(int n, std::vector<unsigned char>& out, const std::vector<double>& S,
+                     const std::vector<double>& lam) {
+  switch (n) {
+    case 2: fill_interior<T, 4>(out, S, lam); break;
+    case 3: fill_interior<T, 6>(out, S, lam); break;
+    case 4: fill_interior<T, 8>(out, S, lam); break;
+    case 5: fill_interior<T, 10>(out, S, lam); break;
+    case 6: fill_interior<T, 12>(out, S, lam); break;
+    case 7: fill_interior<T, 14>(out, S, lam); break;
+    case 8: fill_interior<T, 16>(out, S, lam); break;
+  }
+}
+
+}  // namespace
 
 // Eigenbases of the 1D patch factors of one level, uploaded in the arithmetic precision (FP64 for
 // FP64 vectors, FP32 otherwise):
 // S[(d*4 + t)][X * kMaxP + a] = component X of eigenvector a, L[(d*4 + t)][a] = its eigenvalue,
 // for direction d and boundary type t. A mesh of min(nc, 4) cells with the level's h has every
-// type of the level at its vertices 1 .. min(nc, 4) - 1.
-tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out) {
+// type of the level at its vertices 1 .. min(nc, 4) - 1. C_out: the interior (type 0) bases and
+// eigenvalues as the bytes of the kernel's VPInterior parameter (zeros in a direction without
+// interior vertices, where no patch takes them).
+tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void** S_out, void** L_out,
+                    std::vector<unsigned char>* C_out) {
   const int n = op->n, P = 2 * n;
   std::vector<double> S((size_t)12 * kMaxP * kMaxP, 0.0), lam((size_t)12 * kMaxP, 0.0);
   for (int d = 0; d < 3; ++d) {
@@ -325,6 +458,8 @@ tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void*
     }
   }
   const size_t eb = prec == TP_FP64 ? 8 : 4;
+  if (eb == 8) fill_interior_t<double>(n, *C_out, S, lam);
+  else fill_interior_t<float>(n, *C_out, S, lam);
   std::vector<unsigned char> hS(S.size() * eb), hL(lam.size() * eb);
   for (size_t i = 0; i < S.size(); ++i) {
     if (eb == 8) reinterpret_cast<double*>(hS.data())[i] = S[i];
