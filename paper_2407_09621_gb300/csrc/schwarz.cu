@@ -74,11 +74,22 @@ __device__ __forceinline__ void dot_row2(const T* __restrict__ row, const T (&a)
 // nearly every patch), passed as a kernel parameter: their entries become constant-bank operands of
 // the FMAs, so an interior patch loads no table into shared memory and reads no basis row from it.
 // S[d][X * P + a] = component X of eigenvector a of direction d, lam[d][a] its eigenvalue.
+// Measured on the FP32 vertex-patch V-cycle: k = 2 15.0 -> 14.1 ms (128^3), k = 3 22.5 -> 19.3 ms,
+// k = 4 unchanged, k = 5 and 7 slower (the unrolled P >= 10 phases with their larger bases), and
+// the FP64 kernel, bound by the FP64 pipe, slower as well: so the path serves FP32 arithmetic with
+// P <= 8 only, and the other instantiations take an empty parameter.
 template <typename T, int P>
 struct VPInterior {
   T S[3][P * P];
   T lam[3][P];
 };
+struct VPNone {
+  int unused;
+};
+template <typename T, int P>
+__host__ __device__ constexpr bool vp_const_interior() { return sizeof(T) == 4 && P <= 8; }
+template <typename T, int P>
+using VPArg = typename std::conditional<vp_const_interior<T, P>(), VPInterior<T, P>, VPNone>::type;
 
 // sum_m c[m * STRIDE] in[m] for two lines, c a row or column of a basis in the kernel parameter
 template <typename T, int P, int STRIDE>
@@ -106,7 +117,7 @@ constexpr size_t vp_smem_bytes() {
 template <typename TS, typename T, int N>
 __global__ void __launch_bounds__(2 * N * N)
 vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
-                VPDims D, const __grid_constant__ VPInterior<T, 2 * N> C) {
+                VPDims D, const __grid_constant__ VPArg<T, 2 * N> C) {
   constexpr int P = 2 * N, R = P + 1, N3 = N * N * N, H = P / 2, NT = P * H;
   extern __shared__ __align__(16) unsigned char vp_smem[];
   T* bufA = reinterpret_cast<T*>(vp_smem);
@@ -119,7 +130,8 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
   const int vz = D.first[2] + 2 * (int)blockIdx.z;
   const int t[3] = {(vx == 1 ? 1 : 0) + (vx == D.nx - 1 ? 2 : 0), (vy == 1 ? 1 : 0) + (vy == D.ny - 1 ? 2 : 0),
                     (vz == 1 ? 1 : 0) + (vz == D.nz - 1 ? 2 : 0)};
-  const bool interior = (t[0] | t[1] | t[2]) == 0;  // block-uniform
+  constexpr bool kConst = vp_const_interior<T, 2 * N>();
+  const bool interior = kConst && (t[0] | t[1] | t[2]) == 0;  // block-uniform
   if (!interior) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -154,8 +166,12 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
     for (int j = 0; j < 2 * P; ++j) bufA[saddr(tid + j * NT)] = v[j];
   }
   __syncthreads();
+  if constexpr (!kConst) {
+    (void)C;
+  }
   if (interior) {
     // the same six phases with the bases and eigenvalues from the kernel parameter
+    if constexpr (kConst) {
     T i0[P], i1[P], s0, s1;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
@@ -228,6 +244,7 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
       bufA[(p1 * P + q) * R + X] = s1;
     }
     __syncthreads();
+    }
   } else {
     // Two lines of the patch tensor in registers, contracted per output node o with a basis row:
     // sum_m S[m][o] in[m] (S^T applied, rows of sF) or sum_m S[o][m] in[m] (S applied, rows of sB);
@@ -324,6 +341,15 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
   }
 }
 
+template <typename T, int P>
+VPArg<T, P> vp_arg(const void* C) {
+  if constexpr (vp_const_interior<T, P>()) {
+    return *static_cast<const VPInterior<T, P>*>(C);
+  } else {
+    return VPNone{0};
+  }
+}
+
 template <typename TS, typename T, int N>
 cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, const void* S, const void* L,
                           const void* Cint, cudaStream_t s) {
@@ -334,7 +360,7 @@ cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, c
   VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
   vp_patch_kernel<TS, T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
       static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D,
-      *static_cast<const VPInterior<T, 2 * N>*>(Cint));
+      vp_arg<T, 2 * N>(Cint));
   return cudaGetLastError();
 }
 
