@@ -59,8 +59,9 @@ __device__ __forceinline__ dd fma(dd a, dd b, dd c) {
 }
 
 // double -> dd with integer operations only: hi is the double's top 24 significand bits
-// (truncated), lo the remaining 29 bits rounded to FP32. Magnitudes below 2^-126 become 0 and
-// above 2^127 are not representable (this library's vectors stay far inside that range).
+// (truncated), lo the remaining 29 bits rounded to FP32. Magnitudes below 2^-126 become 0, those
+// below 2^-74 keep hi alone (24 bits: lo would be below the FP32 normal range), and above 2^127 are
+// not representable (this library's vectors stay far inside that range).
 __device__ __forceinline__ dd dd_from_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned sign = (unsigned)(b >> 63) << 31;
