@@ -84,7 +84,7 @@ typedef struct {
                    (about 48 significand bits) and the contractions and face terms run as
                    error-free FP32 transformations on the FMA pipe, the result joined back to FP64
                    on store. On GB300, whose FP64 pipe delivers ~1.25 TFLOP/s against ~75 for FP32,
-                   this is ~3x the FP64 kernel's rate; the relative error per apply is ~1e-14
+                   this is ~3.5-4x the FP64 kernel's rate; the relative error per apply is ~1e-14
                    (FP64 arithmetic: ~1e-15), inside the 1e-12 FP64 tolerance. Inputs of magnitude
                    below 2^-126 are taken as 0, below 2^-74 with 24 significand bits, and above
                    2^127 are out of range. 0 (default): FP64 arithmetic on the DFMA pipe.

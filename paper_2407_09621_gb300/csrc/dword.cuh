@@ -5,10 +5,12 @@
 // keeping a relative error per operation near 2^-47.
 //
 // The building blocks are the classical error-free transformations: TwoSum (Knuth: s + e = a + b
-// exactly, 6 operations), Fast2Sum (Dekker: the same when |a| >= |b|, 3 operations) and the exact
-// product a*b = p + fma(a, b, -p). The multiply-add a*b + c forms the product of the high parts
-// exactly, adds the two cross products (their low-order product is below the format's precision),
-// adds c's high part with TwoSum, folds the low-order terms and renormalizes with Fast2Sum.
+// exactly, 6 operations) and the exact product a*b = p + fma(a, b, -p). The multiply-add a*b + c
+// forms the product of the high parts exactly, adds the two cross products (their low-order product
+// is below the format's precision), adds c's high part with TwoSum and folds the low-order terms into
+// lo. Results are not renormalized (no Fast2Sum after each operation): TwoSum of the high parts is
+// exact whatever the size of lo, the few terms a contraction sums keep lo within a few ulp of hi,
+// and the join to FP64 adds hi and lo exactly; this saves 3 of 15 operations per multiply-add.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -30,14 +32,10 @@ __device__ __forceinline__ dd dd_two_sum(float a, float b) {
   const float bb = s - a;
   return dd(s, (a - (s - bb)) + (b - bb));
 }
-__device__ __forceinline__ dd dd_fast_two_sum(float a, float b) {
-  const float s = a + b;
-  return dd(s, b - (s - a));
-}
 
 __device__ __forceinline__ dd operator+(dd a, dd b) {
   const dd s = dd_two_sum(a.hi, b.hi);
-  return dd_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+  return dd(s.hi, s.lo + (a.lo + b.lo));
 }
 __device__ __forceinline__ dd operator-(dd a, dd b) { return a + dd(-b.hi, -b.lo); }
 __device__ __forceinline__ dd& operator+=(dd& a, dd b) { return a = a + b; }
@@ -46,7 +44,7 @@ __device__ __forceinline__ dd operator*(dd a, dd b) {
   float e = fmaf(a.hi, b.hi, -p);
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
-  return dd_fast_two_sum(p, e);
+  return dd(p, e);
 }
 // a * b + c
 __device__ __forceinline__ dd fma(dd a, dd b, dd c) {
@@ -55,7 +53,7 @@ __device__ __forceinline__ dd fma(dd a, dd b, dd c) {
   e = fmaf(a.hi, b.lo, e);
   e = fmaf(a.lo, b.hi, e);
   const dd s = dd_two_sum(p, c.hi);
-  return dd_fast_two_sum(s.hi, s.lo + (e + c.lo));
+  return dd(s.hi, s.lo + (e + c.lo));
 }
 
 // double -> dd with integer operations only: hi is the double's top 24 significand bits
