@@ -22,6 +22,7 @@
 // r and added to x cell by cell, so that a warp's accesses are contiguous.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -73,33 +74,81 @@ __device__ __forceinline__ void dot_row2(const T* __restrict__ row, const T (&a)
 // The bases and eigenvalues of interior patches (boundary type 0 in every direction: on fine levels
 // nearly every patch), passed as a kernel parameter: their entries become constant-bank operands of
 // the FMAs, so an interior patch loads no table into shared memory and reads no basis row from it.
-// S[d][X * P + a] = component X of eigenvector a of direction d, lam[d][a] its eigenvalue.
-// Measured on the FP32 vertex-patch V-cycle: k = 2 15.0 -> 14.1 ms (128^3), k = 3 22.5 -> 19.3 ms,
-// k = 4 unchanged, k = 5 and 7 slower (the unrolled P >= 10 phases with their larger bases), and
-// the FP64 kernel, bound by the FP64 pipe, slower as well: so the path serves FP32 arithmetic with
-// P <= 8 only, and the other instantiations take an empty parameter.
+// An interior patch's 1D factors are mirror-symmetric about the patch vertex, so its eigenvectors
+// are even or odd (computed as such, in the even and odd subspaces): H = P/2 of each. In the
+// kernel's eigen coordinates the even ones come first. E[d][m * H + c] is component m < H of even
+// eigenvector c (component P-1-m is the same), O[d][m * H + c] that of odd eigenvector c (component
+// P-1-m is its negative), lam[d] the eigenvalues in the same order. A contraction then costs P^2/2
+// multiply-adds instead of P^2 (as the even-odd form of the CUDA-core kernel's 1D matrices), and the
+// parameter holds half the entries. Measured on the FP32 vertex-patch V-cycle, against full bases in
+// the parameter for P <= 8 and shared-memory bases above: k = 2 6.51 -> 6.21 ms (96^3), k = 3
+// 19.41 -> 18.92 ms (128^3), k = 5 14.93 -> 14.14 ms (54^3), k = 7 7.84 -> 7.33 ms (40^3). The FP64
+// kernel, bound by the FP64 pipe, measured slower with full bases in the parameter and keeps the
+// shared-memory path: the path serves FP32 arithmetic, and the other instantiations take an empty
+// parameter.
 template <typename T, int P>
 struct VPInterior {
-  T S[3][P * P];
+  T E[3][(P / 2) * (P / 2)];
+  T O[3][(P / 2) * (P / 2)];
   T lam[3][P];
 };
 struct VPNone {
   int unused;
 };
 template <typename T, int P>
-__host__ __device__ constexpr bool vp_const_interior() { return sizeof(T) == 4 && P <= 8; }
+__host__ __device__ constexpr bool vp_const_interior() { return sizeof(T) == 4 && P <= 16; }
 template <typename T, int P>
 using VPArg = typename std::conditional<vp_const_interior<T, P>(), VPInterior<T, P>, VPNone>::type;
 
-// sum_m c[m * STRIDE] in[m] for two lines, c a row or column of a basis in the kernel parameter
-template <typename T, int P, int STRIDE>
-__device__ __forceinline__ void dotc2(const T* c, const T (&a)[P], const T (&b)[P], T& sa, T& sb) {
-  sa = T(0);
-  sb = T(0);
+// S^T applied to two lines in the even/odd eigenbasis (E, O from the kernel parameter): outputs in
+// eigen coordinates, the even ones first
+template <typename T, int P>
+__device__ __forceinline__ void eo_fwd2(const T* E, const T* O, const T (&a)[P], const T (&b)[P], T (&ya)[P],
+                                        T (&yb)[P]) {
+  constexpr int H = P / 2;
+  T ea[H], oa[H], eb[H], ob[H];
 #pragma unroll
-  for (int m = 0; m < P; ++m) {
-    sa = fma(c[m * STRIDE], a[m], sa);
-    sb = fma(c[m * STRIDE], b[m], sb);
+  for (int m = 0; m < H; ++m) {
+    ea[m] = a[m] + a[P - 1 - m];
+    oa[m] = a[m] - a[P - 1 - m];
+    eb[m] = b[m] + b[P - 1 - m];
+    ob[m] = b[m] - b[P - 1 - m];
+  }
+#pragma unroll
+  for (int c = 0; c < H; ++c) {
+    T se = T(0), so = T(0), te = T(0), to = T(0);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+      se = fma(E[m * H + c], ea[m], se);
+      te = fma(E[m * H + c], eb[m], te);
+      so = fma(O[m * H + c], oa[m], so);
+      to = fma(O[m * H + c], ob[m], to);
+    }
+    ya[c] = se;
+    yb[c] = te;
+    ya[H + c] = so;
+    yb[H + c] = to;
+  }
+}
+// S applied to two lines given in eigen coordinates (even first): node values
+template <typename T, int P>
+__device__ __forceinline__ void eo_inv2(const T* E, const T* O, const T (&a)[P], const T (&b)[P], T (&ya)[P],
+                                        T (&yb)[P]) {
+  constexpr int H = P / 2;
+#pragma unroll
+  for (int X = 0; X < H; ++X) {
+    T se = T(0), so = T(0), te = T(0), to = T(0);
+#pragma unroll
+    for (int c = 0; c < H; ++c) {
+      se = fma(E[X * H + c], a[c], se);
+      te = fma(E[X * H + c], b[c], te);
+      so = fma(O[X * H + c], a[H + c], so);
+      to = fma(O[X * H + c], b[H + c], to);
+    }
+    ya[X] = se + so;
+    ya[P - 1 - X] = se - so;
+    yb[X] = te + to;
+    yb[P - 1 - X] = te - to;
   }
 }
 
@@ -172,76 +221,79 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
   if (interior) {
     // the same six phases with the bases and eigenvalues from the kernel parameter
     if constexpr (kConst) {
-    T i0[P], i1[P], s0, s1;
+    T i0[P], i1[P], y0[P], y1[P];
+    // S_x^T along x-lines (Z = p, Y = q): bufA -> bufB
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       i0[m] = bufA[(p0 * P + q) * R + m];
       i1[m] = bufA[(p1 * P + q) * R + m];
     }
+    eo_fwd2<T, P>(C.E[0], C.O[0], i0, i1, y0, y1);
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-      dotc2<T, P, P>(C.S[0] + a, i0, i1, s0, s1);  // (S_x^T)[a][m] = S_x[m][a]
-      bufB[(p0 * P + q) * R + a] = s0;
-      bufB[(p1 * P + q) * R + a] = s1;
+      bufB[(p0 * P + q) * R + a] = y0[a];
+      bufB[(p1 * P + q) * R + a] = y1[a];
     }
     __syncthreads();
+    // S_y^T along y-lines (Z = p, a = q): bufB -> bufA
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       i0[m] = bufB[(p0 * P + m) * R + q];
       i1[m] = bufB[(p1 * P + m) * R + q];
     }
+    eo_fwd2<T, P>(C.E[1], C.O[1], i0, i1, y0, y1);
 #pragma unroll
     for (int b = 0; b < P; ++b) {
-      dotc2<T, P, P>(C.S[1] + b, i0, i1, s0, s1);
-      bufA[(p0 * P + b) * R + q] = s0;
-      bufA[(p1 * P + b) * R + q] = s1;
+      bufA[(p0 * P + b) * R + q] = y0[b];
+      bufA[(p1 * P + b) * R + q] = y1[b];
     }
     __syncthreads();
+    // z-lines (b = p, a = q): S_z^T, the scaling, S_z, in registers (a thread owns its z-lines)
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       i0[m] = bufA[(m * P + p0) * R + q];
       i1[m] = bufA[(m * P + p1) * R + q];
     }
+    eo_fwd2<T, P>(C.E[2], C.O[2], i0, i1, y0, y1);
     {
-      // S_z^T and the scaling; the z-lines stay in registers for S_z (a thread owns them)
       const T l0 = C.lam[0][q] + C.lam[1][p0], l1 = C.lam[0][q] + C.lam[1][p1];
-      T t0[P], t1[P];
 #pragma unroll
       for (int c = 0; c < P; ++c) {
-        dotc2<T, P, P>(C.S[2] + c, i0, i1, s0, s1);
-        t0[c] = s0 / (l0 + C.lam[2][c]);
-        t1[c] = s1 / (l1 + C.lam[2][c]);
-      }
-#pragma unroll
-      for (int Z = 0; Z < P; ++Z) {
-        dotc2<T, P, 1>(C.S[2] + Z * P, t0, t1, s0, s1);
-        bufA[(Z * P + p0) * R + q] = s0;
-        bufA[(Z * P + p1) * R + q] = s1;
+        y0[c] = y0[c] / (l0 + C.lam[2][c]);
+        y1[c] = y1[c] / (l1 + C.lam[2][c]);
       }
     }
+    eo_inv2<T, P>(C.E[2], C.O[2], y0, y1, i0, i1);
+#pragma unroll
+    for (int Z = 0; Z < P; ++Z) {
+      bufA[(Z * P + p0) * R + q] = i0[Z];
+      bufA[(Z * P + p1) * R + q] = i1[Z];
+    }
     __syncthreads();
+    // S_y along y-lines (Z = p, a = q): bufA -> bufB
 #pragma unroll
     for (int b = 0; b < P; ++b) {
       i0[b] = bufA[(p0 * P + b) * R + q];
       i1[b] = bufA[(p1 * P + b) * R + q];
     }
+    eo_inv2<T, P>(C.E[1], C.O[1], i0, i1, y0, y1);
 #pragma unroll
     for (int Y = 0; Y < P; ++Y) {
-      dotc2<T, P, 1>(C.S[1] + Y * P, i0, i1, s0, s1);
-      bufB[(p0 * P + Y) * R + q] = s0;
-      bufB[(p1 * P + Y) * R + q] = s1;
+      bufB[(p0 * P + Y) * R + q] = y0[Y];
+      bufB[(p1 * P + Y) * R + q] = y1[Y];
     }
     __syncthreads();
+    // S_x along x-lines (Z = p, Y = q): bufB -> bufA
 #pragma unroll
     for (int a = 0; a < P; ++a) {
       i0[a] = bufB[(p0 * P + q) * R + a];
       i1[a] = bufB[(p1 * P + q) * R + a];
     }
+    eo_inv2<T, P>(C.E[0], C.O[0], i0, i1, y0, y1);
 #pragma unroll
     for (int X = 0; X < P; ++X) {
-      dotc2<T, P, 1>(C.S[0] + X * P, i0, i1, s0, s1);
-      bufA[(p0 * P + q) * R + X] = s0;
-      bufA[(p1 * P + q) * R + X] = s1;
+      bufA[(p0 * P + q) * R + X] = y0[X];
+      bufA[(p1 * P + q) * R + X] = y1[X];
     }
     __syncthreads();
     }
@@ -421,30 +473,72 @@ cudaError_t vp_colour(tp_precision prec, int n, const int nc[3], int colour, voi
 
 namespace {
 
-// the type-0 (interior) bases and eigenvalues of a level as the kernel parameter's bytes
+// the interior bases and eigenvalues of a level as the kernel parameter's bytes, from the even and
+// odd half-bases EO[d] (2 H x H: even then odd, [m * H + c]) and their eigenvalues LEO[d] (even then odd)
 template <typename T, int P>
-void fill_interior(std::vector<unsigned char>& out, const std::vector<double>& S, const std::vector<double>& lam) {
+void fill_interior(std::vector<unsigned char>& out, const std::vector<double> (&EO)[3], const std::vector<double> (&LEO)[3]) {
+  constexpr int H = P / 2;
   VPInterior<T, P> c{};
   for (int d = 0; d < 3; ++d) {
-    for (int X = 0; X < P; ++X)
-      for (int a = 0; a < P; ++a) c.S[d][X * P + a] = (T)S[(size_t)(d * 4) * kMaxP * kMaxP + X * kMaxP + a];
-    for (int a = 0; a < P; ++a) c.lam[d][a] = (T)lam[(size_t)(d * 4) * kMaxP + a];
+    if (EO[d].empty()) continue;  // no interior vertex in this direction: no patch takes the tables
+    for (int e = 0; e < H * H; ++e) {
+      c.E[d][e] = (T)EO[d][e];
+      c.O[d][e] = (T)EO[d][H * H + e];
+    }
+    for (int a = 0; a < P; ++a) c.lam[d][a] = (T)LEO[d][a];
   }
   out.assign(reinterpret_cast<const unsigned char*>(&c), reinterpret_cast<const unsigned char*>(&c) + sizeof(c));
 }
 
 template <typename T>
-void fill_interior_t(int n, std::vector<unsigned char>& out, const std::vector<double>& S,
-                     const std::vector<double>& lam) {
+void fill_interior_t(int n, std::vector<unsigned char>& out, const std::vector<double> (&EO)[3],
+                     const std::vector<double> (&LEO)[3]) {
   switch (n) {
-    case 2: fill_interior<T, 4>(out, S, lam); break;
-    case 3: fill_interior<T, 6>(out, S, lam); break;
-    case 4: fill_interior<T, 8>(out, S, lam); break;
-    case 5: fill_interior<T, 10>(out, S, lam); break;
-    case 6: fill_interior<T, 12>(out, S, lam); break;
-    case 7: fill_interior<T, 14>(out, S, lam); break;
-    case 8: fill_interior<T, 16>(out, S, lam); break;
+    case 2: fill_interior<T, 4>(out, EO, LEO); break;
+    case 3: fill_interior<T, 6>(out, EO, LEO); break;
+    case 4: fill_interior<T, 8>(out, EO, LEO); break;
+    case 5: fill_interior<T, 10>(out, EO, LEO); break;
+    case 6: fill_interior<T, 12>(out, EO, LEO); break;
+    case 7: fill_interior<T, 14>(out, EO, LEO); break;
+    case 8: fill_interior<T, 16>(out, EO, LEO); break;
   }
+}
+
+// The eigenpairs of a mirror-symmetric P x P pencil (Mp, Lp) in its even and odd subspaces (basis
+// vectors (e_m +- e_{P-1-m}) / sqrt(2), m < H): EO = [even half-components, odd half-components]
+// (component m < H of the full eigenvector, each H x H as [m * H + c]), LEO = [even eigenvalues,
+// odd eigenvalues]. The full vectors are M-orthonormal like those of gen_eig. False if the pencil is
+// not mirror-symmetric or a reduced mass matrix is not positive definite.
+bool split_even_odd(int P, const std::vector<double>& Mp, const std::vector<double>& Lp, std::vector<double>& EO,
+                    std::vector<double>& LEO) {
+  const int H = P / 2;
+  double big = 0.0, asym = 0.0;
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j) {
+      big = std::fmax(big, std::fabs(Lp[(size_t)i * P + j]) + std::fabs(Mp[(size_t)i * P + j]));
+      asym = std::fmax(asym, std::fabs(Lp[(size_t)i * P + j] - Lp[(size_t)(P - 1 - i) * P + P - 1 - j]) +
+                                 std::fabs(Mp[(size_t)i * P + j] - Mp[(size_t)(P - 1 - i) * P + P - 1 - j]));
+    }
+  if (asym > 1e-12 * big) return false;  // not mirror-symmetric: no even/odd eigenvectors
+  EO.assign((size_t)2 * H * H, 0.0);
+  LEO.assign((size_t)P, 0.0);
+  for (int par = 0; par < 2; ++par) {
+    const double sg = par ? -1.0 : 1.0;
+    std::vector<double> Mr((size_t)H * H), Lr((size_t)H * H), lv, V;
+    for (int i = 0; i < H; ++i)
+      for (int j = 0; j < H; ++j) {
+        const int ri = P - 1 - i, rj = P - 1 - j;
+        Mr[(size_t)i * H + j] = 0.5 * (Mp[(size_t)i * P + j] + sg * Mp[(size_t)i * P + rj] + sg * Mp[(size_t)ri * P + j] +
+                                       Mp[(size_t)ri * P + rj]);
+        Lr[(size_t)i * H + j] = 0.5 * (Lp[(size_t)i * P + j] + sg * Lp[(size_t)i * P + rj] + sg * Lp[(size_t)ri * P + j] +
+                                       Lp[(size_t)ri * P + rj]);
+      }
+    if (!gen_eig(H, Mr, Lr, lv, V)) return false;
+    for (int m = 0; m < H; ++m)
+      for (int c = 0; c < H; ++c) EO[(size_t)par * H * H + m * H + c] = V[(size_t)m * H + c] / std::sqrt(2.0);
+    for (int c = 0; c < H; ++c) LEO[(size_t)par * H + c] = lv[c];
+  }
+  return true;
 }
 
 }  // namespace
@@ -460,6 +554,7 @@ tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void*
                     std::vector<unsigned char>* C_out) {
   const int n = op->n, P = 2 * n;
   std::vector<double> S((size_t)12 * kMaxP * kMaxP, 0.0), lam((size_t)12 * kMaxP, 0.0);
+  std::vector<double> EO[3], LEO[3];  // interior patches: even/odd half-bases (kernel parameter)
   for (int d = 0; d < 3; ++d) {
     if (nc[d] < 2) { set_error("vertex-patch smoother: fewer than two cells in a direction"); return TP_ERR_UNSUPPORTED; }
     const int m = nc[d] >= 4 ? 4 : nc[d];
@@ -481,11 +576,15 @@ tp_status vp_tables(const tp_op_s* op, const int nc[3], tp_precision prec, void*
       for (int X = 0; X < P; ++X)
         for (int a = 0; a < P; ++a) S[(size_t)(d * 4 + t) * kMaxP * kMaxP + X * kMaxP + a] = V[(size_t)X * P + a];
       for (int a = 0; a < P; ++a) lam[(size_t)(d * 4 + t) * kMaxP + a] = lv[a];
+      if (t == 0 && !split_even_odd(P, Mp, Lp, EO[d], LEO[d])) {
+        set_error("vertex-patch smoother: interior patch not mirror-symmetric or not positive definite");
+        return TP_ERR_INVALID_ARG;
+      }
     }
   }
   const size_t eb = prec == TP_FP64 ? 8 : 4;
-  if (eb == 8) fill_interior_t<double>(n, *C_out, S, lam);
-  else fill_interior_t<float>(n, *C_out, S, lam);
+  if (eb == 8) fill_interior_t<double>(n, *C_out, EO, LEO);
+  else fill_interior_t<float>(n, *C_out, EO, LEO);
   std::vector<unsigned char> hS(S.size() * eb), hL(lam.size() * eb);
   for (size_t i = 0; i < S.size(); ++i) {
     if (eb == 8) reinterpret_cast<double*>(hS.data())[i] = S[i];

@@ -338,9 +338,11 @@ VP = 1
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("k,dims", [(1, (4, 4, 4)), (2, (4, 6, 2)), (3, (4, 2, 4)), (2, (6, 4, 4))])
+@pytest.mark.parametrize("k,dims", [(1, (4, 4, 4)), (2, (4, 6, 2)), (3, (4, 2, 4)), (2, (6, 4, 4)), (3, (4, 6, 4)),
+                                    (5, (4, 4, 4))])
 def test_vertex_patch_smoother_matches_oracle(prec, k, dims):
-    """One sweep (colours ascending) on the finest level against the oracle's dense patch solves."""
+    """One sweep (colours ascending) on the finest level against the oracle's dense patch solves. With
+    at least four cells in every direction some patches are interior ones (the even/odd bases)."""
     from oracle.schwarz import VertexPatchSmoother
     from oracle.sipg import assemble
     g = GpuMG(None, k, prec, coarse_cells=1, smoother=VP, dims=dims)
