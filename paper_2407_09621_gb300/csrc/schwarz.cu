@@ -23,6 +23,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <type_traits>
 #include <vector>
 
@@ -159,11 +160,18 @@ constexpr size_t vp_smem_bytes() {
   return sizeof(T) * (2 * (2 * N) * (2 * N) * (2 * N + 1) + 6 * (2 * N) * (2 * N) + 3 * (2 * N));
 }
 
+// FP32 vectors at n = 4 (k = 3) with 16-byte aligned x and r: global accesses by whole cell rows
+// (one 16-byte load or store per row, four rows per thread) instead of single values. A warp's rows
+// are two x-adjacent cells (512 contiguous bytes), and the shared stores of its rows' values hit 32
+// distinct banks, where the value-by-value scatter met two-way conflicts.
+template <typename TS, int N>
+__host__ __device__ constexpr bool vp_rows() { return std::is_same<TS, float>::value && N == 4; }
+
 // P^2 / 2 threads per patch; in every phase a thread owns two lines of the contracted direction,
 // lines p0 and p0 + P/2 of the outer index, so that each basis row it loads serves two lines.
 // TS: storage type of x and r; T: arithmetic type (FP32 for FP16/BF16 storage) of the tables and
-// of every operation.
-template <typename TS, typename T, int N>
+// of every operation. ROWS: the row-wise global accesses above (only where vp_rows holds).
+template <typename TS, typename T, int N, bool ROWS>
 __global__ void __launch_bounds__(2 * N * N)
 vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restrict__ Stab, const T* __restrict__ Ltab,
                 VPDims D, const __grid_constant__ VPArg<T, 2 * N> C) {
@@ -207,7 +215,30 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
     const int X = (lc & 1) * N + node % N, Y = ((lc >> 1) & 1) * N + (node / N) % N, Z = (lc >> 2) * N + node / (N * N);
     return (Z * P + Y) * R + X;
   };
-  {
+  // Row-wise form: row tid + NT * i of the patch (4 per thread) is row rr = tid % N^2 (nodes
+  // rr * N .. rr * N + N - 1) of local cell lc = 2 i + tid / N^2.
+  static_assert(!ROWS || (vp_rows<TS, N>() && NT == 2 * N * N), "row-wise accesses: FP32 vectors, n = 4");
+  auto grow = [&](int i) {
+    const int lc = 2 * i + tid / (N * N);
+    return (c0 + ((long long)(lc >> 2) * D.ny + ((lc >> 1) & 1)) * D.nx + (lc & 1)) * N3 + (tid % (N * N)) * N;
+  };
+  auto srow = [&](int i) {
+    const int lc = 2 * i + tid / (N * N), rr = tid % (N * N);
+    return (((lc >> 2) * N + rr / N) * P + ((lc >> 1) & 1) * N + rr % N) * R + (lc & 1) * N;
+  };
+  if constexpr (ROWS) {
+    float4 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __ldg(reinterpret_cast<const float4*>(r + grow(i)));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      T* d = bufA + srow(i);
+      d[0] = v[i].x;
+      d[1] = v[i].y;
+      d[2] = v[i].z;
+      d[3] = v[i].w;
+    }
+  } else {
     T v[2 * P];  // all loads in flight before the shared stores
 #pragma unroll
     for (int j = 0; j < 2 * P; ++j) v[j] = load_as<TS, T>(r + gaddr(tid + j * NT));
@@ -384,7 +415,20 @@ vp_patch_kernel(TS* __restrict__ x, const TS* __restrict__ r, const T* __restric
     __syncthreads();
   }
   // x_P += the correction, cell by cell like the gather
-  {
+  if constexpr (ROWS) {
+    float4 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = *reinterpret_cast<const float4*>(x + grow(i));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const T* c = bufA + srow(i);
+      v[i].x += c[0];
+      v[i].y += c[1];
+      v[i].z += c[2];
+      v[i].w += c[3];
+      *reinterpret_cast<float4*>(x + grow(i)) = v[i];
+    }
+  } else {
     T v[2 * P];
 #pragma unroll
     for (int j = 0; j < 2 * P; ++j) v[j] = static_cast<T>(x[gaddr(tid + j * NT)]);
@@ -410,7 +454,15 @@ cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, c
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
   VPDims D{nc[0], nc[1], nc[2], {par[0] ? 1 : 2, par[1] ? 1 : 2, par[2] ? 1 : 2}};
-  vp_patch_kernel<TS, T, N><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
+  if constexpr (vp_rows<TS, N>()) {
+    if ((((uintptr_t)x | (uintptr_t)r) & 15) == 0) {
+      vp_patch_kernel<TS, T, N, true><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
+          static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D,
+          vp_arg<T, 2 * N>(Cint));
+      return cudaGetLastError();
+    }
+  }
+  vp_patch_kernel<TS, T, N, false><<<grid, 2 * N * N, vp_smem_bytes<T, N>(), s>>>(
       static_cast<TS*>(x), static_cast<const TS*>(r), static_cast<const T*>(S), static_cast<const T*>(L), D,
       vp_arg<T, 2 * N>(Cint));
   return cudaGetLastError();
@@ -418,8 +470,14 @@ cudaError_t launch_colour(int colour, const int nc[3], void* x, const void* r, c
 
 template <typename TS, typename T, int N>
 cudaError_t prepare_colour() {
-  return cudaFuncSetAttribute(vp_patch_kernel<TS, T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)vp_smem_bytes<T, N>());
+  cudaError_t e = cudaFuncSetAttribute(vp_patch_kernel<TS, T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)vp_smem_bytes<T, N>());
+  if constexpr (vp_rows<TS, N>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(vp_patch_kernel<TS, T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)vp_smem_bytes<T, N>());
+  }
+  return e;
 }
 
 template <typename TS, typename T>
