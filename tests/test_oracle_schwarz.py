@@ -97,6 +97,44 @@ def test_patch_matrix_is_kronecker_sum_of_restricted_1d_factors(k, dims, v):
     assert _rel(AP, K(Lz, My, Mx) + K(Mz, Ly, Mx) + K(Mz, My, Lx)) < 1e-14
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_interior_patch_factors_split_into_even_and_odd_eigenproblems(k):
+    """A patch around an interior vertex (both neighbouring cells away from the boundary) has 1D
+    factors that are mirror-symmetric about the vertex, so its generalized eigenvectors are even or
+    odd and the two half-size problems in the even and odd subspaces give the whole spectrum. The
+    patches next to the boundary are not symmetric (the boundary face terms). Checked against the
+    library's dense generalized eigensolver."""
+    import scipy.linalg as sla
+    n, P = k + 1, 2 * (k + 1)
+    H = P // 2
+    J = np.eye(P)[::-1]
+    M, L = global_1d(k, 6, pen="config")
+    for v, interior in ((1, False), (2, True), (3, True), (5, False)):
+        s = slice((v - 1) * n, (v + 1) * n)
+        Mp, Lp = M[s, s], L[s, s]
+        sym = max(_rel(J @ Mp @ J, Mp), _rel(J @ Lp @ J, Lp))
+        if not interior:
+            assert sym > 1e-3
+            continue
+        assert sym < 1e-14
+        lam_ref = sla.eigh(Lp, Mp, eigvals_only=True)
+        lam, vecs = [], []
+        for sg in (1.0, -1.0):
+            B = np.zeros((P, H))  # orthonormal basis of the even (sg = 1) or odd subspace
+            for m in range(H):
+                B[m, m] = B[P - 1 - m, m] = 1.0 / np.sqrt(2.0)
+                B[P - 1 - m, m] *= sg
+            w, Y = sla.eigh(B.T @ Lp @ B, B.T @ Mp @ B)
+            lam += list(w)
+            vecs.append(B @ Y)
+        V = np.hstack(vecs)
+        assert np.allclose(np.sort(lam), lam_ref, rtol=1e-12, atol=0)
+        assert _rel(V.T @ Mp @ V, np.eye(P)) < 1e-12
+        assert _rel(Lp @ V, Mp @ V @ np.diag(lam)) < 1e-11
+        # the parity: even vectors equal their mirror image, odd ones its negative
+        assert _rel(J @ vecs[0], vecs[0]) < 1e-14 and _rel(J @ vecs[1], -vecs[1]) < 1e-14
+
+
 def test_smoother_iteration_contracts_the_energy_error():
     # as a stationary iteration for the SPD SIPG matrix the sweep reduces the A-norm of the error
     k, dims = 1, (4, 4, 4)
